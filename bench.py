@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Benchmark of the block-forest DG hot path (compressible Euler, SSP-RK3).
+
+Workload (default): 3D Euler on a jittered unit cube of 8 rotated hex root
+blocks with 8^3-cell blocks and two static refinement levels (71 leaves,
+36,352 cells), p = 2 (27 modes x 5 variables), isentropic vortex scaled into
+the cube, CFL 0.1; the FP32 form is the reported line, the FP64 form is
+measured beside it.  One step = one SSP-RK3 time increment (3 stages of
+guard fill + fused residual / inverse mass / stage combination, CFL minimum
+on the last stage).  Metric: DG DOF-updates per second per RK stage
+(= DOF x 3 x steps / time).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Timing: CUDA events on the forest's stream around each step, an L2 flush
+(256 MiB write) before every timed step, warm-up steps first, barrier and
+max over ranks.  Multi-GPU: independent replicas (the path has no exchange
+step on one GPU); value = sum over ranks.  --impl reference times the FP64
+CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+WORKLOAD = "3d-euler-jittered-cube-8roots-71leaves-n8-p2"
+HBM_FALLBACK = 6800.0
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": HBM_FALLBACK}, "fallback"
+
+
+def the_workload():
+    w = W.jitter3d_forest(seed=0)
+    return w, 2
+
+
+def vortex(x):
+    return W.isentropic_vortex(x, scale=10.0)
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.dev)],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.p is None:
+            return
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------- dist
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def barrier_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)])
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- CPU legs
+ORACLE_SAMPLE = r'''
+import sys, time, json, os
+sys.path.insert(0, {root!r})
+import numpy as np
+import workloads as W
+from oracle import dg, forest as FO
+w = W.jitter3d_forest(seed=0)
+S = dg.Solver(FO.build(w), 2, cfl=0.1)
+U = S.project(lambda x: W.isentropic_vortex(x, scale=10.0))
+leaves = list(range(0, len(S.leaves), max(1, len(S.leaves) // {nleaves})))[:{nleaves}]
+times = []
+for it in range({reps}):
+    t0 = time.perf_counter()
+    L = S.residual(U, leaves=leaves)
+    V = U + 1e-4 * L
+    times.append(time.perf_counter() - t0)
+dof = len(leaves) * S.nv * S.ops.M * S.n ** S.d
+print(json.dumps(dict(times=times, dof=dof, nleaves=len(leaves))))
+'''
+
+
+def run_oracle_sample(nleaves, reps):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_SAMPLE.format(root=ROOT, nleaves=nleaves, reps=reps)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline():
+    r = run_oracle_sample(71, 1)
+    t = sum(r["times"])
+    return {"value": r["dof"] * len(r["times"]) / t, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+            "sample": (f"one SSP-RK3 stage (guard fill + residual + mass solve + update) of the full "
+                       f"{r['nleaves']}-leaf workload in FP64 on 1 host thread, {t:.1f} s")}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    # each step: one SSP-RK3 stage on a leaf subset sized so the run stays short
+    per_leaf = 0.1
+    budget = 150.0
+    nleaves = int(max(1, min(71, budget / max(1, args.steps + args.warmup) / per_leaf)))
+    r = run_oracle_sample(nleaves, args.steps + args.warmup)
+    times = r["times"][args.warmup:]
+    t = sum(times)
+    value = r["dof"] * len(times) / t
+    line = {"impl": "reference", "metric": "DG DOF-updates/s per RK stage", "value": value,
+            "unit": "DOF-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_leaves": r["nleaves"]},
+            "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": f"one SSP-RK3 stage per step on {r['nleaves']} of the 71 leaves, FP64, 1 thread"},
+            "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU leg
+def timed_steps(f, steps, stream, flush, torch):
+    """Sum of per-step event times on the forest's stream, L2 flushed between."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            evs[i][0].record(stream)
+            f.rk_step()
+            evs[i][1].record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs)
+
+
+def run_ours(args):
+    import torch
+    import paper_2502_12620_gb300 as pkg
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    pk, pk_kind = peaks()
+    w, p = the_workload()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def make(prec):
+        f = pkg.Forest.from_workload(w, p=p, precision=prec, device=local, cfl=0.1)
+        f.set_stream(stream)
+        f.project(vortex)
+        return f
+
+    f32 = make(pkg.FP32)
+    dof = f32.n_leaves * f32.nv * f32.M * f32.nc
+    U0 = f32.get_state()
+    for _ in range(args.warmup):
+        f32.rk_step()
+    if ws > 1:
+        torch.distributed.barrier()
+    with Clocks(local) as ck:
+        ms = timed_steps(f32, args.steps, stream, flush, torch)
+    ms = barrier_max(ms, ws)
+    value = dof * 3 * args.steps / (ms / 1e3) * ws
+    status = f32.status_word()
+
+    # instrumented replay of the same steps: per-kernel durations
+    f32.set_state(U0)
+    f32.set_time(0.0)
+    f32.set_timing(True)
+    for _ in range(args.warmup):
+        f32.rk_step()
+    f32.kernel_times()
+    timed_steps(f32, args.steps, stream, flush, torch)
+    kt = f32.kernel_times()
+    f32.set_timing(False)
+    stage_ms, stage_n = kt["stage"]
+    nL, nc, NG = f32.n_leaves, f32.nc, 21
+    state_bytes_avg = dof * 4 * (2 + 3 + 3) / 3.0
+    geo_bytes = nL * nc * NG * 4 + nL * nc * 4 / 3.0
+    alg_bytes = state_bytes_avg + geo_bytes
+    achieved = alg_bytes / (stage_ms / stage_n / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": "k_stage<3,2,float>",
+            "bytes_per_launch": alg_bytes, "avg_launch_us": 1e3 * stage_ms / stage_n,
+            "peak_source": pk_kind}
+
+    # FP64 form of the same workload
+    f64 = make(pkg.FP64)
+    for _ in range(max(1, args.warmup // 2)):
+        f64.rk_step()
+    k64 = max(2, min(args.steps, 10))
+    ms64 = barrier_max(timed_steps(f64, k64, stream, flush, torch), ws)
+    value64 = dof * 3 * k64 / (ms64 / 1e3) * ws
+
+    # accuracy: FP32 vs FP64 after the same number of steps from the same state
+    f32.set_timing(False)
+    a32 = make(pkg.FP32)
+    a64 = make(pkg.FP64)
+    nacc = 20
+    for _ in range(nacc):
+        a32.rk_step()
+        a64.rk_step()
+    s32 = a32.get_state().astype(np.float64)
+    s64 = a64.get_state()
+    l2 = float(np.linalg.norm(s32 - s64) / np.linalg.norm(s64))
+    linf = float(np.max(np.abs(s32 - s64)) / np.max(np.abs(s64)))
+
+    # end to end through the public API with host buffers (pinned)
+    host = torch.empty(U0.size, dtype=torch.float32).pin_memory().numpy().reshape(U0.shape)
+    host[...] = U0
+    e = make(pkg.FP32)
+    for _ in range(2):
+        e.set_state(host)
+        e.rk_step()
+        e.get_state(host)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e.set_state(host)
+        e.rk_step()
+        e.get_state(host)
+    torch.cuda.synchronize()
+    te = barrier_max(time.perf_counter() - t0, ws)
+    e2e = {"value": dof * 3 * args.steps / te * ws, "unit": "DOF-updates/s",
+           "h2d_bytes_per_step": int(U0.nbytes), "d2h_bytes_per_step": int(U0.nbytes)}
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "DG DOF-updates/s per RK stage", "value": value, "unit": "DOF-updates/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "leaves": nL, "cells": nL * nc, "p": p, "dof": dof,
+                   "precision": "fp32", "l2_flush": "256 MiB write before every timed step",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": roof,
+        "fp64": {"value": value64, "unit": "DOF-updates/s", "ms_per_step": ms64 / k64, "steps": k64},
+        "accuracy": {"steps": nacc, "l2_rel_fp32_vs_fp64": l2, "linf_rel_fp32_vs_fp64": linf},
+        "e2e": e2e,
+        "clocks": ck.summary(),
+        "gpu_launches": 7 * args.steps,
+        "status_word": status,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

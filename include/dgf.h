@@ -1,0 +1,190 @@
+/*
+ * dgf.h -- C ABI of the GB300 block-forest discontinuous Galerkin library.
+ *
+ * The library implements the per-block explicit DG residual and SSP
+ * Runge-Kutta stage update for the compressible Euler equations on a forest
+ * of unstructured root blocks (arXiv 2502.12620):
+ *   - Sec. 2, Eqs. (1)-(5): DG weak form, mass matrix, Lax-Friedrichs flux;
+ *   - Sec. 3.1-3.3, Eq. (6): forest of quad/oct trees, N_seg^d cells per
+ *     block with (bi/tri)linearly interpolated nodes;
+ *   - Sec. 3.4, Eqs. (11)-(14): L2 data inheritance (split S, combine C);
+ *   - Sec. 3.5, Eqs. (15)-(17): guard-cell fill with relative rotation;
+ *   - Sec. 4.3: CFL time increment, snapshot, guard fill, face fluxes,
+ *     volume integral and update.
+ *
+ * Conventions (all calls):
+ *   - Every call returns a dgf_status: DGF_OK (0) or a negative code.  No
+ *     exception crosses the ABI.  dgf_last_error() returns a thread-local
+ *     message describing the last failure on the calling thread.
+ *   - A forest is an opaque handle created by dgf_forest_create and owned by
+ *     the caller until dgf_forest_destroy.  Device buffers belong to the
+ *     forest; they come from the caller's dgf_allocator (if given) or from
+ *     cudaMalloc.  Host arrays passed in are copied before the call returns.
+ *   - GPU work is enqueued on the stream set by dgf_set_stream (default: the
+ *     legacy default stream).  Only calls that return host values
+ *     synchronise with that stream.
+ *   - Pointers flagged "device" must be device pointers valid on the forest's
+ *     device; "host" pointers are plain host memory.  An is_device argument
+ *     selects between the two.
+ *
+ * Data formats (the same in every call):
+ *   - d = dim in {2,3}; n = n_seg; N = p+1; nv = d+2 conserved variables
+ *     (rho, rho*u_1..rho*u_d, E); M = N^d modes per variable.
+ *   - Modal state: tensor Legendre coefficients (unnormalised P_k), SoA
+ *     layout [leaf][var][mode][cell], mode m = sum_a k_a N^a, cell
+ *     c = sum_a i_a n^a (x fastest), leaves in canonical forest order.
+ *     Element type: double for DGF_FP64 forests, float for DGF_FP32.
+ *   - Canonical forest order: root by root, depth first, children
+ *     c = sum_a bit_a 2^a.  Face f = 2*axis + side (side 1 = +xi).
+ *   - Neighbour kinds: 0 same level, 1 coarser, 2 finer, 3 domain boundary
+ *     (outflow: the guard cell mirrors the face cell).
+ *   - Orientation code of a neighbour: my axis a maps to its axis pi[a] with
+ *     sign sigma[a]; code = perm_index(pi) * 2^d + sum_a [sigma[a] < 0] 2^a,
+ *     perm_index = rank of pi in lexicographic order of permutations.
+ */
+#ifndef DGF_H
+#define DGF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t dgf_status;
+
+#define DGF_OK 0
+#define DGF_EINVAL (-1)       /* bad argument or malformed forest            */
+#define DGF_ENOMEM (-2)       /* host or device allocation failed            */
+#define DGF_ECUDA (-3)        /* a CUDA runtime call failed                  */
+#define DGF_ENONFINITE (-4)   /* rho <= 0, p <= 0 or NaN met on the device   */
+#define DGF_ETIMEOUT (-5)     /* a bounded device wait gave up               */
+#define DGF_EBALANCE (-6)     /* refine/coarsen would break 2:1 balance      */
+#define DGF_ESTATE (-7)       /* call out of order (e.g. no state set)       */
+#define DGF_EUNSUPPORTED (-8) /* valid but unsupported size (e.g. smem)      */
+
+#define DGF_FP64 0
+#define DGF_FP32 1
+
+typedef struct dgf_forest dgf_forest;
+
+/* Forest description (Sec. 3.1-3.3).  Root blocks are hexahedra (3D) or
+ * quadrilaterals (2D) given by 2^d corner node ids in local lexicographic
+ * order (corner bit a = local coordinate a at +1).  Root faces are glued by
+ * shared corner ids or, failing that, by corner positions shifted by a sum
+ * c_1 t_1 + ... + c_k t_k of the periodic translations (c_i in {-1,0,1}). */
+typedef struct {
+  int32_t dim;        /* 2 or 3                                             */
+  int32_t n_seg;      /* cells per block edge: even, 2..16                  */
+  int32_t p;          /* polynomial degree 0..3                             */
+  int32_t precision;  /* DGF_FP64 or DGF_FP32                               */
+  int32_t device;     /* CUDA device ordinal; -1 = host-only forest that
+                         answers topology/geometry queries only             */
+  int32_t n_periodic; /* number of periodic translations, 0..3             */
+  double gamma;       /* ideal-gas ratio of Eq. (23), e.g. 1.4              */
+  double cfl;         /* CFL number of the time increment (Sec. 4.3)        */
+  double periodic[9]; /* n_periodic vectors of dim components, packed       */
+  int64_t n_nodes;
+  const double* nodes;           /* host, n_nodes*dim, copied               */
+  int64_t n_roots;
+  const int64_t* root_corners;   /* host, n_roots*2^dim, copied             */
+  const double* root_cell_nodes; /* host, nullable: n_roots*(n_seg+1)^dim*dim
+                                    cell nodes per root in local order; if
+                                    NULL they follow from Eq. (6)            */
+} dgf_forest_desc;
+
+/* Optional device allocator.  alloc returns NULL on failure; free is given
+ * the size and stream of the matching alloc. */
+typedef struct {
+  void* ctx;
+  void* (*alloc)(void* ctx, size_t bytes, void* stream);
+  void (*free)(void* ctx, void* ptr, size_t bytes, void* stream);
+} dgf_allocator;
+
+/* Thread-local message of the last failed call on this thread. */
+const char* dgf_last_error(void);
+
+/* Build the root forest (Sec. 3.1): validates the description, glues root
+ * faces, computes rotations, and (device >= 0) allocates device buffers.
+ * allocator may be NULL.  On success *out owns everything. */
+dgf_status dgf_forest_create(const dgf_forest_desc* desc, const dgf_allocator* allocator,
+                             dgf_forest** out);
+dgf_status dgf_forest_destroy(dgf_forest* f);
+
+/* Stream for all GPU work of this forest (a cudaStream_t, NULL = legacy). */
+dgf_status dgf_set_stream(dgf_forest* f, void* stream);
+
+/* Refinement (Sec. 3.1, 3.3, 3.4): refine the given leaves (ids in the
+ * current canonical order), then refine coarser leaves until every face
+ * joins leaves at most one level apart.  A state set before the call is
+ * carried over: new children by the split of Eqs. (11)-(12).  Leaf ids are
+ * renumbered afterwards. */
+dgf_status dgf_block_refine(dgf_forest* f, const int64_t* leaf_ids, int64_t n);
+/* Coarsen the parents of the given leaves (all 2^d children of each parent
+ * must be leaves).  DGF_EBALANCE (forest unchanged) if 2:1 balance would
+ * break.  A state is carried over by the combine of Eqs. (13)-(14). */
+dgf_status dgf_block_coarsen(dgf_forest* f, const int64_t* leaf_ids, int64_t n);
+
+/* Number of leaf blocks. */
+dgf_status dgf_leaf_count(const dgf_forest* f, int64_t* n_leaves);
+/* Integer leaf tables (host arrays sized by dgf_leaf_count = L):
+ *   root[L], level[L] (roots are level 1), pos[L*dim] (block coordinates at
+ *   its level in the root's frame), kind[L*2d], nbr[L*2d*4] (neighbour leaf
+ *   ids; for kind 2 entry s is the fine leaf on sub-face s = sum_j bit_j 2^j
+ *   over my tangential axes in increasing order; unused entries -1),
+ *   orient[L*2d].  Any pointer may be NULL. */
+dgf_status dgf_leaf_table(const dgf_forest* f, int32_t* root, int32_t* level, int32_t* pos,
+                          int32_t* kind, int64_t* nbr, int32_t* orient);
+/* Physical volume quadrature points, host [leaf][cell][q][dim] (FP64),
+ * q = sum_a q_a N^a over (p+1)-point Gauss-Legendre nodes. */
+dgf_status dgf_quad_points(const dgf_forest* f, double* xyz);
+
+/* Number of state values (leaves * nv * M * n^d). */
+dgf_status dgf_state_size(const dgf_forest* f, int64_t* n_values);
+/* Copy in / out the modal state (layout above; forest element type). */
+dgf_status dgf_set_state(dgf_forest* f, const void* src, int is_device);
+dgf_status dgf_get_state(dgf_forest* f, void* dst, int is_device);
+/* Set the state from FP64 point values [leaf][cell][q][var] at the volume
+ * quadrature points: the (p+1)-point L2 projection of Eq. (4)'s mass matrix,
+ * i.e. interpolation at the Gauss points. */
+dgf_status dgf_set_state_nodal(dgf_forest* f, const double* vals, int is_device);
+
+/* Standalone guard-cell fill (Sec. 3.5, Eqs. (15)-(17)) of the current state:
+ * writes modal guard cells [leaf][face][var][mode][t] (forest element type),
+ * t = sum_j g_j n^j over my tangential cell coordinates, in my frame. */
+dgf_status dgf_fill_guardcells(dgf_forest* f, void* guard, int is_device);
+/* L(U) = M^{-1} R of Eqs. (3)-(4) for the current state, modal layout. */
+dgf_status dgf_dg_residual(dgf_forest* f, void* dst, int is_device);
+
+/* One SSP-RK3 time increment (Sec. 2 last paragraph; Sec. 4.3): dt = CFL *
+ * min over cells and quadrature points of h / sum_i(|u_i| + c), clipped so
+ * that time does not pass t_end; three stages of guard fill + residual +
+ * Shu-Osher combination.  dt stays on the device; if dt_out is non-NULL the
+ * call synchronises and returns it. */
+dgf_status dgf_rk_step(dgf_forest* f, double t_end, double* dt_out);
+/* Current time (synchronises) / reset it. */
+dgf_status dgf_get_time(dgf_forest* f, double* t);
+dgf_status dgf_set_time(dgf_forest* f, double t);
+/* CFL time increment of the current state (synchronises). */
+dgf_status dgf_compute_dt(dgf_forest* f, double* dt);
+
+/* Conserved totals T_v = sum_cells sum_q w_q J_q u_v(q), FP64, fixed-order
+ * reduction; totals[nv] host (synchronises). */
+dgf_status dgf_conserved_totals(dgf_forest* f, double* totals);
+
+/* Device status word: 0 or DGF_ENONFINITE (synchronises); reset clears it. */
+dgf_status dgf_status_word(dgf_forest* f, int32_t* status, int reset);
+
+/* Kernel timing: when on, rk_step launches stage by stage (no graph) with
+ * CUDA events around every kernel; dgf_kernel_times synchronises and returns
+ * summed milliseconds and launch counts for the kernel classes
+ * 0 = dt, 1 = guard, 2 = stage, then resets the sums. */
+dgf_status dgf_set_timing(dgf_forest* f, int on);
+dgf_status dgf_kernel_times(dgf_forest* f, double* ms, int64_t* launches, int n_classes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGF_H */

@@ -270,26 +270,27 @@ class Solver:
             out[:, :, t] = _rotate(ops, Kchild, pi, sigma)
         return out
 
-    def fill_guardcells(self, U):
-        """G[leaf][face][var][mode][t], t = sum_j g_{t_j} n^j."""
+    def fill_guardcells(self, U, leaves=None):
+        """G[leaf][face][var][mode][t], t = sum_j g_{t_j} n^j (all leaves,
+        or only the listed ones; the others stay zero)."""
         d, n = self.d, self.n
         nl = len(self.leaves)
         G = np.zeros((nl, 2 * d, self.nv, self.ops.M, n ** (d - 1)))
-        for li in range(nl):
+        for li in (range(nl) if leaves is None else leaves):
             for f in range(2 * d):
                 G[li, f] = self.guard_face(U, li, f)
         return G
 
     # -------------------------------------------------------------- residual
-    def residual(self, U, G=None):
-        """L(U) = M^{-1} R per cell (Eqs. (3)-(4)); guard cells from Sec. 3.5."""
+    def residual(self, U, G=None, leaves=None):
+        """L(U) = M^{-1} R per cell (Eqs. (3)-(4)); guard cells from Sec. 3.5.
+        ``leaves`` restricts the evaluation to a subset (others stay zero)."""
         ops, d, n, nv = self.ops, self.d, self.n, self.nv
         if G is None:
-            G = self.fill_guardcells(U)
+            G = self.fill_guardcells(U, leaves)
         out = np.zeros_like(U)
-        cells = _cells(d, n)
         nc = n ** d
-        for li in range(len(self.leaves)):
+        for li in (range(len(self.leaves)) if leaves is None else leaves):
             K = np.transpose(U[li], (2, 0, 1))                      # (nc, nv, M)
             J, Ja = self.geo_vol[li]
             uq = np.einsum("qm,cvm->cqv", ops.Phi, K)

@@ -1,0 +1,1105 @@
+// C ABI of the block-forest DG library (declared in include/dgf.h).
+//
+// This layer owns the forest (host topology + device buffers), precomputes
+// the FP64 geometry (trilinear coefficients per cell, cell sizes) and the
+// FP64 combine operators of Sec. 3.4 for every finer-neighbour guard cell,
+// and enqueues the kernels of one SSP-RK3 time increment (Sec. 4.3):
+//   k_dt -> 3 x { k_guard (guard traces, Sec. 3.5) ; k_stage (residual +
+//   inverse mass + stage combination, CFL minimum on the last stage) },
+// captured once into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dgf.h"
+#include "forest_host.hpp"
+#include "launch.hpp"
+
+using namespace dgf;
+
+namespace {
+
+thread_local std::string g_err;
+
+dgf_status fail(dgf_status code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+struct DevScalars {
+  double t, dt, t_end;
+  unsigned long long lam_bits;  // min over cells of h / lambda, as double bits
+  int status;
+  int pad;
+};
+
+constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
+
+__global__ void k_dt(DevScalars* s, double cfl) {
+  const unsigned long long lb = s->lam_bits;
+  double dt = 0.0;
+  if (lb != kInfBits) {
+    dt = cfl * __longlong_as_double((long long)lb);
+    const double rem = s->t_end - s->t;
+    if (dt > rem) dt = rem;
+    if (!(dt > 0.0)) dt = 0.0;
+  } else {
+    s->status = -4;
+  }
+  s->dt = dt;
+  s->t = s->t + dt;
+  s->lam_bits = kInfBits;
+}
+
+__global__ void k_reset_lam(DevScalars* s) { s->lam_bits = kInfBits; }
+
+__global__ void k_dt_only(DevScalars* s, double cfl, double* out) {
+  const unsigned long long lb = s->lam_bits;
+  *out = lb == kInfBits ? 0.0 : cfl * __longlong_as_double((long long)lb);
+}
+
+// fixed-order reduction of nv arrays of length len (one CTA per variable)
+__global__ void k_reduce(const double* __restrict__ part, size_t len, double* out) {
+  __shared__ double red[1024];
+  const int v = blockIdx.x, tid = threadIdx.x;
+  double s = 0.0;
+  for (size_t i = tid; i < len; i += blockDim.x) s += part[(size_t)v * len + i];
+  red[tid] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (tid < w) red[tid] += red[tid + w];
+    __syncthreads();
+  }
+  if (tid == 0) out[v] = red[0];
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (dev >= 0) {
+      cudaGetDevice(&prev);
+      if (prev != dev) cudaSetDevice(dev);
+      else prev = -1;
+    }
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct dgf_forest {
+  Forest host;
+  int precision = DGF_FP64;
+  int device = -1;
+  double gamma = 1.4, cfl = 0.1;
+  dgf_allocator alloc{};
+  bool has_alloc = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t esize = 8;
+  int d = 0, n = 0, p = 0, N = 0, nv = 0, M = 0, nc = 0, NG = 0, nt = 0, NFP = 0;
+  int64_t nL = 0;
+  RtTables tab{};
+  Basis1D basis;
+
+  struct Buf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+  };
+  Buf U[3], geo, geo64, hcell, gtr, gmod, cop, kind, nbr, orient, qbits, copoff, part, scal, tot,
+      dtout, nodal;
+  bool have_state = false;
+  bool graph_valid = false;
+  cudaGraphExec_t graph = nullptr;
+  double t_end_dev = NAN;
+  int zchunk = 0;
+  bool timing = false;
+  struct TEv {
+    cudaEvent_t a, b;
+    int cls;
+  };
+  std::vector<TEv> ev;
+  double ms[3] = {0, 0, 0};
+  int64_t launches[3] = {0, 0, 0};
+};
+
+namespace {
+
+void* dev_alloc(dgf_forest* f, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (f->has_alloc) return f->alloc.alloc(f->alloc.ctx, bytes, (void*)f->stream);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  return p;
+}
+
+void dev_free(dgf_forest* f, dgf_forest::Buf& b) {
+  if (!b.ptr) return;
+  if (f->has_alloc) f->alloc.free(f->alloc.ctx, b.ptr, b.bytes, (void*)f->stream);
+  else cudaFree(b.ptr);
+  b.ptr = nullptr;
+  b.bytes = 0;
+}
+
+bool ensure(dgf_forest* f, dgf_forest::Buf& b, size_t bytes) {
+  if (b.ptr && b.bytes >= bytes) return true;
+  dev_free(f, b);
+  b.ptr = dev_alloc(f, bytes);
+  b.bytes = b.ptr ? bytes : 0;
+  return b.ptr != nullptr;
+}
+
+dgf_status cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return DGF_OK;
+  if (e == cudaErrorInvalidConfiguration)
+    return fail(DGF_EUNSUPPORTED, std::string(what) + ": shared-memory footprint too large for "
+                                                      "this (dim, p, n_seg, precision)");
+  return fail(DGF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int pack_orient(const Orient& o, int d) {
+  int v = 0;
+  for (int a = 0; a < d; ++a) {
+    v |= o.pi[a] << (2 * a);
+    if (o.sg[a] < 0) v |= 1 << (6 + a);
+  }
+  return v;
+}
+
+template <typename T>
+dgf_status upload(dgf_forest* f, dgf_forest::Buf& b, const std::vector<T>& v) {
+  if (!ensure(f, b, sizeof(T) * std::max<size_t>(v.size(), 1))) return fail(DGF_ENOMEM, "device allocation failed");
+  if (!v.empty())
+    return cuda_check(cudaMemcpyAsync(b.ptr, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, f->stream),
+                      "upload");
+  return DGF_OK;
+}
+
+template <typename T>
+std::vector<T> convert(const std::vector<double>& v) {
+  return std::vector<T>(v.begin(), v.end());
+}
+
+double phi(const Basis1D& B, int d, int m, const double* xi) {
+  double r = 1.0;
+  for (int a = 0; a < d; ++a) {
+    r *= legendre(m % B.N, xi[a]);
+    m /= B.N;
+  }
+  return r;
+}
+
+// Cholesky solve of an SPD system with several right-hand sides (FP64).
+bool chol_solve(int M, std::vector<double>& A, std::vector<double>& B, int nrhs) {
+  for (int j = 0; j < M; ++j) {
+    double s = A[j * M + j];
+    for (int k = 0; k < j; ++k) s -= A[j * M + k] * A[j * M + k];
+    if (!(s > 0)) return false;
+    A[j * M + j] = std::sqrt(s);
+    for (int i = j + 1; i < M; ++i) {
+      double t = A[i * M + j];
+      for (int k = 0; k < j; ++k) t -= A[i * M + k] * A[j * M + k];
+      A[i * M + j] = t / A[j * M + j];
+    }
+  }
+  for (int r = 0; r < nrhs; ++r) {
+    for (int i = 0; i < M; ++i) {
+      double t = B[i * nrhs + r];
+      for (int k = 0; k < i; ++k) t -= A[i * M + k] * B[k * nrhs + r];
+      B[i * nrhs + r] = t / A[i * M + i];
+    }
+    for (int i = M - 1; i >= 0; --i) {
+      double t = B[i * nrhs + r];
+      for (int k = i + 1; k < M; ++k) t -= A[k * M + i] * B[k * nrhs + r];
+      B[i * nrhs + r] = t / A[i * M + i];
+    }
+  }
+  return true;
+}
+
+// Build every leaf-dependent device array: integer tables, FP64 geometry,
+// cell sizes, combine operators, state and scratch buffers.
+dgf_status build_device(dgf_forest* f) {
+  Forest& F = f->host;
+  const int d = f->d, n = f->n, nf = 2 * d, M = f->M, nc = f->nc, NG = f->NG, N = f->N;
+  const int64_t L = F.n_leaves();
+  if (f->device >= 0 && f->stream) {
+    DeviceGuard dg(f->device);
+    cudaStreamSynchronize(f->stream);  // buffers may be freed or reused below
+  }
+  f->nL = L;
+  Forest::Tables T = F.tables();
+
+  std::vector<int> kind(L * nf), nbr(L * nf * 4), orient(L * nf), qbits(L), copoff(L * nf, -1);
+  for (int64_t i = 0; i < L * nf; ++i) {
+    kind[i] = T.kind[i];
+    orient[i] = pack_orient(orient_from_code(T.orient[i], d), d);
+    for (int s = 0; s < 4; ++s) nbr[i * 4 + s] = (int)T.nbr[i * 4 + s];
+  }
+  for (int64_t i = 0; i < L; ++i) {
+    int q = 0;
+    for (int a = 0; a < d; ++a) q |= (T.pos[i * d + a] & 1) << a;
+    qbits[i] = q;
+  }
+
+  // geometry: per-cell trilinear coefficients (c >= 1) and sizes h
+  std::vector<std::vector<double>> coef(L);
+  std::vector<double> geo64((size_t)L * NG * nc), hcell((size_t)L * nc);
+  const Basis1D& B = f->basis;
+  for (int64_t i = 0; i < L; ++i) {
+    F.cell_coefficients(F.leaves[i], coef[i]);
+    for (int g = 0; g < NG; ++g)
+      for (int c = 0; c < nc; ++c) geo64[((size_t)i * NG + g) * nc + c] = coef[i][(size_t)(d + g) * nc + c];
+    for (int c = 0; c < nc; ++c) {
+      double cc[8 * 3];
+      for (int k = 0; k < (1 << d) * d; ++k) cc[k] = coef[i][(size_t)k * nc + c];
+      double vol = 0.0;
+      for (int q = 0; q < M; ++q) {
+        double xi[3], wq = 1.0;
+        int r = q;
+        for (int a = 0; a < d; ++a) {
+          xi[a] = B.x[r % N];
+          wq *= B.w[r % N];
+          r /= N;
+        }
+        double A[9], Ja[9];
+        eval_map(d, cc, xi, nullptr, A);
+        vol += wq * det_and_cofactor(d, A, Ja);
+      }
+      hcell[(size_t)i * nc + c] = std::pow(vol, 1.0 / d);
+    }
+  }
+
+  // combine operators for every finer-neighbour guard cell (Eqs. (13)-(14),
+  // J-weighted, integrals by each child's Gauss rule), rotated into my frame
+  const int nt = f->nt;
+  std::vector<double> cop;
+  int64_t nops = 0;
+  const int KC = (1 << d) * M;
+  for (int64_t i = 0; i < L; ++i)
+    for (int fc = 0; fc < nf; ++fc)
+      if (kind[i * nf + fc] == kFiner) {
+        copoff[i * nf + fc] = (int)nops;
+        nops += nt;
+      }
+  cop.assign((size_t)nops * M * KC, 0.0);
+  for (int64_t i = 0; i < L; ++i) {
+    for (int fc = 0; fc < nf; ++fc) {
+      if (kind[i * nf + fc] != kFiner) continue;
+      const Orient o = orient_from_code(T.orient[i * nf + fc], d);
+      const int a = fc >> 1, s = fc & 1;
+      const int b2 = o.pi[a];
+      const int s2 = o.sg[a] > 0 ? 1 - s : s;
+      for (int t = 0; t < nt; ++t) {
+        int g[3] = {0, 0, 0}, j = 0;
+        for (int ax = 0; ax < d; ++ax) {
+          if (ax == a) continue;
+          g[ax] = j == 0 ? t % n : t / n;
+          ++j;
+        }
+        int h[3] = {0, 0, 0};
+        for (int ax = 0; ax < d; ++ax) {
+          if (ax == a) continue;
+          h[o.pi[ax]] = o.sg[ax] > 0 ? g[ax] : n - 1 - g[ax];
+        }
+        h[b2] = s2 == 0 ? 0 : n - 1;
+        int sub = 0;
+        j = 0;
+        for (int ax = 0; ax < d; ++ax) {
+          if (ax == a) continue;
+          if (g[ax] >= n / 2) sub |= 1 << j;
+          ++j;
+        }
+        const int64_t fine = T.nbr[(i * nf + fc) * 4 + sub];
+        int cN[3] = {0, 0, 0};
+        for (int ax = 0; ax < d; ++ax) cN[ax] = (2 * h[ax]) / n;
+        std::vector<double> MP(M * M, 0.0), RHS((size_t)M * KC, 0.0);
+        for (int e = 0; e < (1 << d); ++e) {
+          int cell = 0, st = 1;
+          for (int ax = 0; ax < d; ++ax) {
+            cell += (2 * h[ax] + ((e >> ax) & 1) - cN[ax] * n) * st;
+            st *= n;
+          }
+          double cc[8 * 3];
+          for (int k = 0; k < (1 << d) * d; ++k) cc[k] = coef[fine][(size_t)k * nc + cell];
+          for (int q = 0; q < M; ++q) {
+            double xi[3], xp[3], wq = 1.0;
+            int r = q;
+            for (int ax = 0; ax < d; ++ax) {
+              xi[ax] = B.x[r % N];
+              wq *= B.w[r % N];
+              xp[ax] = 0.5 * (xi[ax] + (((e >> ax) & 1) ? 1.0 : -1.0));
+              r /= N;
+            }
+            double A[9], Ja[9];
+            eval_map(d, cc, xi, nullptr, A);
+            const double wj = wq * det_and_cofactor(d, A, Ja);
+            double pp[64], pc[64];
+            for (int m = 0; m < M; ++m) {
+              pp[m] = phi(B, d, m, xp);
+              pc[m] = phi(B, d, m, xi);
+            }
+            for (int m = 0; m < M; ++m) {
+              for (int m2 = 0; m2 < M; ++m2) MP[m * M + m2] += wj * pp[m] * pp[m2];
+              for (int k = 0; k < M; ++k) RHS[(size_t)m * KC + e * M + k] += wj * pp[m] * pc[k];
+            }
+          }
+        }
+        if (!chol_solve(M, MP, RHS, KC)) return fail(DGF_EINVAL, "singular combine mass matrix");
+        // rotate rows into my frame: my mode m <- source mode m', sign
+        double* dst = &cop[((size_t)copoff[i * nf + fc] + t) * M * KC];
+        for (int m = 0; m < M; ++m) {
+          int ms = 0, rem = m;
+          double sg = 1.0;
+          for (int ax = 0; ax < d; ++ax) {
+            const int ka = rem % N;
+            rem /= N;
+            int st = 1;
+            for (int u = 0; u < o.pi[ax]; ++u) st *= N;
+            ms += ka * st;
+            if (o.sg[ax] < 0 && (ka & 1)) sg = -sg;
+          }
+          for (int k = 0; k < KC; ++k) dst[(size_t)m * KC + k] = sg * RHS[(size_t)ms * KC + k];
+        }
+      }
+    }
+  }
+
+  if (f->device < 0) return DGF_OK;
+  DeviceGuard dg(f->device);
+  dgf_status st;
+  if ((st = upload(f, f->kind, kind)) || (st = upload(f, f->nbr, nbr)) || (st = upload(f, f->orient, orient)) ||
+      (st = upload(f, f->qbits, qbits)) || (st = upload(f, f->copoff, copoff)) || (st = upload(f, f->geo64, geo64)))
+    return st;
+  if (f->precision == DGF_FP64) {
+    if ((st = upload(f, f->geo, geo64)) || (st = upload(f, f->hcell, hcell)) || (st = upload(f, f->cop, cop)))
+      return st;
+  } else {
+    if ((st = upload(f, f->geo, convert<float>(geo64))) || (st = upload(f, f->hcell, convert<float>(hcell))) ||
+        (st = upload(f, f->cop, convert<float>(cop))))
+      return st;
+  }
+  const size_t sbytes = (size_t)L * f->nv * M * nc * f->esize;
+  for (int k = 0; k < 3; ++k)
+    if (!ensure(f, f->U[k], sbytes)) return fail(DGF_ENOMEM, "state allocation failed");
+  if (!ensure(f, f->gtr, (size_t)L * nf * f->nv * f->NFP * nt * f->esize) ||
+      !ensure(f, f->part, (size_t)L * nc * f->nv * sizeof(double)))
+    return fail(DGF_ENOMEM, "scratch allocation failed");
+  // parallel split of a block into z-chunks when the forest is small
+  if (d == 3) {
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device);
+    int chunks = (int)std::min<int64_t>(n, std::max<int64_t>(1, (2 * sms + L - 1) / L));
+    f->zchunk = (n + chunks - 1) / chunks;
+    if (const char* zc = getenv("DGF_ZCHUNK")) f->zchunk = std::max(1, std::min(n, atoi(zc)));
+  } else {
+    f->zchunk = 1;
+  }
+  if (f->graph) {
+    cudaGraphExecDestroy(f->graph);
+    f->graph = nullptr;
+  }
+  f->graph_valid = false;
+  return DGF_OK;
+}
+
+RtStage stage_args(dgf_forest* f, int src, int dst, double ca, double cb, int mode, int last) {
+  RtStage r{};
+  r.p = f->p;
+  r.nL = (int)f->nL;
+  r.n = f->n;
+  r.zchunk = f->zchunk;
+  r.threads = 256;
+  r.U = f->U[src].ptr;
+  r.Un = f->U[0].ptr;
+  r.Uout = f->U[dst].ptr;
+  r.geo = f->geo.ptr;
+  r.gtr = f->gtr.ptr;
+  r.hcell = f->hcell.ptr;
+  r.dtp = &((DevScalars*)f->scal.ptr)->dt;
+  r.lam_bits = &((DevScalars*)f->scal.ptr)->lam_bits;
+  r.status = &((DevScalars*)f->scal.ptr)->status;
+  r.ca = ca;
+  r.cb = cb;
+  r.gamma = f->gamma;
+  r.mode = mode;
+  r.last = last;
+  r.T = f->tab;
+  return r;
+}
+
+RtGuard guard_args(dgf_forest* f, int src, void* out, int mode) {
+  RtGuard r{};
+  r.p = f->p;
+  r.nL = (int)f->nL;
+  r.n = f->n;
+  r.mode = mode;
+  r.U = f->U[src].ptr;
+  r.out = out;
+  r.kind = (const int*)f->kind.ptr;
+  r.nbr = (const int*)f->nbr.ptr;
+  r.orient = (const int*)f->orient.ptr;
+  r.qbits = (const int*)f->qbits.ptr;
+  r.copoff = (const int*)f->copoff.ptr;
+  r.cop = f->cop.ptr;
+  r.T = f->tab;
+  return r;
+}
+
+RtMisc misc_args(dgf_forest* f, int src) {
+  RtMisc r{};
+  r.p = f->p;
+  r.nL = (int)f->nL;
+  r.n = f->n;
+  r.U = f->U[src].ptr;
+  r.Uout = f->U[src].ptr;
+  r.hcell = f->hcell.ptr;
+  r.geo64 = (const double*)f->geo64.ptr;
+  r.part = (double*)f->part.ptr;
+  r.gamma = f->gamma;
+  r.lam_bits = &((DevScalars*)f->scal.ptr)->lam_bits;
+  r.status = &((DevScalars*)f->scal.ptr)->status;
+  r.T = f->tab;
+  return r;
+}
+
+cudaError_t do_stage(dgf_forest* f, const RtStage& r) {
+  if (f->d == 2) return f->precision == DGF_FP64 ? launch_stage<2, double>(r, f->stream) : launch_stage<2, float>(r, f->stream);
+  return f->precision == DGF_FP64 ? launch_stage<3, double>(r, f->stream) : launch_stage<3, float>(r, f->stream);
+}
+cudaError_t do_guard(dgf_forest* f, const RtGuard& r) {
+  if (f->d == 2) return f->precision == DGF_FP64 ? launch_guard<2, double>(r, f->stream) : launch_guard<2, float>(r, f->stream);
+  return f->precision == DGF_FP64 ? launch_guard<3, double>(r, f->stream) : launch_guard<3, float>(r, f->stream);
+}
+cudaError_t do_cfl(dgf_forest* f, const RtMisc& r) {
+  if (f->d == 2) return f->precision == DGF_FP64 ? launch_cfl<2, double>(r, f->stream) : launch_cfl<2, float>(r, f->stream);
+  return f->precision == DGF_FP64 ? launch_cfl<3, double>(r, f->stream) : launch_cfl<3, float>(r, f->stream);
+}
+cudaError_t do_project(dgf_forest* f, const RtMisc& r) {
+  if (f->d == 2) return f->precision == DGF_FP64 ? launch_project<2, double>(r, f->stream) : launch_project<2, float>(r, f->stream);
+  return f->precision == DGF_FP64 ? launch_project<3, double>(r, f->stream) : launch_project<3, float>(r, f->stream);
+}
+cudaError_t do_totals(dgf_forest* f, const RtMisc& r) {
+  if (f->d == 2) return f->precision == DGF_FP64 ? launch_totals<2, double>(r, f->stream) : launch_totals<2, float>(r, f->stream);
+  return f->precision == DGF_FP64 ? launch_totals<3, double>(r, f->stream) : launch_totals<3, float>(r, f->stream);
+}
+
+dgf_status require_device(dgf_forest* f) {
+  if (!f) return fail(DGF_EINVAL, "null forest");
+  if (f->device < 0) return fail(DGF_ESTATE, "host-only forest has no device state");
+  return DGF_OK;
+}
+
+dgf_status init_lambda(dgf_forest* f) {
+  DevScalars* s = (DevScalars*)f->scal.ptr;
+  k_reset_lam<<<1, 1, 0, f->stream>>>(s);
+  dgf_status st = cuda_check(cudaGetLastError(), "reset");
+  if (st) return st;
+  return cuda_check(do_cfl(f, misc_args(f, 0)), "cfl");
+}
+
+// enqueue one time increment; timing mode records events around kernels
+dgf_status enqueue_step(dgf_forest* f) {
+  DevScalars* s = (DevScalars*)f->scal.ptr;
+  auto rec = [&](int cls, auto&& launch) -> dgf_status {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (f->timing) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, f->stream);
+    }
+    cudaError_t e = launch();
+    if (f->timing) {
+      cudaEventRecord(b, f->stream);
+      f->ev.push_back({a, b, cls});
+      f->launches[cls] += 1;
+    }
+    return cuda_check(e, cls == 0 ? "dt" : (cls == 1 ? "guard" : "stage"));
+  };
+  dgf_status st = rec(0, [&]() {
+    k_dt<<<1, 1, 0, f->stream>>>(s, f->cfl);
+    return cudaGetLastError();
+  });
+  if (st) return st;
+  // Shu-Osher SSP-RK3: (src, dst, a, b): dst = a U^n + b (src + dt L(src))
+  const int src[3] = {0, 1, 2}, dst[3] = {1, 2, 0};
+  const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
+  for (int k = 0; k < 3; ++k) {
+    if ((st = rec(1, [&]() { return do_guard(f, guard_args(f, src[k], f->gtr.ptr, 1)); }))) return st;
+    if ((st = rec(2, [&]() { return do_stage(f, stage_args(f, src[k], dst[k], ca[k], cb[k], 0, k == 2)); })))
+      return st;
+  }
+  return DGF_OK;
+}
+
+dgf_status set_t_end(dgf_forest* f, double t_end) {
+  if (f->t_end_dev == t_end) return DGF_OK;
+  DevScalars* s = (DevScalars*)f->scal.ptr;
+  f->t_end_dev = t_end;
+  return cuda_check(cudaMemcpyAsync(&s->t_end, &f->t_end_dev, sizeof(double), cudaMemcpyHostToDevice, f->stream),
+                    "t_end");
+}
+
+dgf_status copy_state(dgf_forest* f, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+  dgf_status st = cuda_check(cudaMemcpyAsync(dst, src, bytes, kind, f->stream), "state copy");
+  if (st) return st;
+  return cuda_check(cudaStreamSynchronize(f->stream), "sync");
+}
+
+}  // namespace
+
+// =================================================================== ABI
+extern "C" {
+
+const char* dgf_last_error(void) { return g_err.c_str(); }
+
+dgf_status dgf_forest_create(const dgf_forest_desc* desc, const dgf_allocator* allocator, dgf_forest** out) {
+  if (!desc || !out) return fail(DGF_EINVAL, "null argument");
+  *out = nullptr;
+  if (desc->precision != DGF_FP64 && desc->precision != DGF_FP32) return fail(DGF_EINVAL, "bad precision");
+  if (!(desc->gamma > 1.0) || !(desc->cfl > 0.0)) return fail(DGF_EINVAL, "gamma must be > 1 and cfl > 0");
+  dgf_forest* f = new (std::nothrow) dgf_forest();
+  if (!f) return fail(DGF_ENOMEM, "host allocation failed");
+  if (!f->host.init(desc->dim, desc->n_seg, desc->p, desc->n_nodes, desc->nodes, desc->n_roots,
+                    desc->root_corners, desc->root_cell_nodes, desc->n_periodic, desc->periodic)) {
+    std::string e = f->host.error;
+    delete f;
+    return fail(DGF_EINVAL, e);
+  }
+  f->precision = desc->precision;
+  f->device = desc->device;
+  f->gamma = desc->gamma;
+  f->cfl = desc->cfl;
+  f->esize = desc->precision == DGF_FP64 ? 8 : 4;
+  f->d = desc->dim;
+  f->n = desc->n_seg;
+  f->p = desc->p;
+  f->N = f->p + 1;
+  f->nv = f->d + 2;
+  f->M = (int)std::pow(f->N, f->d);
+  f->nc = (int)std::pow(f->n, f->d);
+  f->NG = ((1 << f->d) - 1) * f->d;
+  f->nt = (int)std::pow(f->n, f->d - 1);
+  f->NFP = (int)std::pow(f->N, f->d - 1);
+  f->basis.build(f->N);
+  RtTables& T = f->tab;
+  T.N = f->N;
+  for (int i = 0; i < f->N; ++i) {
+    T.x[i] = f->basis.x[i];
+    T.w[i] = f->basis.w[i];
+    T.lp[i] = f->basis.lp[i];
+    T.lm[i] = f->basis.lm[i];
+  }
+  for (int i = 0; i < f->N * f->N; ++i) {
+    T.V[i] = f->basis.V[i];
+    T.Vi[i] = f->basis.Vi[i];
+    T.Sh[i] = f->basis.Sh[i];
+    T.Sm[i] = f->basis.Sm[i];
+    T.Sp[i] = f->basis.Sp[i];
+  }
+  if (allocator) {
+    f->alloc = *allocator;
+    f->has_alloc = allocator->alloc && allocator->free;
+  }
+  if (f->device >= 0) {
+    DeviceGuard dg(f->device);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || f->device >= ndev) {
+      delete f;
+      return fail(DGF_ECUDA, "no such CUDA device");
+    }
+    if (cudaStreamCreateWithFlags(&f->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete f;
+      return fail(DGF_ECUDA, "stream creation failed");
+    }
+    f->own_stream = true;
+    if (!ensure(f, f->scal, sizeof(DevScalars)) || !ensure(f, f->tot, 8 * sizeof(double)) ||
+        !ensure(f, f->dtout, sizeof(double))) {
+      dgf_forest_destroy(f);
+      return fail(DGF_ENOMEM, "device allocation failed");
+    }
+    DevScalars s0{};
+    s0.t_end = INFINITY;
+    s0.lam_bits = kInfBits;
+    f->t_end_dev = INFINITY;
+    cudaMemcpy(f->scal.ptr, &s0, sizeof(s0), cudaMemcpyHostToDevice);
+  }
+  dgf_status st = build_device(f);
+  if (st) {
+    std::string e = g_err;
+    dgf_forest_destroy(f);
+    return fail(st, e);
+  }
+  if (f->device >= 0) {
+    DeviceGuard dg(f->device);
+    if ((st = cuda_check(cudaStreamSynchronize(f->stream), "create"))) {
+      dgf_forest_destroy(f);
+      return st;
+    }
+  }
+  *out = f;
+  return DGF_OK;
+}
+
+dgf_status dgf_forest_destroy(dgf_forest* f) {
+  if (!f) return DGF_OK;
+  if (f->device >= 0) {
+    DeviceGuard dg(f->device);
+    cudaStreamSynchronize(f->stream);
+    if (f->graph) cudaGraphExecDestroy(f->graph);
+    for (auto& e : f->ev) {
+      cudaEventDestroy(e.a);
+      cudaEventDestroy(e.b);
+    }
+    dgf_forest::Buf* bufs[] = {&f->U[0], &f->U[1], &f->U[2], &f->geo, &f->geo64, &f->hcell, &f->gtr,
+                               &f->gmod, &f->cop, &f->kind, &f->nbr, &f->orient, &f->qbits, &f->copoff,
+                               &f->part, &f->scal, &f->tot, &f->dtout, &f->nodal};
+    for (auto* b : bufs) dev_free(f, *b);
+    if (f->own_stream && f->stream) cudaStreamDestroy(f->stream);
+  }
+  delete f;
+  return DGF_OK;
+}
+
+dgf_status dgf_set_stream(dgf_forest* f, void* stream) {
+  if (dgf_status st = require_device(f)) return st;
+  DeviceGuard dg(f->device);
+  cudaStreamSynchronize(f->stream);
+  if (f->own_stream) cudaStreamDestroy(f->stream);
+  f->own_stream = false;
+  f->stream = (cudaStream_t)stream;
+  if (f->graph) cudaGraphExecDestroy(f->graph);
+  f->graph = nullptr;
+  f->graph_valid = false;
+  return DGF_OK;
+}
+
+static dgf_status regrid(dgf_forest* f, const std::vector<uint64_t>& old_leaves);
+
+dgf_status dgf_block_refine(dgf_forest* f, const int64_t* ids, int64_t n) {
+  if (!f || (n > 0 && !ids)) return fail(DGF_EINVAL, "null argument");
+  std::vector<uint64_t> keys;
+  for (int64_t i = 0; i < n; ++i) {
+    if (ids[i] < 0 || ids[i] >= f->host.n_leaves()) return fail(DGF_EINVAL, "leaf id out of range");
+    keys.push_back(f->host.leaves[ids[i]]);
+  }
+  std::sort(keys.begin(), keys.end());
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+  std::vector<uint64_t> old = f->host.leaves;
+  auto saved = f->host.tree;
+  if (!f->host.refine(keys)) {
+    f->host.tree = saved;
+    f->host.order_leaves();
+    return fail(DGF_EINVAL, f->host.error);
+  }
+  return regrid(f, old);
+}
+
+dgf_status dgf_block_coarsen(dgf_forest* f, const int64_t* ids, int64_t n) {
+  if (!f || (n > 0 && !ids)) return fail(DGF_EINVAL, "null argument");
+  std::vector<uint64_t> parents;
+  for (int64_t i = 0; i < n; ++i) {
+    if (ids[i] < 0 || ids[i] >= f->host.n_leaves()) return fail(DGF_EINVAL, "leaf id out of range");
+    int64_t r;
+    int lev, pos[3];
+    Forest::unkey(f->host.leaves[ids[i]], &r, &lev, pos);
+    if (lev <= 1) return fail(DGF_EINVAL, "a root block has no parent");
+    int pp[3] = {pos[0] >> 1, pos[1] >> 1, pos[2] >> 1};
+    parents.push_back(Forest::key(r, lev - 1, pp));
+  }
+  std::sort(parents.begin(), parents.end());
+  parents.erase(std::unique(parents.begin(), parents.end()), parents.end());
+  std::vector<uint64_t> old = f->host.leaves;
+  bool viol = false;
+  if (!f->host.coarsen(parents, &viol)) return fail(DGF_EBALANCE, f->host.error);
+  return regrid(f, old);
+}
+
+dgf_status dgf_leaf_count(const dgf_forest* f, int64_t* n) {
+  if (!f || !n) return fail(DGF_EINVAL, "null argument");
+  *n = f->host.n_leaves();
+  return DGF_OK;
+}
+
+dgf_status dgf_leaf_table(const dgf_forest* f, int32_t* root, int32_t* level, int32_t* pos, int32_t* kind,
+                          int64_t* nbr, int32_t* orient) {
+  if (!f) return fail(DGF_EINVAL, "null forest");
+  Forest::Tables T = f->host.tables();
+  if (root) std::memcpy(root, T.root.data(), T.root.size() * sizeof(int32_t));
+  if (level) std::memcpy(level, T.level.data(), T.level.size() * sizeof(int32_t));
+  if (pos) std::memcpy(pos, T.pos.data(), T.pos.size() * sizeof(int32_t));
+  if (kind) std::memcpy(kind, T.kind.data(), T.kind.size() * sizeof(int32_t));
+  if (nbr) std::memcpy(nbr, T.nbr.data(), T.nbr.size() * sizeof(int64_t));
+  if (orient) std::memcpy(orient, T.orient.data(), T.orient.size() * sizeof(int32_t));
+  return DGF_OK;
+}
+
+dgf_status dgf_quad_points(const dgf_forest* fc, double* xyz) {
+  if (!fc || !xyz) return fail(DGF_EINVAL, "null argument");
+  dgf_forest* f = const_cast<dgf_forest*>(fc);
+  const int d = f->d, M = f->M, nc = f->nc, N = f->N;
+  std::vector<double> coef;
+  for (int64_t i = 0; i < f->host.n_leaves(); ++i) {
+    f->host.cell_coefficients(f->host.leaves[i], coef);
+    for (int c = 0; c < nc; ++c) {
+      double cc[8 * 3];
+      for (int k = 0; k < (1 << d) * d; ++k) cc[k] = coef[(size_t)k * nc + c];
+      for (int q = 0; q < M; ++q) {
+        double xi[3], A[9];
+        int r = q;
+        for (int a = 0; a < d; ++a) {
+          xi[a] = f->basis.x[r % N];
+          r /= N;
+        }
+        eval_map(d, cc, xi, &xyz[(((size_t)i * nc + c) * M + q) * d], A);
+      }
+    }
+  }
+  return DGF_OK;
+}
+
+dgf_status dgf_state_size(const dgf_forest* f, int64_t* n) {
+  if (!f || !n) return fail(DGF_EINVAL, "null argument");
+  *n = f->host.n_leaves() * f->nv * f->M * f->nc;
+  return DGF_OK;
+}
+
+dgf_status dgf_set_state(dgf_forest* f, const void* src, int is_device) {
+  if (dgf_status st = require_device(f)) return st;
+  if (!src) return fail(DGF_EINVAL, "null source");
+  DeviceGuard dg(f->device);
+  const size_t bytes = (size_t)f->nL * f->nv * f->M * f->nc * f->esize;
+  dgf_status st = cuda_check(cudaMemcpyAsync(f->U[0].ptr, src, bytes,
+                                             is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                             f->stream),
+                             "set_state");
+  if (st) return st;
+  f->have_state = true;
+  return init_lambda(f);
+}
+
+dgf_status dgf_get_state(dgf_forest* f, void* dst, int is_device) {
+  if (dgf_status st = require_device(f)) return st;
+  if (!dst) return fail(DGF_EINVAL, "null destination");
+  if (!f->have_state) return fail(DGF_ESTATE, "no state set");
+  DeviceGuard dg(f->device);
+  const size_t bytes = (size_t)f->nL * f->nv * f->M * f->nc * f->esize;
+  return copy_state(f, dst, f->U[0].ptr, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+}
+
+dgf_status dgf_set_state_nodal(dgf_forest* f, const double* vals, int is_device) {
+  if (dgf_status st = require_device(f)) return st;
+  if (!vals) return fail(DGF_EINVAL, "null source");
+  DeviceGuard dg(f->device);
+  const size_t bytes = (size_t)f->nL * f->nc * f->M * f->nv * sizeof(double);
+  const double* src = vals;
+  dgf_status st;
+  if (!is_device) {
+    if (!ensure(f, f->nodal, bytes)) return fail(DGF_ENOMEM, "scratch allocation failed");
+    if ((st = cuda_check(cudaMemcpyAsync(f->nodal.ptr, vals, bytes, cudaMemcpyHostToDevice, f->stream), "copy")))
+      return st;
+    src = (const double*)f->nodal.ptr;
+  }
+  RtMisc r = misc_args(f, 0);
+  r.vals = src;
+  if ((st = cuda_check(do_project(f, r), "project"))) return st;
+  f->have_state = true;
+  if ((st = init_lambda(f))) return st;
+  return cuda_check(cudaStreamSynchronize(f->stream), "sync");
+}
+
+dgf_status dgf_fill_guardcells(dgf_forest* f, void* guard, int is_device) {
+  if (dgf_status st = require_device(f)) return st;
+  if (!guard) return fail(DGF_EINVAL, "null destination");
+  if (!f->have_state) return fail(DGF_ESTATE, "no state set");
+  DeviceGuard dg(f->device);
+  const size_t bytes = (size_t)f->nL * 2 * f->d * f->nv * f->M * f->nt * f->esize;
+  if (!ensure(f, f->gmod, bytes)) return fail(DGF_ENOMEM, "guard allocation failed");
+  dgf_status st = cuda_check(do_guard(f, guard_args(f, 0, f->gmod.ptr, 0)), "guard");
+  if (st) return st;
+  return copy_state(f, guard, f->gmod.ptr, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+}
+
+dgf_status dgf_dg_residual(dgf_forest* f, void* dst, int is_device) {
+  if (dgf_status st = require_device(f)) return st;
+  if (!dst) return fail(DGF_EINVAL, "null destination");
+  if (!f->have_state) return fail(DGF_ESTATE, "no state set");
+  DeviceGuard dg(f->device);
+  dgf_status st = cuda_check(do_guard(f, guard_args(f, 0, f->gtr.ptr, 1)), "guard");
+  if (st) return st;
+  if ((st = cuda_check(do_stage(f, stage_args(f, 0, 1, 0.0, 1.0, 1, 0)), "stage"))) return st;
+  const size_t bytes = (size_t)f->nL * f->nv * f->M * f->nc * f->esize;
+  return copy_state(f, dst, f->U[1].ptr, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+}
+
+dgf_status dgf_rk_step(dgf_forest* f, double t_end, double* dt_out) {
+  if (dgf_status st = require_device(f)) return st;
+  if (!f->have_state) return fail(DGF_ESTATE, "no state set");
+  DeviceGuard dg(f->device);
+  dgf_status st = set_t_end(f, t_end);
+  if (st) return st;
+  if (f->timing) {
+    if ((st = enqueue_step(f))) return st;
+  } else {
+    if (!f->graph_valid) {
+      cudaGraph_t g = nullptr;
+      if ((st = cuda_check(cudaStreamBeginCapture(f->stream, cudaStreamCaptureModeThreadLocal), "capture")))
+        return st;
+      dgf_status est = enqueue_step(f);
+      cudaError_t e = cudaStreamEndCapture(f->stream, &g);
+      if (est) {
+        if (g) cudaGraphDestroy(g);
+        return est;
+      }
+      if ((st = cuda_check(e, "end capture"))) return st;
+      e = cudaGraphInstantiate(&f->graph, g, 0);
+      cudaGraphDestroy(g);
+      if ((st = cuda_check(e, "instantiate"))) return st;
+      f->graph_valid = true;
+    }
+    if ((st = cuda_check(cudaGraphLaunch(f->graph, f->stream), "graph launch"))) return st;
+  }
+  if (dt_out) {
+    DevScalars* s = (DevScalars*)f->scal.ptr;
+    if ((st = cuda_check(cudaMemcpyAsync(dt_out, &s->dt, sizeof(double), cudaMemcpyDeviceToHost, f->stream), "dt")))
+      return st;
+    return cuda_check(cudaStreamSynchronize(f->stream), "sync");
+  }
+  return DGF_OK;
+}
+
+dgf_status dgf_get_time(dgf_forest* f, double* t) {
+  if (dgf_status st = require_device(f)) return st;
+  if (!t) return fail(DGF_EINVAL, "null argument");
+  DeviceGuard dg(f->device);
+  DevScalars* s = (DevScalars*)f->scal.ptr;
+  return copy_state(f, t, &s->t, sizeof(double), cudaMemcpyDeviceToHost);
+}
+
+dgf_status dgf_set_time(dgf_forest* f, double t) {
+  if (dgf_status st = require_device(f)) return st;
+  DeviceGuard dg(f->device);
+  DevScalars* s = (DevScalars*)f->scal.ptr;
+  double tt = t;
+  return copy_state(f, &s->t, &tt, sizeof(double), cudaMemcpyHostToDevice);
+}
+
+dgf_status dgf_compute_dt(dgf_forest* f, double* dt) {
+  if (dgf_status st = require_device(f)) return st;
+  if (!dt) return fail(DGF_EINVAL, "null argument");
+  if (!f->have_state) return fail(DGF_ESTATE, "no state set");
+  DeviceGuard dg(f->device);
+  dgf_status st = init_lambda(f);
+  if (st) return st;
+  DevScalars* s = (DevScalars*)f->scal.ptr;
+  k_dt_only<<<1, 1, 0, f->stream>>>(s, f->cfl, (double*)f->dtout.ptr);
+  if ((st = cuda_check(cudaGetLastError(), "dt"))) return st;
+  return copy_state(f, dt, f->dtout.ptr, sizeof(double), cudaMemcpyDeviceToHost);
+}
+
+dgf_status dgf_conserved_totals(dgf_forest* f, double* totals) {
+  if (dgf_status st = require_device(f)) return st;
+  if (!totals) return fail(DGF_EINVAL, "null argument");
+  if (!f->have_state) return fail(DGF_ESTATE, "no state set");
+  DeviceGuard dg(f->device);
+  dgf_status st = cuda_check(do_totals(f, misc_args(f, 0)), "totals");
+  if (st) return st;
+  k_reduce<<<f->nv, 1024, 0, f->stream>>>((const double*)f->part.ptr, (size_t)f->nL * f->nc, (double*)f->tot.ptr);
+  if ((st = cuda_check(cudaGetLastError(), "reduce"))) return st;
+  return copy_state(f, totals, f->tot.ptr, f->nv * sizeof(double), cudaMemcpyDeviceToHost);
+}
+
+dgf_status dgf_status_word(dgf_forest* f, int32_t* status, int reset) {
+  if (dgf_status st = require_device(f)) return st;
+  if (!status) return fail(DGF_EINVAL, "null argument");
+  DeviceGuard dg(f->device);
+  DevScalars* s = (DevScalars*)f->scal.ptr;
+  int v = 0;
+  dgf_status st = copy_state(f, &v, &s->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (st) return st;
+  *status = v;
+  if (reset) {
+    int z = 0;
+    return copy_state(f, &s->status, &z, sizeof(int), cudaMemcpyHostToDevice);
+  }
+  return DGF_OK;
+}
+
+dgf_status dgf_set_timing(dgf_forest* f, int on) {
+  if (dgf_status st = require_device(f)) return st;
+  f->timing = on != 0;
+  return DGF_OK;
+}
+
+dgf_status dgf_kernel_times(dgf_forest* f, double* ms, int64_t* launches, int n_classes) {
+  if (dgf_status st = require_device(f)) return st;
+  DeviceGuard dg(f->device);
+  dgf_status st = cuda_check(cudaStreamSynchronize(f->stream), "sync");
+  if (st) return st;
+  for (auto& e : f->ev) {
+    float m = 0.f;
+    cudaEventElapsedTime(&m, e.a, e.b);
+    f->ms[e.cls] += m;
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  f->ev.clear();
+  for (int c = 0; c < n_classes && c < 3; ++c) {
+    if (ms) ms[c] = f->ms[c];
+    if (launches) launches[c] = f->launches[c];
+    f->ms[c] = 0;
+    f->launches[c] = 0;
+  }
+  return DGF_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------- regrid
+// New leaves get their state from the old ones: copies, splits (Eqs.
+// (11)-(12)) or combines (Eqs. (13)-(14)); done on the host in FP64 from a
+// device snapshot (regrids are rare compared with time increments).
+static dgf_status regrid(dgf_forest* f, const std::vector<uint64_t>& old_leaves) {
+  const int d = f->d, n = f->n, M = f->M, nc = f->nc, nv = f->nv, N = f->N;
+  std::vector<double> old_state;
+  const bool carry = f->device >= 0 && f->have_state;
+  std::vector<std::vector<double>> old_coef;
+  if (carry) {
+    DeviceGuard dg(f->device);
+    const size_t cnt = (size_t)old_leaves.size() * nv * M * nc;
+    old_state.resize(cnt);
+    if (f->precision == DGF_FP64) {
+      dgf_status st = copy_state(f, old_state.data(), f->U[0].ptr, cnt * 8, cudaMemcpyDeviceToHost);
+      if (st) return st;
+    } else {
+      std::vector<float> tmp(cnt);
+      dgf_status st = copy_state(f, tmp.data(), f->U[0].ptr, cnt * 4, cudaMemcpyDeviceToHost);
+      if (st) return st;
+      for (size_t i = 0; i < cnt; ++i) old_state[i] = tmp[i];
+    }
+  }
+  dgf_status st = build_device(f);
+  if (st) return st;
+  if (!carry) return DGF_OK;
+  std::unordered_map<uint64_t, int64_t> old_index;
+  for (size_t i = 0; i < old_leaves.size(); ++i) old_index[old_leaves[i]] = (int64_t)i;
+  const Basis1D& B = f->basis;
+  const int64_t L = f->host.n_leaves();
+  std::vector<double> ns((size_t)L * nv * M * nc, 0.0);
+  auto at = [&](std::vector<double>& s, int64_t leaf, int v, int m, int c) -> double& {
+    return s[(((size_t)leaf * nv + v) * M + m) * nc + c];
+  };
+  std::vector<double> coef;
+  for (int64_t i = 0; i < L; ++i) {
+    const uint64_t k = f->host.leaves[i];
+    auto it = old_index.find(k);
+    if (it != old_index.end()) {
+      std::memcpy(&at(ns, i, 0, 0, 0), &at(old_state, it->second, 0, 0, 0), sizeof(double) * nv * M * nc);
+      continue;
+    }
+    int64_t r;
+    int lev, pos[3];
+    Forest::unkey(k, &r, &lev, pos);
+    int pp[3] = {pos[0] >> 1, pos[1] >> 1, pos[2] >> 1};
+    auto pit = old_index.find(Forest::key(r, lev - 1, pp));
+    if (pit != old_index.end()) {
+      // split each parent cell to this child's cells (tensor form, exact)
+      for (int c = 0; c < nc; ++c) {
+        int I[3] = {0, 0, 0}, tt = c, Pc = 0, st = 1, e[3] = {0, 0, 0};
+        for (int a = 0; a < d; ++a) {
+          I[a] = tt % n;
+          tt /= n;
+          const int H = (pos[a] & 1) * n + I[a];
+          Pc += (H >> 1) * st;
+          e[a] = H & 1;
+          st *= n;
+        }
+        for (int v = 0; v < nv; ++v) {
+          for (int m = 0; m < M; ++m) {
+            double acc = 0.0;
+            for (int kk = 0; kk < M; ++kk) {
+              double w = 1.0;
+              int rm = m, rk = kk;
+              for (int a = 0; a < d; ++a) {
+                const std::vector<double>& S = e[a] ? B.Sp : B.Sm;
+                w *= S[(rm % N) * N + (rk % N)];
+                rm /= N;
+                rk /= N;
+              }
+              acc += w * at(old_state, pit->second, v, kk, Pc);
+            }
+            at(ns, i, v, m, c) = acc;
+          }
+        }
+      }
+      continue;
+    }
+    // combine: this leaf is a new parent of old leaves
+    for (int c = 0; c < nc; ++c) {
+      int I[3] = {0, 0, 0}, tt = c;
+      for (int a = 0; a < d; ++a) {
+        I[a] = tt % n;
+        tt /= n;
+      }
+      const int KC = (1 << d) * M;
+      std::vector<double> MP(M * M, 0.0), RHS((size_t)M * nv, 0.0);
+      for (int e = 0; e < (1 << d); ++e) {
+        int cb[3] = {0, 0, 0}, cc = 0, st = 1;
+        for (int a = 0; a < d; ++a) {
+          const int H = 2 * I[a] + ((e >> a) & 1);
+          cb[a] = H / n;
+          cc += (H - cb[a] * n) * st;
+          st *= n;
+        }
+        int kp[3] = {0, 0, 0};
+        for (int a = 0; a < d; ++a) kp[a] = 2 * pos[a] + cb[a];
+        const int64_t kid = old_index.at(Forest::key(r, lev + 1, kp));
+        f->host.cell_coefficients(Forest::key(r, lev + 1, kp), coef);
+        double ccoef[24];
+        for (int kk = 0; kk < (1 << d) * d; ++kk) ccoef[kk] = coef[(size_t)kk * nc + cc];
+        for (int q = 0; q < M; ++q) {
+          double xi[3], xp[3], wq = 1.0;
+          int rq = q;
+          for (int a = 0; a < d; ++a) {
+            xi[a] = B.x[rq % N];
+            wq *= B.w[rq % N];
+            xp[a] = 0.5 * (xi[a] + (((e >> a) & 1) ? 1.0 : -1.0));
+            rq /= N;
+          }
+          double A[9], Ja[9];
+          eval_map(d, ccoef, xi, nullptr, A);
+          const double wj = wq * det_and_cofactor(d, A, Ja);
+          double pp2[64];
+          for (int m = 0; m < M; ++m) pp2[m] = phi(B, d, m, xp);
+          for (int v = 0; v < nv; ++v) {
+            double u = 0.0;
+            for (int kk = 0; kk < M; ++kk) u += phi(B, d, kk, xi) * at(old_state, kid, v, kk, cc);
+            for (int m = 0; m < M; ++m) RHS[(size_t)m * nv + v] += wj * pp2[m] * u;
+          }
+          for (int m = 0; m < M; ++m)
+            for (int m2 = 0; m2 < M; ++m2) MP[m * M + m2] += wj * pp2[m] * pp2[m2];
+        }
+        (void)KC;
+      }
+      if (!chol_solve(M, MP, RHS, nv)) return fail(DGF_EINVAL, "singular combine mass matrix");
+      for (int v = 0; v < nv; ++v)
+        for (int m = 0; m < M; ++m) at(ns, i, v, m, c) = RHS[(size_t)m * nv + v];
+    }
+  }
+  DeviceGuard dg(f->device);
+  if (f->precision == DGF_FP64) {
+    st = copy_state(f, f->U[0].ptr, ns.data(), ns.size() * 8, cudaMemcpyHostToDevice);
+  } else {
+    std::vector<float> tmp(ns.begin(), ns.end());
+    st = copy_state(f, f->U[0].ptr, tmp.data(), tmp.size() * 4, cudaMemcpyHostToDevice);
+  }
+  if (st) return st;
+  return init_lambda(f);
+}

@@ -1,0 +1,170 @@
+// Explicit kernel instantiations for one (dimension, precision); included by
+// the small k_<dim>_<prec>.cu translation units so they compile in parallel.
+#pragma once
+
+#include "dg_device.cuh"
+#include "launch.hpp"
+
+namespace dgf {
+
+template <int N, typename Real>
+static Tab<N, Real> make_tab(const RtTables& r) {
+  Tab<N, Real> t;
+  for (int i = 0; i < N; ++i) {
+    t.x[i] = (Real)r.x[i];
+    t.w[i] = (Real)r.w[i];
+    t.lp[i] = (Real)r.lp[i];
+    t.lm[i] = (Real)r.lm[i];
+    t.lpw[i] = (Real)(r.lp[i] / r.w[i]);
+    t.lmw[i] = (Real)(r.lm[i] / r.w[i]);
+    for (int j = 0; j < N; ++j) {
+      t.V[i][j] = (Real)r.V[i * N + j];
+      t.Vi[i][j] = (Real)r.Vi[i * N + j];
+      t.Sh[i][j] = (Real)r.Sh[i * N + j];
+      t.Sm[i][j] = (Real)r.Sm[i * N + j];
+      t.Sp[i][j] = (Real)r.Sp[i * N + j];
+    }
+  }
+  return t;
+}
+
+template <int D, int P, typename Real>
+static cudaError_t stage_p(const RtStage& r, cudaStream_t s) {
+  StageArgs<D, P, Real> a;
+  a.nL = r.nL;
+  a.n = r.n;
+  a.zchunk = r.zchunk;
+  a.U = (const Real*)r.U;
+  a.Un = (const Real*)r.Un;
+  a.Uout = (Real*)r.Uout;
+  a.geo = (const Real*)r.geo;
+  a.gtr = (const Real*)r.gtr;
+  a.hcell = (const Real*)r.hcell;
+  a.dtp = r.dtp;
+  a.lam_bits = r.lam_bits;
+  a.status = r.status;
+  a.ca = (Real)r.ca;
+  a.cb = (Real)r.cb;
+  a.gamma = (Real)r.gamma;
+  a.mode = r.mode;
+  a.last = r.last;
+  a.T = make_tab<P + 1, Real>(r.T);
+  const size_t smem = stage_smem<D, P, Real>(r.n);
+  int dev = 0, maxs = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem + 512 > (size_t)maxs) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k_stage<D, P, Real>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int nchunks = D == 3 ? (r.n + r.zchunk - 1) / r.zchunk : 1;
+  dim3 grid(r.nL, nchunks);
+  k_stage<D, P, Real><<<grid, r.threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int D, int P, typename Real>
+static cudaError_t guard_p(const RtGuard& r, cudaStream_t s) {
+  GuardArgs<D, P, Real> a;
+  a.nL = r.nL;
+  a.n = r.n;
+  a.mode = r.mode;
+  a.U = (const Real*)r.U;
+  a.out = (Real*)r.out;
+  a.kind = r.kind;
+  a.nbr = r.nbr;
+  a.orient = r.orient;
+  a.qbits = r.qbits;
+  a.copoff = r.copoff;
+  a.cop = (const Real*)r.cop;
+  a.T = make_tab<P + 1, Real>(r.T);
+  const int nt = D == 3 ? r.n * r.n : r.n;
+  const size_t total = (size_t)r.nL * 2 * D * nt * (D + 2);
+  const int th = 128;
+  k_guard<D, P, Real><<<(unsigned)((total + th - 1) / th), th, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int D, int P, typename Real>
+static cudaError_t cfl_p(const RtMisc& r, cudaStream_t s) {
+  const int nc = D == 3 ? r.n * r.n * r.n : r.n * r.n;
+  const size_t total = (size_t)r.nL * nc * ipow(P + 1, D);
+  const int th = 256;
+  k_cfl<D, P, Real><<<(unsigned)((total + th - 1) / th), th, 0, s>>>(
+      r.nL, r.n, (const Real*)r.U, (const Real*)r.hcell, (Real)r.gamma, r.lam_bits, r.status,
+      make_tab<P + 1, Real>(r.T));
+  return cudaGetLastError();
+}
+
+template <int D, int P, typename Real>
+static cudaError_t project_p(const RtMisc& r, cudaStream_t s) {
+  const int nc = D == 3 ? r.n * r.n * r.n : r.n * r.n;
+  const size_t total = (size_t)r.nL * nc * (D + 2);
+  const int th = 128;
+  k_project<D, P, Real><<<(unsigned)((total + th - 1) / th), th, 0, s>>>(
+      r.nL, r.n, r.vals, (Real*)r.Uout, make_tab<P + 1, double>(r.T));
+  return cudaGetLastError();
+}
+
+template <int D, int P, typename Real>
+static cudaError_t totals_p(const RtMisc& r, cudaStream_t s) {
+  const int nc = D == 3 ? r.n * r.n * r.n : r.n * r.n;
+  const size_t total = (size_t)r.nL * nc;
+  const int th = 128;
+  k_totals<D, P, Real><<<(unsigned)((total + th - 1) / th), th, 0, s>>>(
+      r.nL, r.n, (const Real*)r.U, r.geo64, r.part, make_tab<P + 1, double>(r.T));
+  return cudaGetLastError();
+}
+
+#define DGF_DISPATCH_P(fn, r, s)                 \
+  switch ((r).p) {                               \
+    case 0: return fn<D, 0, Real>(r, s);         \
+    case 1: return fn<D, 1, Real>(r, s);         \
+    case 2: return fn<D, 2, Real>(r, s);         \
+    case 3: return fn<D, 3, Real>(r, s);         \
+    default: return cudaErrorInvalidValue;       \
+  }
+
+#define DGF_INSTANTIATE(DIM, REAL)                                                          \
+  template <>                                                                               \
+  cudaError_t launch_stage<DIM, REAL>(const RtStage& r, cudaStream_t s) {                   \
+    constexpr int D = DIM;                                                                  \
+    using Real = REAL;                                                                      \
+    DGF_DISPATCH_P(stage_p, r, s)                                                           \
+  }                                                                                         \
+  template <>                                                                               \
+  cudaError_t launch_guard<DIM, REAL>(const RtGuard& r, cudaStream_t s) {                   \
+    constexpr int D = DIM;                                                                  \
+    using Real = REAL;                                                                      \
+    DGF_DISPATCH_P(guard_p, r, s)                                                           \
+  }                                                                                         \
+  template <>                                                                               \
+  cudaError_t launch_cfl<DIM, REAL>(const RtMisc& r, cudaStream_t s) {                      \
+    constexpr int D = DIM;                                                                  \
+    using Real = REAL;                                                                      \
+    DGF_DISPATCH_P(cfl_p, r, s)                                                             \
+  }                                                                                         \
+  template <>                                                                               \
+  cudaError_t launch_project<DIM, REAL>(const RtMisc& r, cudaStream_t s) {                  \
+    constexpr int D = DIM;                                                                  \
+    using Real = REAL;                                                                      \
+    DGF_DISPATCH_P(project_p, r, s)                                                         \
+  }                                                                                         \
+  template <>                                                                               \
+  cudaError_t launch_totals<DIM, REAL>(const RtMisc& r, cudaStream_t s) {                   \
+    constexpr int D = DIM;                                                                  \
+    using Real = REAL;                                                                      \
+    DGF_DISPATCH_P(totals_p, r, s)                                                          \
+  }                                                                                         \
+  template <>                                                                               \
+  size_t stage_smem_bytes<DIM, REAL>(int p, int n) {                                        \
+    switch (p) {                                                                            \
+      case 0: return stage_smem<DIM, 0, REAL>(n);                                           \
+      case 1: return stage_smem<DIM, 1, REAL>(n);                                           \
+      case 2: return stage_smem<DIM, 2, REAL>(n);                                           \
+      case 3: return stage_smem<DIM, 3, REAL>(n);                                           \
+    }                                                                                       \
+    return 0;                                                                               \
+  }
+
+}  // namespace dgf

@@ -1,0 +1,74 @@
+// Type-erased launch descriptors passed from the C ABI layer to the
+// per-(dimension, precision) translation units that instantiate the kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dgf {
+
+// 1D reference tables in FP64, N <= 4 (converted to the kernel precision).
+struct RtTables {
+  int N;
+  double x[4], w[4], V[16], Vi[16], Sh[16], lp[4], lm[4], Sm[16], Sp[16];
+};
+
+struct RtStage {
+  int p, nL, n, zchunk, threads;
+  const void* U;
+  const void* Un;
+  void* Uout;
+  const void* geo;
+  const void* gtr;
+  const void* hcell;
+  const double* dtp;
+  unsigned long long* lam_bits;
+  int* status;
+  double ca, cb, gamma;
+  int mode, last;
+  RtTables T;
+};
+
+struct RtGuard {
+  int p, nL, n, mode;
+  const void* U;
+  void* out;
+  const int* kind;
+  const int* nbr;
+  const int* orient;
+  const int* qbits;
+  const int* copoff;
+  const void* cop;
+  RtTables T;
+};
+
+struct RtMisc {
+  int p, nL, n;
+  const void* U;
+  void* Uout;
+  const void* hcell;
+  const double* vals;
+  const double* geo64;
+  double* part;
+  double gamma;
+  unsigned long long* lam_bits;
+  int* status;
+  RtTables T;
+};
+
+// returns cudaErrorInvalidConfiguration when the shared-memory footprint
+// exceeds what the device allows
+template <int D, typename Real>
+cudaError_t launch_stage(const RtStage& r, cudaStream_t s);
+template <int D, typename Real>
+cudaError_t launch_guard(const RtGuard& r, cudaStream_t s);
+template <int D, typename Real>
+cudaError_t launch_cfl(const RtMisc& r, cudaStream_t s);
+template <int D, typename Real>
+cudaError_t launch_project(const RtMisc& r, cudaStream_t s);
+template <int D, typename Real>
+cudaError_t launch_totals(const RtMisc& r, cudaStream_t s);
+template <int D, typename Real>
+size_t stage_smem_bytes(int p, int n);
+
+}  // namespace dgf

@@ -1,0 +1,148 @@
+"""C ABI checks that need no GPU: the library loads and exports every symbol
+that include/dgf.h declares, and its host forest reproduces the oracle's
+integer tables bit for bit (independent code, same canonical rules)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import forest as FO
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def dgf():
+    import paper_2502_12620_gb300 as pkg
+    if not os.path.exists(pkg.LIB_PATH):
+        from paper_2502_12620_gb300 import build
+        build.build()
+    return pkg
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "dgf.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:dgf_status|const char\*)\s+(dgf_\w+)\s*\(", src, re.M)))
+
+
+def test_library_exports_every_declared_symbol(dgf):
+    L = ctypes.CDLL(dgf.LIB_PATH)
+    syms = declared_symbols()
+    assert len(syms) >= 20
+    for s in syms:
+        assert hasattr(L, s), s
+    # the binding wraps every declared call
+    assert set(syms) - {"dgf_last_error"} <= set(dgf._SIGS)
+
+
+def _host_forest(dgf, w, p=2):
+    return dgf.Forest.from_workload(w, p=p, device=-1, torch_memory=False)
+
+
+CASES = {
+    "rotated_pair": lambda: W.rotated_pair_2d(),
+    "vortex2d": W.vortex2d_forest,
+    "jitter3d_s0": lambda: W.jitter3d_forest(seed=0),
+    "jitter3d_s3": lambda: W.jitter3d_forest(seed=3, n_seg=2),
+    "cube_rot": lambda: W.periodic_cube_forest(3, n_seg=2, rotate_roots=True, seed=7),
+    "outflow2d": lambda: dict(W.lattice_forest(2, 2, 1.0, 2, periodic=False), refine=[[(1, 1, (0, 0))]]),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_leaf_tables_bit_exact_vs_oracle(dgf, case):
+    w = CASES[case]()
+    f = _host_forest(dgf, w)
+    T = f.leaf_table()
+    O = FO.build(w).leaf_table()
+    for k in ("root", "level", "pos", "kind", "nbr", "orient"):
+        assert np.array_equal(T[k].astype(np.int64), O[k].astype(np.int64)), k
+
+
+def test_refine_closure_and_coarsen_match_oracle(dgf):
+    w = W.lattice_forest(3, 2, 1.0, 2, rotate_roots=True, seed=11)
+    f = _host_forest(dgf, w)
+    o = FO.build(w)
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        ids = sorted(rng.choice(f.n_leaves, size=3, replace=False).tolist())
+        keys = [o.leaves()[i] for i in ids]
+        f.refine(ids)
+        o.refine(keys)
+        T, O = f.leaf_table(), o.leaf_table()
+        for k in ("root", "level", "pos", "kind", "nbr", "orient"):
+            assert np.array_equal(T[k].astype(np.int64), O[k].astype(np.int64)), k
+    # coarsening: both implementations accept or refuse (2:1) the same parents
+    import copy
+    deep = int(np.argmax(f.leaf_table()["level"]))
+    f.refine([deep])
+    o.refine([o.leaves()[deep]])
+    lv = f.leaf_table()["level"]
+    outcomes = set()
+    for i in range(len(lv)):
+        if lv[i] < 2:
+            continue
+        key = o.leaves()[i]
+        parent = (key[0], key[1] - 1, tuple(x >> 1 for x in key[2]))
+        oc = copy.deepcopy(o)
+        try:
+            oc.coarsen([parent])
+            o_ok = True
+        except FO.BalanceError:
+            o_ok = False
+        fc = _host_forest(dgf, w)
+        for batch in _replay(o):
+            fc.refine(batch)
+        try:
+            fc.coarsen([i])
+            f_ok = True
+        except dgf.DgfError as e:
+            assert e.code == -6
+            f_ok = False
+        assert o_ok == f_ok, (i, key)
+        outcomes.add(o_ok)
+        if o_ok:
+            T, O = fc.leaf_table(), oc.leaf_table()
+            for k in ("level", "pos", "kind", "nbr", "orient"):
+                assert np.array_equal(T[k].astype(np.int64), O[k].astype(np.int64)), k
+        if len(outcomes) == 2 and i > 40:
+            break
+    assert outcomes == {True, False}
+
+
+def _replay(o):
+    """Refinement batches (leaf ids, level by level) that rebuild o's leaves
+    from its roots: refine every internal node, shallowest first."""
+    internal = sorted((k for k, v in o.tree.items() if v is False), key=lambda k: k[1])
+    cur = FO.Forest(o.d, o.n, o.nodes, o.root_corners, None, o.periodic)
+    batches = []
+    for lev in sorted({k[1] for k in internal}):
+        keys = [k for k in internal if k[1] == lev and cur.tree.get(k) is True]
+        ids = [cur.leaves().index(k) for k in keys]
+        cur.refine(keys)
+        batches.append(ids)
+    return batches
+
+
+def test_quad_points_match_oracle_geometry(dgf):
+    from oracle import dg
+    w = W.jitter3d_forest(seed=2, n_seg=2)
+    f = _host_forest(dgf, w)
+    S = dg.Solver(FO.build(w), 2)
+    assert np.allclose(f.quad_points(), S.quad_points(), rtol=0, atol=1e-14)
+
+
+def test_bad_descriptions_are_rejected(dgf):
+    w = W.rotated_pair_2d()
+    with pytest.raises(dgf.DgfError) as e:
+        dgf.Forest(2, 3, 2, w["nodes"], w["root_corners"], device=-1, torch_memory=False)
+    assert e.value.code == -1
+    with pytest.raises(dgf.DgfError):
+        dgf.Forest(2, 2, 5, w["nodes"], w["root_corners"], device=-1, torch_memory=False)
+    bad = np.array(w["root_corners"])
+    bad[0, 0] = 99
+    with pytest.raises(dgf.DgfError):
+        dgf.Forest(2, 2, 2, w["nodes"], bad, device=-1, torch_memory=False)
