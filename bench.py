@@ -46,9 +46,19 @@ def peaks():
         return {"hbm_gbs": HBM_FALLBACK}, "fallback"
 
 
+WORKLOADS = {
+    # the benchmark line: 71 leaves, 36,352 cells, p=2
+    "jitter3d": (WORKLOAD, lambda: W.jitter3d_forest(seed=0), 2),
+    # larger affine case for profiling (state 141 MB FP32, above L2)
+    "cube8": ("3d-euler-periodic-cube-8^3-roots-n8-p2", lambda: W.periodic_cube_forest(8), 2),
+    "cube8p1": ("3d-euler-periodic-cube-8^3-roots-n8-p1", lambda: W.periodic_cube_forest(8), 1),
+}
+_SEL = ["jitter3d"]
+
+
 def the_workload():
-    w = W.jitter3d_forest(seed=0)
-    return w, 2
+    name, mk, p = WORKLOADS[_SEL[0]]
+    return mk(), p
 
 
 def vortex(x):
@@ -230,6 +240,12 @@ def run_ours(args):
     ms = barrier_max(ms, ws)
     value = dof * 3 * args.steps / (ms / 1e3) * ws
     status = f32.status_word()
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"workload": WORKLOADS[_SEL[0]][0], "value": value, "unit": "DOF-updates/s",
+                              "ms_per_step": ms / args.steps, "dof": dof, "status_word": status,
+                              "clocks": ck.summary()}))
+        return 0
 
     # instrumented replay of the same steps: per-kernel durations
     f32.set_state(U0)
@@ -323,7 +339,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="jitter3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--quick", action="store_true", help="FP32 timed steps only (profiling runs)")
     args = ap.parse_args()
+    _SEL[0] = args.workload
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

@@ -233,13 +233,15 @@ __device__ __forceinline__ void lf_flux(const Real (&uL)[D + 2], const Real (&uR
 // ------------------------------------------------------------ kernel args
 template <int D, int P, typename Real>
 struct StageArgs {
-  int nL, n, zchunk;
+  int nL, n, zchunk, nchunks;
   const Real* __restrict__ U;    // stage input U^(k)
   const Real* __restrict__ Un;   // U^n
   Real* __restrict__ Uout;       // stage output (or L(U) when mode == 1)
-  const Real* __restrict__ geo;  // [b][g][cell]
+  const Real* __restrict__ geo;  // [b][g][cell] trilinear coefficients
   const Real* __restrict__ gtr;  // [b][f][v][fp][t] guard traces
   const Real* __restrict__ hcell;  // [b][cell]
+  const unsigned char* __restrict__ affine;  // [b] 1 if every cell has the same constant metric
+  const Real* __restrict__ ameta;  // [b][D*D+1]: rows of J dxi/dx, then 1/J
   const double* __restrict__ dtp;
   unsigned long long* lam_bits;
   int* status;
@@ -258,8 +260,18 @@ struct GuardArgs {
   const int* __restrict__ orient;  // [b][f] packed decoded orientation
   const int* __restrict__ qbits;   // [b] pos & 1 bits
   const int* __restrict__ copoff;  // [b][f] first combine operator or -1
-  const Real* __restrict__ cop;    // [op][M][2^D M]
+  const Real* __restrict__ cop;    // [op][2^D M][M]: column k' of the operator is contiguous
+  const int* __restrict__ fine_list;  // [nfine] leaf * 2D + face of every finer-neighbour face
+  int nfine;
   Tab<P + 1, Real> T;
+};
+
+// threads per CTA and CTAs per SM of the stage kernel (registers and shared
+// memory decide: FP32 up to p=2 runs 2 x 512 threads per SM)
+template <int P, typename Real>
+struct StageCfg {
+  static constexpr int NT = sizeof(Real) == 4 ? 512 : (P <= 1 ? 512 : 256);
+  static constexpr int MINB = (sizeof(Real) == 4 && P <= 2) ? 2 : 1;
 };
 
 // shared-memory footprint of the stage kernel (bytes)
@@ -275,399 +287,475 @@ __host__ __device__ constexpr size_t stage_smem(int n) {
   return (us + rs + fs + fz + gs) * sizeof(Real);
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// metric of one cell: affine blocks use block constants, curvilinear cells
+// their trilinear coefficients (held in registers by the caller)
+template <int D, typename Real>
+struct CellMetric {
+  bool aff;
+  const Real* am;  // shared: rows of J dxi/dx, then 1/J
+  const Real* X;   // shared: trilinear coefficients of the cell, stride ncl
+  int stride;
+  __device__ __forceinline__ void load(bool affine, const Real* amsh, const Real* gs, int ncl, int c) {
+    aff = affine;
+    am = amsh;
+    X = gs + c;
+    stride = ncl;
+  }
+  __device__ __forceinline__ void row(const Real* xi, int dir, Real (&Ja)[D]) const {
+    if (aff) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) Ja[j] = am[dir * D + j];
+    } else {
+      Real tg[D][D];
+      tangents<D, Real>(X, stride, xi, tg);
+      contra_row<D, Real>(tg, dir, Ja);
+    }
+  }
+  // row `dir` and 1/J at one point
+  __device__ __forceinline__ Real row_inv_jac(const Real* xi, int dir, Real (&Ja)[D]) const {
+    if (aff) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) Ja[j] = am[dir * D + j];
+      return am[D * D];
+    }
+    Real tg[D][D];
+    tangents<D, Real>(X, stride, xi, tg);
+    contra_row<D, Real>(tg, dir, Ja);
+    Real J = Real(0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) J += tg[dir][j] * Ja[j];
+    return Real(1) / J;
+  }
+};
+
 // ============================================================ stage kernel
-// grid: (leaf, z-chunk); one CTA sweeps the layers of its chunk.
+// Persistent CTAs; work item = (leaf, z-chunk); a CTA sweeps the layers of
+// its chunk.  Per layer: modal -> nodal in shared memory, x and y face
+// fluxes (each face once) and volume terms, z faces carried between layers,
+// 1/J, nodal -> modal, SSP-RK combination, CFL minimum on the last stage.
 template <int D, int P, typename Real>
-__global__ void __launch_bounds__(256) k_stage(const StageArgs<D, P, Real> A) {
+__global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB)
+    k_stage(const StageArgs<D, P, Real> A) {
   constexpr int N = P + 1, NV = D + 2, M = ipow(N, D), Q = M, NFP = ipow(N, D - 1);
   constexpr int NG = ((1 << D) - 1) * D;
   const int n = A.n;
   const int NCL = n * n;
   const int nc = D == 3 ? NCL * n : NCL;
-  const int nt = ipow(n, 1) * (D == 3 ? n : 1);  // guard cells per face
-  const int b = blockIdx.x;
-  const int chunk = blockIdx.y;
-  const int k0 = D == 3 ? chunk * A.zchunk : 0;
-  const int k1 = D == 3 ? min(n, k0 + A.zchunk) : 1;
+  const int nt = D == 3 ? n * n : n;  // guard cells per face
   const auto& T = A.T;
   const Real gamma = A.gamma;
+  const Real gm1 = gamma - Real(1);
   const Real dt = Real(*A.dtp);
+  const int tid = threadIdx.x, nthr = blockDim.x;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Real sx[N];
+  __shared__ Real sam[D * D + 1];
   Real* us = reinterpret_cast<Real*>(smem_raw);
   Real* rs = us + NV * Q * NCL;
   Real* fs = rs + NV * Q * NCL;
   Real* fz = fs + NV * NFP * (n + 1) * n;
   Real* gs = fz + (D == 3 ? NV * NFP * NCL : 0);
   Real* tb = fs;  // top/bottom halo traces reuse the in-layer face buffer
+  if (tid < N) sx[tid] = T.x[tid];
 
   const size_t ustride = (size_t)nc;
-  const Real* Ub = A.U + (size_t)b * NV * M * nc;
-  const Real* Unb = A.Un + (size_t)b * NV * M * nc;
-  Real* Ob = A.Uout + (size_t)b * NV * M * nc;
-  const Real* Gb = A.geo + (size_t)b * NG * nc;
-  const Real* Tb = A.gtr + (size_t)b * 2 * D * NV * NFP * nt;
-  const int tid = threadIdx.x, nthr = blockDim.x;
   Real lam_min = Real(3.0e38);
   bool bad = false;
+  const int items = A.nL * A.nchunks;
 
 #define US(v, q, c) us[((v) * Q + (q)) * NCL + (c)]
 #define RS(v, q, c) rs[((v) * Q + (q)) * NCL + (c)]
 #define GS(g, c) gs[(g) * NCL + (c)]
 #define GTR(f, v, fp, t) Tb[(((size_t)(f) * NV + (v)) * NFP + (fp)) * nt + (t)]
+// x faces: [v][fp][row j][face fi]; y faces: [v][fp][face fi][column i]
+#define FX(v, fp, j, fi) fs[(((v) * NFP + (fp)) * n + (j)) * (n + 1) + (fi)]
+#define FY(v, fp, fi, i) fs[(((v) * NFP + (fp)) * (n + 1) + (fi)) * n + (i)]
 
-  for (int k = k0; k < k1; ++k) {
-    const int cbase = D == 3 ? k * NCL : 0;
-    // ---------------------------------------------------- load layer k
-    for (int w = tid; w < NCL * NV; w += nthr) {
-      const int c = w % NCL, v = w / NCL;
-      Real a[M], t2[M];
-#pragma unroll
-      for (int m = 0; m < M; ++m) a[m] = Ub[((size_t)v * M + m) * ustride + cbase + c];
-      apply_all<D, N, Real>(T.V, a, t2);
-#pragma unroll
-      for (int q = 0; q < Q; ++q) US(v, q, c) = a[q];
-    }
-    for (int w = tid; w < NCL * NG; w += nthr) {
-      const int c = w % NCL, g = w / NCL;
-      GS(g, c) = Gb[(size_t)g * nc + cbase + c];
-    }
-    __syncthreads();
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int b = item / A.nchunks;
+    const int chunk = item % A.nchunks;
+    const int k0 = D == 3 ? chunk * A.zchunk : 0;
+    const int k1 = D == 3 ? min(n, k0 + A.zchunk) : 1;
+    const Real* Ub = A.U + (size_t)b * NV * M * nc;
+    const Real* Unb = A.Un + (size_t)b * NV * M * nc;
+    Real* Ob = A.Uout + (size_t)b * NV * M * nc;
+    const Real* Gb = A.geo + (size_t)b * NG * nc;
+    const Real* Tb = A.gtr + (size_t)b * 2 * D * NV * NFP * nt;
+    const bool aff = A.affine[b] != 0;
+    __syncthreads();  // previous item is done with the shared buffers
+    if (aff && tid < D * D + 1) sam[tid] = A.ameta[(size_t)b * (D * D + 1) + tid];
 
-    if constexpr (D == 3) {
-      if (k == k0) {
-        // bottom halo trace of layer k0: guard (block face z-) or the layer below
+    for (int k = k0; k < k1; ++k) {
+      const int cbase = D == 3 ? k * NCL : 0;
+      // ------------------------------------------- L2 prefetch of what comes next
+      {
+        const int lines_per_row = (NCL * (int)sizeof(Real) + 127) / 128;
+        const int rows = NV * M;
+        for (int w = tid; w < rows * lines_per_row; w += nthr) {
+          const int r = w / lines_per_row, l = w % lines_per_row;
+          if (D == 3 && k + 1 < n)
+            prefetch_l2(Ub + (size_t)r * ustride + (k + 1) * NCL + l * (128 / sizeof(Real)));
+          if (A.mode == 0 && A.ca != Real(0)) prefetch_l2(Unb + (size_t)r * ustride + cbase + l * (128 / sizeof(Real)));
+        }
+      }
+      // ------------------------------------------- load layer k (modal -> nodal)
+      for (int w = tid; w < NCL * NV; w += nthr) {
+        const int c = w % NCL, v = w / NCL;
+        Real a[M], t2[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) a[m] = Ub[((size_t)v * M + m) * ustride + cbase + c];
+        apply_all<D, N, Real>(T.V, a, t2);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) US(v, q, c) = a[q];
+      }
+      if (!aff) {
+        for (int w = tid; w < NCL * NG; w += nthr) {
+          const int c = w % NCL, g = w / NCL;
+          GS(g, c) = Gb[(size_t)g * nc + cbase + c];
+        }
+      }
+      __syncthreads();
+
+      if constexpr (D == 3) {
+        if (k == k0) {
+          // bottom halo trace of the first layer: guard (z-) or the layer below
+          for (int w = tid; w < NCL * NV; w += nthr) {
+            const int c = w % NCL, v = w / NCL;
+            Real tr[NFP];
+            if (k0 == 0) {
+#pragma unroll
+              for (int fp = 0; fp < NFP; ++fp) tr[fp] = GTR(4, v, fp, c);
+            } else {
+              Real K[M];
+#pragma unroll
+              for (int m = 0; m < M; ++m) K[m] = Ub[((size_t)v * M + m) * ustride + (k0 - 1) * NCL + c];
+              modal_trace<3, N, 2, Real>(T, K, +1, tr);
+            }
+#pragma unroll
+            for (int fp = 0; fp < NFP; ++fp) tb[(v * NFP + fp) * NCL + c] = tr[fp];
+          }
+          __syncthreads();
+          for (int w = tid; w < NCL * NFP; w += nthr) {
+            const int c = w % NCL, fp = w / NCL;
+            Real uL[NV], uR[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+              uL[v] = tb[(v * NFP + fp) * NCL + c];
+              Real s = Real(0);
+#pragma unroll
+              for (int qz = 0; qz < N; ++qz) s += T.lm[qz] * US(v, fp + NFP * qz, c);
+              uR[v] = s;
+            }
+            CellMetric<3, Real> cm;
+            cm.load(aff, sam, gs, NCL, c);
+            const Real xi[3] = {sx[fp % N], sx[fp / N], Real(-1)};
+            Real Ja[3], Fh[NV];
+            cm.row(xi, 2, Ja);
+            lf_flux<3, Real>(uL, uR, Ja, gamma, Fh);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) fz[(v * NFP + fp) * NCL + c] = Fh[v];
+          }
+          __syncthreads();
+        }
+      }
+
+      // ------------------------------------------------- x faces
+      for (int w = tid; w < (n + 1) * n * NFP; w += nthr) {
+        const int fi = w % (n + 1);
+        const int j = (w / (n + 1)) % n;
+        const int fp = w / ((n + 1) * n);
+        const int t = D == 3 ? j + n * k : j;
+        Real uL[NV], uR[NV];
+        const int cl = (fi - 1) + n * j, cr = fi + n * j;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          if (fi == 0) {
+            uL[v] = GTR(0, v, fp, t);
+          } else {
+            Real s = Real(0);
+#pragma unroll
+            for (int qx = 0; qx < N; ++qx) s += T.lp[qx] * US(v, qx + N * fp, cl);
+            uL[v] = s;
+          }
+          if (fi == n) {
+            uR[v] = GTR(1, v, fp, t);
+          } else {
+            Real s = Real(0);
+#pragma unroll
+            for (int qx = 0; qx < N; ++qx) s += T.lm[qx] * US(v, qx + N * fp, cr);
+            uR[v] = s;
+          }
+        }
+        CellMetric<D, Real> cm;
+        cm.load(aff, sam, gs, NCL, fi == n ? cl : cr);
+        Real xi[D];
+        xi[0] = fi == n ? Real(1) : Real(-1);
+        xi[1] = sx[fp % N];
+        if constexpr (D == 3) xi[2] = sx[fp / N];
+        Real Ja[D], Fh[NV];
+        cm.row(xi, 0, Ja);
+        lf_flux<D, Real>(uL, uR, Ja, gamma, Fh);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) FX(v, fp, j, fi) = Fh[v];
+      }
+      __syncthreads();
+      // ------------------------------------------------- x volume + lift
+      for (int w = tid; w < NCL * NFP; w += nthr) {
+        const int c = w % NCL, fp = w / NCL;
+        const int i = c % n, j = c / n;
+        CellMetric<D, Real> cm;
+        cm.load(aff, sam, gs, NCL, c);
+        Real xi[D];
+        xi[1] = sx[fp % N];
+        if constexpr (D == 3) xi[2] = sx[fp / N];
+        Real F[N][NV];
+#pragma unroll
+        for (int qx = 0; qx < N; ++qx) {
+          Real u[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) u[v] = US(v, qx + N * fp, c);
+          xi[0] = T.x[qx];
+          Real Ja[D], Fq[NV];
+          cm.row(xi, 0, Ja);
+          flux_along<D, Real>(u, Ja, gm1, Fq);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) F[qx][v] = Fq[v];
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const Real fm = FX(v, fp, j, i);
+          const Real fpl = FX(v, fp, j, i + 1);
+#pragma unroll
+          for (int qx = 0; qx < N; ++qx) {
+            Real s = Real(0);
+#pragma unroll
+            for (int jj = 0; jj < N; ++jj) s += T.Sh[qx][jj] * F[jj][v];
+            RS(v, qx + N * fp, c) = s - T.lpw[qx] * fpl + T.lmw[qx] * fm;
+          }
+        }
+      }
+      __syncthreads();
+      // ------------------------------------------------- y faces
+      for (int w = tid; w < (n + 1) * n * NFP; w += nthr) {
+        const int i = w % n;
+        const int fi = (w / n) % (n + 1);
+        const int fp = w / ((n + 1) * n);  // qx + N qz
+        const int qx = fp % N, qz = fp / N;
+        const int t = D == 3 ? i + n * k : i;
+        Real uL[NV], uR[NV];
+        const int cl = i + n * (fi - 1), cr = i + n * fi;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          if (fi == 0) {
+            uL[v] = GTR(2, v, fp, t);
+          } else {
+            Real s = Real(0);
+#pragma unroll
+            for (int qy = 0; qy < N; ++qy) s += T.lp[qy] * US(v, qx + N * qy + N * N * qz, cl);
+            uL[v] = s;
+          }
+          if (fi == n) {
+            uR[v] = GTR(3, v, fp, t);
+          } else {
+            Real s = Real(0);
+#pragma unroll
+            for (int qy = 0; qy < N; ++qy) s += T.lm[qy] * US(v, qx + N * qy + N * N * qz, cr);
+            uR[v] = s;
+          }
+        }
+        CellMetric<D, Real> cm;
+        cm.load(aff, sam, gs, NCL, fi == n ? cl : cr);
+        Real xi[D];
+        xi[0] = sx[qx];
+        xi[1] = fi == n ? Real(1) : Real(-1);
+        if constexpr (D == 3) xi[2] = sx[qz];
+        Real Ja[D], Fh[NV];
+        cm.row(xi, 1, Ja);
+        lf_flux<D, Real>(uL, uR, Ja, gamma, Fh);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) FY(v, fp, fi, i) = Fh[v];
+      }
+      __syncthreads();
+      // ------------------------------------------------- y volume + lift
+      for (int w = tid; w < NCL * NFP; w += nthr) {
+        const int c = w % NCL, fp = w / NCL;
+        const int i = c % n, j = c / n;
+        const int qx = fp % N, qz = fp / N;
+        CellMetric<D, Real> cm;
+        cm.load(aff, sam, gs, NCL, c);
+        Real xi[D];
+        xi[0] = sx[qx];
+        if constexpr (D == 3) xi[2] = sx[qz];
+        Real F[N][NV];
+        Real iJ[N];
+#pragma unroll
+        for (int qy = 0; qy < N; ++qy) {
+          Real u[NV];
+          const int q = qx + N * qy + N * N * qz;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) u[v] = US(v, q, c);
+          xi[1] = T.x[qy];
+          Real Ja[D], Fq[NV];
+          if constexpr (D == 2) iJ[qy] = cm.row_inv_jac(xi, 1, Ja);
+          else cm.row(xi, 1, Ja);
+          flux_along<D, Real>(u, Ja, gm1, Fq);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) F[qy][v] = Fq[v];
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const Real fm = FY(v, fp, j, i);
+          const Real fpl = FY(v, fp, j + 1, i);
+#pragma unroll
+          for (int qy = 0; qy < N; ++qy) {
+            Real s = Real(0);
+#pragma unroll
+            for (int jj = 0; jj < N; ++jj) s += T.Sh[qy][jj] * F[jj][v];
+            const int q = qx + N * qy + N * N * qz;
+            Real r = RS(v, q, c) + s - T.lpw[qy] * fpl + T.lmw[qy] * fm;
+            if constexpr (D == 2) r *= iJ[qy];
+            RS(v, q, c) = r;
+          }
+        }
+      }
+      __syncthreads();
+
+      if constexpr (D == 3) {
+        // ------------------------------------------- top halo trace of layer k
         for (int w = tid; w < NCL * NV; w += nthr) {
           const int c = w % NCL, v = w / NCL;
           Real tr[NFP];
-          if (k0 == 0) {
+          if (k == n - 1) {
 #pragma unroll
-            for (int fp = 0; fp < NFP; ++fp) tr[fp] = GTR(4, v, fp, c);
+            for (int fp = 0; fp < NFP; ++fp) tr[fp] = GTR(5, v, fp, c);
           } else {
             Real K[M];
 #pragma unroll
-            for (int m = 0; m < M; ++m) K[m] = Ub[((size_t)v * M + m) * ustride + (k0 - 1) * NCL + c];
-            modal_trace<3, N, 2, Real>(T, K, +1, tr);
+            for (int m = 0; m < M; ++m) K[m] = Ub[((size_t)v * M + m) * ustride + (k + 1) * NCL + c];
+            modal_trace<3, N, 2, Real>(T, K, -1, tr);
           }
 #pragma unroll
           for (int fp = 0; fp < NFP; ++fp) tb[(v * NFP + fp) * NCL + c] = tr[fp];
         }
         __syncthreads();
+        // ------------------------------------------- z volume + z faces, 1/J
         for (int w = tid; w < NCL * NFP; w += nthr) {
           const int c = w % NCL, fp = w / NCL;
           const int qx = fp % N, qy = fp / N;
-          Real uL[NV], uR[NV];
+          CellMetric<3, Real> cm;
+          cm.load(aff, sam, gs, NCL, c);
+          Real xi[3] = {sx[qx], sx[qy], Real(0)};
+          Real F[N][NV];
+          Real iJ[N];
+#pragma unroll
+          for (int qz = 0; qz < N; ++qz) {
+            Real u[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) u[v] = US(v, fp + NFP * qz, c);
+            xi[2] = T.x[qz];
+            Real Ja[3], Fq[NV];
+            iJ[qz] = cm.row_inv_jac(xi, 2, Ja);
+            flux_along<3, Real>(u, Ja, gm1, Fq);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) F[qz][v] = Fq[v];
+          }
+          // top face flux: own top trace vs the halo trace above
+          Real uL[NV], uR[NV], Fh[NV];
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
-            uL[v] = tb[(v * NFP + fp) * NCL + c];
             Real s = Real(0);
 #pragma unroll
-            for (int qz = 0; qz < N; ++qz) s += T.lm[qz] * US(v, fp + NFP * qz, c);
-            uR[v] = s;
+            for (int qz = 0; qz < N; ++qz) s += T.lp[qz] * US(v, fp + NFP * qz, c);
+            uL[v] = s;
+            uR[v] = tb[(v * NFP + fp) * NCL + c];
           }
-          const Real xi[3] = {T.x[qx], T.x[qy], Real(-1)};
-          Real tg[3][3], Ja[3], Fh[NV];
-          tangents<3, Real>(&GS(0, c), NCL, xi, tg);
-          contra_row<3, Real>(tg, 2, Ja);
-          lf_flux<3, Real>(uL, uR, Ja, gamma, Fh);
+          {
+            xi[2] = Real(1);
+            Real Ja[3];
+            cm.row(xi, 2, Ja);
+            lf_flux<3, Real>(uL, uR, Ja, gamma, Fh);
+          }
 #pragma unroll
-          for (int v = 0; v < NV; ++v) fz[(v * NFP + fp) * NCL + c] = Fh[v];
+          for (int v = 0; v < NV; ++v) {
+            const Real fbot = fz[(v * NFP + fp) * NCL + c];
+#pragma unroll
+            for (int qz = 0; qz < N; ++qz) {
+              Real s = Real(0);
+#pragma unroll
+              for (int jj = 0; jj < N; ++jj) s += T.Sh[qz][jj] * F[jj][v];
+              const int q = fp + NFP * qz;
+              RS(v, q, c) = (RS(v, q, c) + s - T.lpw[qz] * Fh[v] + T.lmw[qz] * fbot) * iJ[qz];
+            }
+            fz[(v * NFP + fp) * NCL + c] = Fh[v];
+          }
         }
         __syncthreads();
       }
-    }
 
-    // ---------------------------------------------------- x faces
-    for (int w = tid; w < (n + 1) * n * NFP; w += nthr) {
-      const int fi = w % (n + 1);
-      const int j = (w / (n + 1)) % n;
-      const int fp = w / ((n + 1) * n);
-      const int t = D == 3 ? j + n * k : j;
-      Real uL[NV], uR[NV];
-      const int cl = (fi - 1) + n * j, cr = fi + n * j;
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        if (fi == 0) {
-          uL[v] = GTR(0, v, fp, t);
-        } else {
-          Real s = Real(0);
-#pragma unroll
-          for (int qx = 0; qx < N; ++qx) s += T.lp[qx] * US(v, qx + N * fp, cl);
-          uL[v] = s;
-        }
-        if (fi == n) {
-          uR[v] = GTR(1, v, fp, t);
-        } else {
-          Real s = Real(0);
-#pragma unroll
-          for (int qx = 0; qx < N; ++qx) s += T.lm[qx] * US(v, qx + N * fp, cr);
-          uR[v] = s;
-        }
-      }
-      const int cg = fi == n ? cl : cr;
-      Real xi[D];
-      xi[0] = fi == n ? Real(1) : Real(-1);
-      xi[1] = T.x[fp % N];
-      if constexpr (D == 3) xi[2] = T.x[fp / N];
-      Real tg[D][D], Ja[D], Fh[NV];
-      tangents<D, Real>(&GS(0, cg), NCL, xi, tg);
-      contra_row<D, Real>(tg, 0, Ja);
-      lf_flux<D, Real>(uL, uR, Ja, gamma, Fh);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) fs[((v * NFP + fp) * (n + 1) + fi) * n + j] = Fh[v];
-    }
-    __syncthreads();
-    // ---------------------------------------------------- x volume + lift
-    for (int w = tid; w < NCL * NFP; w += nthr) {
-      const int c = w % NCL, fp = w / NCL;
-      const int i = c % n, j = c / n;
-      Real F[N][NV];
-      const Real* Xc = &GS(0, c);
-#pragma unroll
-      for (int qx = 0; qx < N; ++qx) {
-        Real u[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) u[v] = US(v, qx + N * fp, c);
-        Real xi[D];
-        xi[0] = T.x[qx];
-        xi[1] = T.x[fp % N];
-        if constexpr (D == 3) xi[2] = T.x[fp / N];
-        Real tg[D][D], Ja[D], Fq[NV];
-        tangents<D, Real>(Xc, NCL, xi, tg);
-        contra_row<D, Real>(tg, 0, Ja);
-        flux_along<D, Real>(u, Ja, gamma - Real(1), Fq);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) F[qx][v] = Fq[v];
-      }
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const Real fm = fs[((v * NFP + fp) * (n + 1) + i) * n + j];
-        const Real fpl = fs[((v * NFP + fp) * (n + 1) + i + 1) * n + j];
-#pragma unroll
-        for (int qx = 0; qx < N; ++qx) {
-          Real s = Real(0);
-#pragma unroll
-          for (int jj = 0; jj < N; ++jj) s += T.Sh[qx][jj] * F[jj][v];
-          RS(v, qx + N * fp, c) = s - T.lpw[qx] * fpl + T.lmw[qx] * fm;
-        }
-      }
-    }
-    __syncthreads();
-    // ---------------------------------------------------- y faces
-    for (int w = tid; w < (n + 1) * n * NFP; w += nthr) {
-      const int fi = w % (n + 1);
-      const int i = (w / (n + 1)) % n;
-      const int fp = w / ((n + 1) * n);  // qx + N qz
-      const int qx = fp % N, qz = fp / N;
-      const int t = D == 3 ? i + n * k : i;
-      Real uL[NV], uR[NV];
-      const int cl = i + n * (fi - 1), cr = i + n * fi;
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        if (fi == 0) {
-          uL[v] = GTR(2, v, fp, t);
-        } else {
-          Real s = Real(0);
-#pragma unroll
-          for (int qy = 0; qy < N; ++qy) s += T.lp[qy] * US(v, qx + N * qy + N * N * qz, cl);
-          uL[v] = s;
-        }
-        if (fi == n) {
-          uR[v] = GTR(3, v, fp, t);
-        } else {
-          Real s = Real(0);
-#pragma unroll
-          for (int qy = 0; qy < N; ++qy) s += T.lm[qy] * US(v, qx + N * qy + N * N * qz, cr);
-          uR[v] = s;
-        }
-      }
-      const int cg = fi == n ? cl : cr;
-      Real xi[D];
-      xi[0] = T.x[qx];
-      xi[1] = fi == n ? Real(1) : Real(-1);
-      if constexpr (D == 3) xi[2] = T.x[qz];
-      Real tg[D][D], Ja[D], Fh[NV];
-      tangents<D, Real>(&GS(0, cg), NCL, xi, tg);
-      contra_row<D, Real>(tg, 1, Ja);
-      lf_flux<D, Real>(uL, uR, Ja, gamma, Fh);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) fs[((v * NFP + fp) * (n + 1) + fi) * n + i] = Fh[v];
-    }
-    __syncthreads();
-    // ---------------------------------------------------- y volume + lift
-    for (int w = tid; w < NCL * NFP; w += nthr) {
-      const int c = w % NCL, fp = w / NCL;
-      const int i = c % n, j = c / n;
-      const int qx = fp % N, qz = fp / N;
-      Real F[N][NV];
-      const Real* Xc = &GS(0, c);
-      Real Jd[N];
-#pragma unroll
-      for (int qy = 0; qy < N; ++qy) {
-        Real u[NV];
-        const int q = qx + N * qy + N * N * qz;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) u[v] = US(v, q, c);
-        Real xi[D];
-        xi[0] = T.x[qx];
-        xi[1] = T.x[qy];
-        if constexpr (D == 3) xi[2] = T.x[qz];
-        Real tg[D][D], Ja[D], Fq[NV];
-        tangents<D, Real>(Xc, NCL, xi, tg);
-        contra_row<D, Real>(tg, 1, Ja);
-        flux_along<D, Real>(u, Ja, gamma - Real(1), Fq);
-        Jd[qy] = jacobian_det<D, Real>(tg);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) F[qy][v] = Fq[v];
-      }
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const Real fm = fs[((v * NFP + fp) * (n + 1) + j) * n + i];
-        const Real fpl = fs[((v * NFP + fp) * (n + 1) + j + 1) * n + i];
-#pragma unroll
-        for (int qy = 0; qy < N; ++qy) {
-          Real s = Real(0);
-#pragma unroll
-          for (int jj = 0; jj < N; ++jj) s += T.Sh[qy][jj] * F[jj][v];
-          const int q = qx + N * qy + N * N * qz;
-          Real r = RS(v, q, c) + s - T.lpw[qy] * fpl + T.lmw[qy] * fm;
-          if constexpr (D == 2) r = r / Jd[qy];
-          RS(v, q, c) = r;
-        }
-      }
-    }
-    __syncthreads();
-
-    if constexpr (D == 3) {
-      // ------------------------------------------- top halo trace of layer k
+      // ------------------------------------------------- epilogue
       for (int w = tid; w < NCL * NV; w += nthr) {
         const int c = w % NCL, v = w / NCL;
-        Real tr[NFP];
-        if (k == n - 1) {
+        Real a[M], t2[M];
 #pragma unroll
-          for (int fp = 0; fp < NFP; ++fp) tr[fp] = GTR(5, v, fp, c);
-        } else {
-          Real K[M];
+        for (int q = 0; q < Q; ++q) a[q] = RS(v, q, c);
+        apply_all<D, N, Real>(T.Vi, a, t2);  // a = modal L(U)
 #pragma unroll
-          for (int m = 0; m < M; ++m) K[m] = Ub[((size_t)v * M + m) * ustride + (k + 1) * NCL + c];
-          modal_trace<3, N, 2, Real>(T, K, -1, tr);
-        }
-#pragma unroll
-        for (int fp = 0; fp < NFP; ++fp) tb[(v * NFP + fp) * NCL + c] = tr[fp];
-      }
-      __syncthreads();
-      // ------------------------------------------- z volume + z faces
-      for (int w = tid; w < NCL * NFP; w += nthr) {
-        const int c = w % NCL, fp = w / NCL;
-        const int qx = fp % N, qy = fp / N;
-        Real F[N][NV];
-        Real Jd[N];
-        const Real* Xc = &GS(0, c);
-#pragma unroll
-        for (int qz = 0; qz < N; ++qz) {
-          Real u[NV];
-#pragma unroll
-          for (int v = 0; v < NV; ++v) u[v] = US(v, fp + NFP * qz, c);
-          const Real xi[3] = {T.x[qx], T.x[qy], T.x[qz]};
-          Real tg[3][3], Ja[3], Fq[NV];
-          tangents<3, Real>(Xc, NCL, xi, tg);
-          contra_row<3, Real>(tg, 2, Ja);
-          flux_along<3, Real>(u, Ja, gamma - Real(1), Fq);
-          Jd[qz] = tg[2][0] * Ja[0] + tg[2][1] * Ja[1] + tg[2][2] * Ja[2];
-#pragma unroll
-          for (int v = 0; v < NV; ++v) F[qz][v] = Fq[v];
-        }
-        // top face flux: own top trace vs the halo trace above
-        Real uL[NV], uR[NV], Fh[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          Real s = Real(0);
-#pragma unroll
-          for (int qz = 0; qz < N; ++qz) s += T.lp[qz] * US(v, fp + NFP * qz, c);
-          uL[v] = s;
-          uR[v] = tb[(v * NFP + fp) * NCL + c];
-        }
-        {
-          const Real xi[3] = {T.x[qx], T.x[qy], Real(1)};
-          Real tg[3][3], Ja[3];
-          tangents<3, Real>(Xc, NCL, xi, tg);
-          contra_row<3, Real>(tg, 2, Ja);
-          lf_flux<3, Real>(uL, uR, Ja, gamma, Fh);
-        }
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const Real fbot = fz[(v * NFP + fp) * NCL + c];
-#pragma unroll
-          for (int qz = 0; qz < N; ++qz) {
-            Real s = Real(0);
-#pragma unroll
-            for (int jj = 0; jj < N; ++jj) s += T.Sh[qz][jj] * F[jj][v];
-            const int q = fp + NFP * qz;
-            RS(v, q, c) = (RS(v, q, c) + s - T.lpw[qz] * Fh[v] + T.lmw[qz] * fbot) / Jd[qz];
+        for (int m = 0; m < M; ++m) {
+          const size_t gi = ((size_t)v * M + m) * ustride + cbase + c;
+          Real o;
+          if (A.mode == 1) {
+            o = a[m];
+          } else {
+            o = A.cb * (Ub[gi] + dt * a[m]);
+            if (A.ca != Real(0)) o += A.ca * Unb[gi];
           }
-          fz[(v * NFP + fp) * NCL + c] = Fh[v];
+          Ob[gi] = o;
+          a[m] = o;
         }
-      }
-      __syncthreads();
-    }
-
-    // ---------------------------------------------------- epilogue
-    for (int w = tid; w < NCL * NV; w += nthr) {
-      const int c = w % NCL, v = w / NCL;
-      Real a[M], t2[M];
+        if (A.last) {
+          apply_all<D, N, Real>(T.V, a, t2);
 #pragma unroll
-      for (int q = 0; q < Q; ++q) a[q] = RS(v, q, c);
-      apply_all<D, N, Real>(T.Vi, a, t2);  // a = modal L(U)
-#pragma unroll
-      for (int m = 0; m < M; ++m) {
-        const size_t gi = ((size_t)v * M + m) * ustride + cbase + c;
-        Real o;
-        if (A.mode == 1) {
-          o = a[m];
-        } else {
-          o = A.cb * (Ub[gi] + dt * a[m]);
-          if (A.ca != Real(0)) o += A.ca * Unb[gi];
+          for (int q = 0; q < Q; ++q) US(v, q, c) = a[q];
         }
-        Ob[gi] = o;
-        a[m] = o;
       }
       if (A.last) {
-        apply_all<D, N, Real>(T.V, a, t2);
+        __syncthreads();
+        for (int w = tid; w < NCL * Q; w += nthr) {
+          const int c = w % NCL, q = w / NCL;
+          Real u[NV];
 #pragma unroll
-        for (int q = 0; q < Q; ++q) US(v, q, c) = a[q];
+          for (int v = 0; v < NV; ++v) u[v] = US(v, q, c);
+          const Real ri = Real(1) / u[0];
+          Real ke = Real(0), sv = Real(0);
+#pragma unroll
+          for (int j = 0; j < D; ++j) {
+            ke += u[1 + j] * u[1 + j];
+            sv += fabs(u[1 + j]) * ri;
+          }
+          const Real p = gm1 * (u[D + 1] - Real(0.5) * ke * ri);
+          if (!(u[0] > Real(0)) || !(p > Real(0)) || !(p < Real(3.0e38))) {
+            bad = true;
+          } else {
+            const Real lam = sv + Real(D) * sqrt(gamma * p * ri);
+            const Real hv = A.hcell[(size_t)b * nc + cbase + c] / lam;
+            lam_min = hv < lam_min ? hv : lam_min;
+          }
+        }
       }
-    }
-    if (A.last) {
       __syncthreads();
-      const Real gm1 = gamma - Real(1);
-      for (int w = tid; w < NCL * Q; w += nthr) {
-        const int c = w % NCL, q = w / NCL;
-        Real u[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) u[v] = US(v, q, c);
-        const Real ri = Real(1) / u[0];
-        Real ke = Real(0), sv = Real(0);
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-          ke += u[1 + j] * u[1 + j];
-          sv += fabs(u[1 + j]) * ri;
-        }
-        const Real p = gm1 * (u[D + 1] - Real(0.5) * ke * ri);
-        if (!(u[0] > Real(0)) || !(p > Real(0)) || !(p < Real(3.0e38))) {
-          bad = true;
-        } else {
-          const Real lam = sv + Real(D) * sqrt(gamma * p * ri);
-          const Real hv = A.hcell[(size_t)b * nc + cbase + c] / lam;
-          lam_min = hv < lam_min ? hv : lam_min;
-        }
-      }
     }
-    __syncthreads();
   }
 #undef US
 #undef RS
 #undef GS
 #undef GTR
+#undef FX
+#undef FY
 
   if (A.last) {
     // block min of h/lambda -> one atomic per CTA
@@ -694,8 +782,58 @@ __global__ void __launch_bounds__(256) k_stage(const StageArgs<D, P, Real> A) {
   }
 }
 
-// ============================================================ guard kernel
-// One thread per (leaf, face, guard cell t, var): Sec. 3.5, Eqs. (15)-(17).
+// ============================================================ guard kernels
+// Sec. 3.5, Eqs. (15)-(17).  The stage kernel needs, for every block face,
+// the guard cell's trace at my face Gauss points in my frame; the ABI's
+// standalone fill needs the guard cells' modal coefficients in my frame.
+// Same-level and coarser neighbours: the trace (or the modes) is computed in
+// the neighbour's frame and scattered into my point (mode) order, so no
+// register array is indexed at run time.  Finer neighbours use k_guard_fine.
+
+// source-frame face point j -> my face point index, for my face axis a and
+// the neighbour's face axis b2 (orientation packed as in opi/osg)
+template <int D, int N>
+__device__ __forceinline__ int map_face_point(int j, int a, int b2, int pk) {
+  if constexpr (D == 2) {
+    const int t0 = 1 - a;  // my only tangential axis
+    const int q = j;       // source tangential index
+    return osg(pk, t0) > 0 ? q : N - 1 - q;
+  } else {
+    const int u0 = b2 == 0 ? 1 : 0;  // first source tangential axis
+    const int qu0 = j % N, qu1 = j / N;
+    const int t0 = a == 0 ? 1 : 0, t1 = a == 2 ? 1 : 2;   // my tangential axes
+    const int s0 = opi(pk, t0) == u0 ? qu0 : qu1;
+    const int s1 = opi(pk, t1) == u0 ? qu0 : qu1;
+    const int q0 = osg(pk, t0) > 0 ? s0 : N - 1 - s0;
+    const int q1 = osg(pk, t1) > 0 ? s1 : N - 1 - s1;
+    return q0 + N * q1;
+  }
+}
+
+// source mode ms (digits in the neighbour's frame) -> my mode and sign
+template <int D, int N>
+__device__ __forceinline__ int map_mode(int ms, int pk, float* sign) {
+  int k[3] = {0, 0, 0};
+  int r = ms;
+#pragma unroll
+  for (int u = 0; u < D; ++u) {
+    k[u] = r % N;
+    r /= N;
+  }
+  int m = 0, st = 1;
+  float sg = 1.f;
+#pragma unroll
+  for (int ax = 0; ax < D; ++ax) {
+    const int ka = k[opi(pk, ax)];
+    m += ka * st;
+    st *= N;
+    if (osg(pk, ax) < 0 && (ka & 1)) sg = -sg;
+  }
+  *sign = sg;
+  return m;
+}
+
+// one thread per (leaf, face, guard cell t, var); finer faces are skipped
 template <int D, int P, typename Real>
 __global__ void __launch_bounds__(128) k_guard(const GuardArgs<D, P, Real> A) {
   constexpr int N = P + 1, NV = D + 2, M = ipow(N, D), NFP = ipow(N, D - 1);
@@ -710,148 +848,190 @@ __global__ void __launch_bounds__(128) k_guard(const GuardArgs<D, P, Real> A) {
   const int f = (int)((w / ((size_t)nt * NV)) % (2 * D));
   const int b = (int)(w / ((size_t)nt * NV * 2 * D));
   const int a = f >> 1, s = f & 1;
+  const int kind = A.kind[b * 2 * D + f];
+  if (kind == 2) return;
   const auto& T = A.T;
-
-  // my tangential cell coordinates
   int g[3] = {0, 0, 0};
   {
-    int tt = t, j = 0;
+    int j = 0;
     for (int ax = 0; ax < D; ++ax) {
       if (ax == a) continue;
-      g[ax] = j == 0 ? (tt % n) : (tt / n);
+      g[ax] = j == 0 ? (t % n) : (t / n);
       ++j;
     }
   }
-  const int kind = A.kind[b * 2 * D + f];
   const int pk = A.orient[b * 2 * D + f];
-  Real K[M];
-
-  auto cell_index = [&](const int* h) {
+  auto load = [&](int leaf, const int* h, Real* dst) {
     int c = 0, st = 1;
     for (int ax = 0; ax < D; ++ax) {
       c += h[ax] * st;
       st *= n;
     }
-    return c;
-  };
-  auto load = [&](int leaf, int cell, Real* dst) {
-    const Real* src = A.U + (size_t)leaf * NV * M * nc + (size_t)v * M * nc + cell;
+    const Real* src = A.U + ((size_t)leaf * NV + v) * M * nc + c;
 #pragma unroll
     for (int m = 0; m < M; ++m) dst[m] = src[(size_t)m * nc];
   };
-  // source (neighbour frame) modal -> my frame: my k_a = source k_{pi[a]}
-  auto rotate = [&](const Real* src) {
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-      int ms = 0;
-      Real sg = Real(1);
-      int rem = m;
-#pragma unroll
-      for (int ax = 0; ax < D; ++ax) {
-        const int ka = rem % N;
-        rem /= N;
-        const int pa = opi(pk, ax);
-        ms += ka * (pa == 0 ? 1 : (pa == 1 ? N : N * N));
-        if (osg(pk, ax) < 0 && (ka & 1)) sg = -sg;
-      }
-      K[m] = sg * src[ms];
-    }
-  };
+  Real* out_modal = A.out + (((size_t)b * 2 * D + f) * NV + v) * M * nt + t;
+  Real* out_trace = A.out + (((size_t)b * 2 * D + f) * NV + v) * NFP * nt + t;
 
-  if (kind == 3) {  // outflow: mirror of my own face cell
+  if (kind == 3) {  // outflow: the guard is the mirror image of my face cell
     int h[3] = {g[0], g[1], g[2]};
     h[a] = s ? n - 1 : 0;
-    load(b, cell_index(h), K);
+    Real K[M];
+    load(b, h, K);
+    if (A.mode == 0) {
 #pragma unroll
-    for (int m = 0; m < M; ++m) {
-      int ka = m;
-      for (int u = 0; u < a; ++u) ka /= N;
-      ka %= N;
-      if (ka & 1) K[m] = -K[m];
+      for (int m = 0; m < M; ++m) {
+        int ka = m;
+        for (int u = 0; u < a; ++u) ka /= N;
+        out_modal[(size_t)m * nt] = (ka % N) & 1 ? -K[m] : K[m];
+      }
+    } else {
+      Real tr[NFP];
+      modal_trace_rt<D, N, Real>(T, K, a, s ? +1 : -1, tr);
+#pragma unroll
+      for (int fp = 0; fp < NFP; ++fp) out_trace[(size_t)fp * nt] = tr[fp];
     }
-  } else {
-    const int b2 = opi(pk, a);
-    const int s2 = osg(pk, a) > 0 ? 1 - s : s;
-    int h[3] = {0, 0, 0};
-    if (kind == 0 || kind == 2) {
-      for (int ax = 0; ax < D; ++ax) {
-        if (ax == a) continue;
-        h[opi(pk, ax)] = osg(pk, ax) > 0 ? g[ax] : n - 1 - g[ax];
-      }
-      h[b2] = s2 == 0 ? 0 : n - 1;
+    return;
+  }
+  const int b2 = opi(pk, a);
+  const int s2 = osg(pk, a) > 0 ? 1 - s : s;
+  int h[3] = {0, 0, 0};
+  Real S[M];
+  if (kind == 0) {
+    for (int ax = 0; ax < D; ++ax) {
+      if (ax == a) continue;
+      h[opi(pk, ax)] = osg(pk, ax) > 0 ? g[ax] : n - 1 - g[ax];
     }
-    if (kind == 0) {
-      Real S[M];
-      load(A.nbr[(b * 2 * D + f) * 4], cell_index(h), S);
-      rotate(S);
-    } else if (kind == 1) {
-      const int qb = A.qbits[b];
-      int e[3] = {0, 0, 0};
-      for (int ax = 0; ax < D; ++ax) {
-        if (ax == a) continue;
-        const int G = ((qb >> ax) & 1) * n + g[ax];
-        const int hh = G >> 1, ee = G & 1;
-        h[opi(pk, ax)] = osg(pk, ax) > 0 ? hh : n - 1 - hh;
-        e[opi(pk, ax)] = osg(pk, ax) > 0 ? ee : 1 - ee;
-      }
-      h[b2] = s2 == 0 ? 0 : n - 1;
-      e[b2] = s2 == 0 ? 0 : 1;
-      Real S[M], S2[M];
-      load(A.nbr[(b * 2 * D + f) * 4], cell_index(h), S);
-      // split along each source axis (Eqs. (11)-(12) in tensor form)
-      if (e[0]) apply_axis<D, N, 0, Real>(T.Sp, S, S2);
-      else apply_axis<D, N, 0, Real>(T.Sm, S, S2);
-      if constexpr (D >= 2) {
-        if (e[1]) apply_axis<D, N, 1, Real>(T.Sp, S2, S);
-        else apply_axis<D, N, 1, Real>(T.Sm, S2, S);
-      }
-      if constexpr (D == 3) {
-        if (e[2]) apply_axis<D, N, 2, Real>(T.Sp, S, S2);
-        else apply_axis<D, N, 2, Real>(T.Sm, S, S2);
+    h[b2] = s2 == 0 ? 0 : n - 1;
+    load(A.nbr[(b * 2 * D + f) * 4], h, S);
+  } else {  // coarser: split of Eqs. (11)-(12) in tensor form, neighbour frame
+    const int qb = A.qbits[b];
+    int e[3] = {0, 0, 0};
+    for (int ax = 0; ax < D; ++ax) {
+      if (ax == a) continue;
+      const int G = ((qb >> ax) & 1) * n + g[ax];
+      const int hh = G >> 1, ee = G & 1;
+      h[opi(pk, ax)] = osg(pk, ax) > 0 ? hh : n - 1 - hh;
+      e[opi(pk, ax)] = osg(pk, ax) > 0 ? ee : 1 - ee;
+    }
+    h[b2] = s2 == 0 ? 0 : n - 1;
+    e[b2] = s2 == 0 ? 0 : 1;
+    Real S2[M];
+    load(A.nbr[(b * 2 * D + f) * 4], h, S);
+    if (e[0]) apply_axis<D, N, 0, Real>(T.Sp, S, S2);
+    else apply_axis<D, N, 0, Real>(T.Sm, S, S2);
+    if (e[1]) apply_axis<D, N, 1, Real>(T.Sp, S2, S);
+    else apply_axis<D, N, 1, Real>(T.Sm, S2, S);
+    if constexpr (D == 3) {
+      if (e[2]) apply_axis<D, N, 2, Real>(T.Sp, S, S2);
+      else apply_axis<D, N, 2, Real>(T.Sm, S, S2);
 #pragma unroll
-        for (int m = 0; m < M; ++m) S[m] = S2[m];
-      }
-      rotate(S);
-    } else {  // kind 2: combine of 2^D fine cells, operator already rotated
-      int sub = 0, j = 0;
-      for (int ax = 0; ax < D; ++ax) {
-        if (ax == a) continue;
-        if (g[ax] >= n / 2) sub |= 1 << j;
-        ++j;
-      }
-      const int fine = A.nbr[(b * 2 * D + f) * 4 + sub];
-      int cN[3] = {0, 0, 0};
-      for (int ax = 0; ax < D; ++ax) cN[ax] = (2 * h[ax]) / n;
-      const Real* op = A.cop + (size_t)(A.copoff[b * 2 * D + f] + t) * M * ((1 << D) * M);
-#pragma unroll
-      for (int m = 0; m < M; ++m) K[m] = Real(0);
-      for (int e = 0; e < (1 << D); ++e) {
-        int hc[3] = {0, 0, 0};
-        for (int ax = 0; ax < D; ++ax) hc[ax] = 2 * h[ax] + ((e >> ax) & 1) - cN[ax] * n;
-        Real S[M];
-        load(fine, cell_index(hc), S);
-        for (int m = 0; m < M; ++m) {
-          const Real* row = op + (size_t)m * (1 << D) * M + e * M;
-          Real acc = K[m];
-#pragma unroll
-          for (int kk = 0; kk < M; ++kk) acc += row[kk] * S[kk];
-          K[m] = acc;
-        }
-      }
+      for (int m = 0; m < M; ++m) S[m] = S2[m];
     }
   }
-
   if (A.mode == 0) {
-    Real* o = A.out + ((((size_t)b * 2 * D + f) * NV + v) * M) * nt + t;
 #pragma unroll
-    for (int m = 0; m < M; ++m) o[(size_t)m * nt] = K[m];
+    for (int ms = 0; ms < M; ++ms) {
+      float sg;
+      const int m = map_mode<D, N>(ms, pk, &sg);
+      out_modal[(size_t)m * nt] = sg < 0 ? -S[ms] : S[ms];
+    }
   } else {
+    // trace on the neighbour's face (b2, s2), then into my point order
     Real tr[NFP];
-    // the guard cell touches me with its face on the side opposite to s
-    modal_trace_rt<D, N, Real>(T, K, a, s ? -1 : +1, tr);
-    Real* o = A.out + ((((size_t)b * 2 * D + f) * NV + v) * NFP) * nt + t;
+    modal_trace_rt<D, N, Real>(T, S, b2, s2 ? +1 : -1, tr);
 #pragma unroll
-    for (int fp = 0; fp < NFP; ++fp) o[(size_t)fp * nt] = tr[fp];
+    for (int j = 0; j < NFP; ++j) out_trace[(size_t)map_face_point<D, N>(j, a, b2, pk) * nt] = tr[j];
+  }
+}
+
+// Finer neighbours (Eqs. (13)-(14)): one warp per (finer face, guard cell t,
+// var); the 2^D x M fine-cell modes are staged in shared memory and lane m
+// forms output mode m with the precomputed, already rotated operator.
+template <int D, int P, typename Real>
+__global__ void __launch_bounds__(128) k_guard_fine(const GuardArgs<D, P, Real> A) {
+  constexpr int N = P + 1, NV = D + 2, M = ipow(N, D), NFP = ipow(N, D - 1);
+  constexpr int KC = (1 << D) * M;
+  __shared__ Real stage[4][KC + M];
+  const int n = A.n;
+  const int nt = D == 3 ? n * n : n;
+  const int nc = D == 3 ? n * n * n : n * n;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const size_t item = (size_t)blockIdx.x * 4 + wib;
+  if (item >= (size_t)A.nfine * nt * NV) return;
+  const int t = (int)(item % nt);
+  const int v = (int)((item / nt) % NV);
+  const int bf = A.fine_list[item / ((size_t)nt * NV)];
+  const int b = bf / (2 * D), f = bf % (2 * D);
+  const int a = f >> 1, s = f & 1;
+  const int pk = A.orient[bf];
+  const auto& T = A.T;
+  int g[3] = {0, 0, 0};
+  {
+    int j = 0;
+    for (int ax = 0; ax < D; ++ax) {
+      if (ax == a) continue;
+      g[ax] = j == 0 ? (t % n) : (t / n);
+      ++j;
+    }
+  }
+  const int b2 = opi(pk, a);
+  const int s2 = osg(pk, a) > 0 ? 1 - s : s;
+  int h[3] = {0, 0, 0}, sub = 0, j = 0;
+  for (int ax = 0; ax < D; ++ax) {
+    if (ax == a) continue;
+    h[opi(pk, ax)] = osg(pk, ax) > 0 ? g[ax] : n - 1 - g[ax];
+    if (g[ax] >= n / 2) sub |= 1 << j;
+    ++j;
+  }
+  h[b2] = s2 == 0 ? 0 : n - 1;
+  const int fine = A.nbr[bf * 4 + sub];
+  Real* src = stage[wib];
+  Real* K = stage[wib] + KC;
+  for (int i = lane; i < KC; i += 32) {
+    const int e = i / M, k = i % M;
+    int c = 0, st = 1;
+    for (int ax = 0; ax < D; ++ax) {
+      const int cN = (2 * h[ax]) / n;
+      c += (2 * h[ax] + ((e >> ax) & 1) - cN * n) * st;
+      st *= n;
+    }
+    src[i] = A.U[(((size_t)fine * NV + v) * M + k) * nc + c];
+  }
+  __syncwarp();
+  const Real* op = A.cop + (size_t)(A.copoff[bf] + t) * KC * M;
+  for (int m = lane; m < M; m += 32) {
+    Real acc = Real(0);
+    for (int i = 0; i < KC; ++i) acc += op[(size_t)i * M + m] * src[i];
+    if (A.mode == 0) A.out[((((size_t)b * 2 * D + f) * NV + v) * M + m) * nt + t] = acc;
+    K[m] = acc;
+  }
+  if (A.mode == 0) return;
+  __syncwarp();
+  // trace of the guard cell (my frame) on its face touching me: xi_a = -+1
+  const int side = s ? -1 : +1;
+  for (int fp = lane; fp < NFP; fp += 32) {
+    int qt[3] = {0, 0, 0}, jj = 0, r = fp;
+    for (int ax = 0; ax < D; ++ax) {
+      if (ax == a) continue;
+      qt[ax] = r % N;
+      r /= N;
+      ++jj;
+    }
+    Real acc = Real(0);
+    for (int m = 0; m < M; ++m) {
+      Real ph = Real(1);
+      int rm = m;
+      for (int ax = 0; ax < D; ++ax) {
+        const int k = rm % N;
+        rm /= N;
+        if (ax == a) ph *= (side > 0 || (k & 1) == 0) ? Real(1) : Real(-1);
+        else ph *= T.V[qt[ax]][k];
+      }
+      acc += ph * K[m];
+    }
+    A.out[((((size_t)b * 2 * D + f) * NV + v) * NFP + fp) * nt + t] = acc;
   }
 }
 

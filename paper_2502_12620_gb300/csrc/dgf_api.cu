@@ -114,7 +114,9 @@ struct dgf_forest {
     size_t bytes = 0;
   };
   Buf U[3], geo, geo64, hcell, gtr, gmod, cop, kind, nbr, orient, qbits, copoff, part, scal, tot,
-      dtout, nodal;
+      dtout, nodal, fine, affine, ameta;
+  int nfine = 0;
+  int slots = 0;
   bool have_state = false;
   bool graph_valid = false;
   cudaGraphExec_t graph = nullptr;
@@ -277,18 +279,52 @@ dgf_status build_device(dgf_forest* f) {
     }
   }
 
+  // affine blocks: every cell a congruent parallelogram/parallelepiped ->
+  // constant J dxi/dx rows and 1/J per block
+  std::vector<unsigned char> affine(L, 0);
+  std::vector<double> ameta((size_t)L * (d * d + 1), 0.0);
+  for (int64_t i = 0; i < L; ++i) {
+    const std::vector<double>& C = coef[i];
+    double scale = 0.0;
+    for (int k = d; k < (1 << d) * d; ++k)
+      for (int c = 0; c < nc; ++c) scale = std::max(scale, std::fabs(C[(size_t)k * nc + c]));
+    bool ok = scale > 0.0;
+    for (int cm = 1; cm < (1 << d) && ok; ++cm) {
+      const bool linear = (cm & (cm - 1)) == 0;
+      for (int j = 0; j < d && ok; ++j) {
+        const double* row = &C[((size_t)cm * d + j) * nc];
+        for (int c = 0; c < nc && ok; ++c) {
+          if (!linear && std::fabs(row[c]) > 1e-13 * scale) ok = false;
+          if (linear && std::fabs(row[c] - row[0]) > 1e-13 * scale) ok = false;
+        }
+      }
+    }
+    if (!ok) continue;
+    double cc[24], A[9], Ja[9], xi[3] = {0, 0, 0};
+    for (int k = 0; k < (1 << d) * d; ++k) cc[k] = C[(size_t)k * nc];
+    eval_map(d, cc, xi, nullptr, A);
+    const double J = det_and_cofactor(d, A, Ja);
+    if (!(J > 0)) continue;
+    affine[i] = 1;
+    for (int k = 0; k < d * d; ++k) ameta[(size_t)i * (d * d + 1) + k] = Ja[k];
+    ameta[(size_t)i * (d * d + 1) + d * d] = 1.0 / J;
+  }
+
   // combine operators for every finer-neighbour guard cell (Eqs. (13)-(14),
   // J-weighted, integrals by each child's Gauss rule), rotated into my frame
   const int nt = f->nt;
   std::vector<double> cop;
   int64_t nops = 0;
   const int KC = (1 << d) * M;
+  std::vector<int> fine_list;
   for (int64_t i = 0; i < L; ++i)
     for (int fc = 0; fc < nf; ++fc)
       if (kind[i * nf + fc] == kFiner) {
         copoff[i * nf + fc] = (int)nops;
         nops += nt;
+        fine_list.push_back((int)(i * nf + fc));
       }
+  f->nfine = (int)fine_list.size();
   cop.assign((size_t)nops * M * KC, 0.0);
   for (int64_t i = 0; i < L; ++i) {
     for (int fc = 0; fc < nf; ++fc) {
@@ -366,7 +402,7 @@ dgf_status build_device(dgf_forest* f) {
             ms += ka * st;
             if (o.sg[ax] < 0 && (ka & 1)) sg = -sg;
           }
-          for (int k = 0; k < KC; ++k) dst[(size_t)m * KC + k] = sg * RHS[(size_t)ms * KC + k];
+          for (int k = 0; k < KC; ++k) dst[(size_t)k * M + m] = sg * RHS[(size_t)ms * KC + k];
         }
       }
     }
@@ -376,14 +412,17 @@ dgf_status build_device(dgf_forest* f) {
   DeviceGuard dg(f->device);
   dgf_status st;
   if ((st = upload(f, f->kind, kind)) || (st = upload(f, f->nbr, nbr)) || (st = upload(f, f->orient, orient)) ||
-      (st = upload(f, f->qbits, qbits)) || (st = upload(f, f->copoff, copoff)) || (st = upload(f, f->geo64, geo64)))
+      (st = upload(f, f->qbits, qbits)) || (st = upload(f, f->copoff, copoff)) || (st = upload(f, f->geo64, geo64)) ||
+      (st = upload(f, f->fine, fine_list)))
     return st;
+  if ((st = upload(f, f->affine, affine))) return st;
   if (f->precision == DGF_FP64) {
-    if ((st = upload(f, f->geo, geo64)) || (st = upload(f, f->hcell, hcell)) || (st = upload(f, f->cop, cop)))
+    if ((st = upload(f, f->geo, geo64)) || (st = upload(f, f->hcell, hcell)) || (st = upload(f, f->cop, cop)) ||
+        (st = upload(f, f->ameta, ameta)))
       return st;
   } else {
     if ((st = upload(f, f->geo, convert<float>(geo64))) || (st = upload(f, f->hcell, convert<float>(hcell))) ||
-        (st = upload(f, f->cop, convert<float>(cop))))
+        (st = upload(f, f->cop, convert<float>(cop))) || (st = upload(f, f->ameta, convert<float>(ameta))))
       return st;
   }
   const size_t sbytes = (size_t)L * f->nv * M * nc * f->esize;
@@ -392,15 +431,30 @@ dgf_status build_device(dgf_forest* f) {
   if (!ensure(f, f->gtr, (size_t)L * nf * f->nv * f->NFP * nt * f->esize) ||
       !ensure(f, f->part, (size_t)L * nc * f->nv * sizeof(double)))
     return fail(DGF_ENOMEM, "scratch allocation failed");
-  // parallel split of a block into z-chunks when the forest is small
-  if (d == 3) {
+  // resident stage CTAs, and the z-chunk length that balances the
+  // persistent CTAs best (a chunk costs its layers plus ~0.3 layer of halo)
+  {
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device);
-    int chunks = (int)std::min<int64_t>(n, std::max<int64_t>(1, (2 * sms + L - 1) / L));
-    f->zchunk = (n + chunks - 1) / chunks;
-    if (const char* zc = getenv("DGF_ZCHUNK")) f->zchunk = std::max(1, std::min(n, atoi(zc)));
-  } else {
+    int occ = 0;
+    if (d == 2) occ = f->precision == DGF_FP64 ? stage_occupancy<2, double>(f->p, n) : stage_occupancy<2, float>(f->p, n);
+    else occ = f->precision == DGF_FP64 ? stage_occupancy<3, double>(f->p, n) : stage_occupancy<3, float>(f->p, n);
+    f->slots = occ * sms;
     f->zchunk = 1;
+    if (d == 3 && f->slots > 0) {
+      double best = 1e300;
+      for (int z = n; z >= 1; z /= 2) {
+        const int64_t items = L * ((n + z - 1) / z);
+        const double rounds = (double)((items + f->slots - 1) / f->slots);
+        const double cost = rounds * (z + 0.3);
+        if (cost < best - 1e-9) {
+          best = cost;
+          f->zchunk = z;
+        }
+        if (z == 1) break;
+      }
+      if (const char* zc = getenv("DGF_ZCHUNK")) f->zchunk = std::max(1, std::min(n, atoi(zc)));
+    }
   }
   if (f->graph) {
     cudaGraphExecDestroy(f->graph);
@@ -416,7 +470,9 @@ RtStage stage_args(dgf_forest* f, int src, int dst, double ca, double cb, int mo
   r.nL = (int)f->nL;
   r.n = f->n;
   r.zchunk = f->zchunk;
-  r.threads = 256;
+  r.slots = f->slots;
+  r.affine = (const unsigned char*)f->affine.ptr;
+  r.ameta = f->ameta.ptr;
   r.U = f->U[src].ptr;
   r.Un = f->U[0].ptr;
   r.Uout = f->U[dst].ptr;
@@ -449,6 +505,8 @@ RtGuard guard_args(dgf_forest* f, int src, void* out, int mode) {
   r.qbits = (const int*)f->qbits.ptr;
   r.copoff = (const int*)f->copoff.ptr;
   r.cop = f->cop.ptr;
+  r.fine_list = (const int*)f->fine.ptr;
+  r.nfine = f->nfine;
   r.T = f->tab;
   return r;
 }
@@ -660,7 +718,7 @@ dgf_status dgf_forest_destroy(dgf_forest* f) {
     }
     dgf_forest::Buf* bufs[] = {&f->U[0], &f->U[1], &f->U[2], &f->geo, &f->geo64, &f->hcell, &f->gtr,
                                &f->gmod, &f->cop, &f->kind, &f->nbr, &f->orient, &f->qbits, &f->copoff,
-                               &f->part, &f->scal, &f->tot, &f->dtout, &f->nodal};
+                               &f->part, &f->scal, &f->tot, &f->dtout, &f->nodal, &f->fine, &f->affine, &f->ameta};
     for (auto* b : bufs) dev_free(f, *b);
     if (f->own_stream && f->stream) cudaStreamDestroy(f->stream);
   }

@@ -29,17 +29,37 @@ static Tab<N, Real> make_tab(const RtTables& r) {
 }
 
 template <int D, int P, typename Real>
+static int stage_blocks_per_sm(int n) {
+  const size_t smem = stage_smem<D, P, Real>(n);
+  int dev = 0, maxs = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem + 1024 > (size_t)maxs) return 0;
+  if (cudaFuncSetAttribute(k_stage<D, P, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage<D, P, Real>, StageCfg<P, Real>::NT, smem) !=
+      cudaSuccess)
+    return 0;
+  return nb;
+}
+
+template <int D, int P, typename Real>
 static cudaError_t stage_p(const RtStage& r, cudaStream_t s) {
   StageArgs<D, P, Real> a;
   a.nL = r.nL;
   a.n = r.n;
   a.zchunk = r.zchunk;
+  a.nchunks = D == 3 ? (r.n + r.zchunk - 1) / r.zchunk : 1;
   a.U = (const Real*)r.U;
   a.Un = (const Real*)r.Un;
   a.Uout = (Real*)r.Uout;
   a.geo = (const Real*)r.geo;
   a.gtr = (const Real*)r.gtr;
   a.hcell = (const Real*)r.hcell;
+  a.affine = r.affine;
+  a.ameta = (const Real*)r.ameta;
   a.dtp = r.dtp;
   a.lam_bits = r.lam_bits;
   a.status = r.status;
@@ -50,16 +70,10 @@ static cudaError_t stage_p(const RtStage& r, cudaStream_t s) {
   a.last = r.last;
   a.T = make_tab<P + 1, Real>(r.T);
   const size_t smem = stage_smem<D, P, Real>(r.n);
-  int dev = 0, maxs = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (smem + 512 > (size_t)maxs) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(k_stage<D, P, Real>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const int nchunks = D == 3 ? (r.n + r.zchunk - 1) / r.zchunk : 1;
-  dim3 grid(r.nL, nchunks);
-  k_stage<D, P, Real><<<grid, r.threads, smem, s>>>(a);
+  if (r.slots <= 0) return cudaErrorInvalidConfiguration;
+  const int items = a.nL * a.nchunks;
+  const int grid = items < r.slots ? items : r.slots;
+  k_stage<D, P, Real><<<grid, StageCfg<P, Real>::NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -77,11 +91,17 @@ static cudaError_t guard_p(const RtGuard& r, cudaStream_t s) {
   a.qbits = r.qbits;
   a.copoff = r.copoff;
   a.cop = (const Real*)r.cop;
+  a.fine_list = r.fine_list;
+  a.nfine = r.nfine;
   a.T = make_tab<P + 1, Real>(r.T);
   const int nt = D == 3 ? r.n * r.n : r.n;
   const size_t total = (size_t)r.nL * 2 * D * nt * (D + 2);
   const int th = 128;
   k_guard<D, P, Real><<<(unsigned)((total + th - 1) / th), th, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || r.nfine == 0) return e;
+  const size_t warps = (size_t)r.nfine * nt * (D + 2);
+  k_guard_fine<D, P, Real><<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -155,6 +175,16 @@ static cudaError_t totals_p(const RtMisc& r, cudaStream_t s) {
     constexpr int D = DIM;                                                                  \
     using Real = REAL;                                                                      \
     DGF_DISPATCH_P(totals_p, r, s)                                                          \
+  }                                                                                         \
+  template <>                                                                               \
+  int stage_occupancy<DIM, REAL>(int p, int n) {                                            \
+    switch (p) {                                                                            \
+      case 0: return stage_blocks_per_sm<DIM, 0, REAL>(n);                                  \
+      case 1: return stage_blocks_per_sm<DIM, 1, REAL>(n);                                  \
+      case 2: return stage_blocks_per_sm<DIM, 2, REAL>(n);                                  \
+      case 3: return stage_blocks_per_sm<DIM, 3, REAL>(n);                                  \
+    }                                                                                       \
+    return 0;                                                                               \
   }                                                                                         \
   template <>                                                                               \
   size_t stage_smem_bytes<DIM, REAL>(int p, int n) {                                        \

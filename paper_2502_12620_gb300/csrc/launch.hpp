@@ -14,13 +14,15 @@ struct RtTables {
 };
 
 struct RtStage {
-  int p, nL, n, zchunk, threads;
+  int p, nL, n, zchunk, slots;
   const void* U;
   const void* Un;
   void* Uout;
   const void* geo;
   const void* gtr;
   const void* hcell;
+  const unsigned char* affine;
+  const void* ameta;
   const double* dtp;
   unsigned long long* lam_bits;
   int* status;
@@ -39,6 +41,8 @@ struct RtGuard {
   const int* qbits;
   const int* copoff;
   const void* cop;
+  const int* fine_list;
+  int nfine;
   RtTables T;
 };
 
@@ -70,5 +74,8 @@ template <int D, typename Real>
 cudaError_t launch_totals(const RtMisc& r, cudaStream_t s);
 template <int D, typename Real>
 size_t stage_smem_bytes(int p, int n);
+// resident stage CTAs per SM (0: does not fit)
+template <int D, typename Real>
+int stage_occupancy(int p, int n);
 
 }  // namespace dgf
