@@ -8,19 +8,23 @@
 //   (split S) and finer (combine C) neighbours, all rotated into the
 //   receiving block's frame.
 //
-// How (GB300 design, not the paper's): the state is stored modally
-// (tensor Legendre, SoA [leaf][var][mode][cell]); inside a CTA one layer of
-// a block is converted to nodal values at the (p+1)^d Gauss points, which
-// makes the (p+1)-point mass matrix diagonal (M = V^T diag(wJ) V, so
-// V M^{-1} = diag(1/(wJ)) V^{-T}) and turns the volume and face integrals
-// into 1D line operations (weak derivative Sh, boundary lifts l(+-1)/w).
+// How (GB300 design, not the paper's): on the device the state is held as
+// values at the (p+1)^d Gauss points (SoA [leaf][var][point][cell]); the
+// modal coefficients of the C ABI are converted at the boundary (u = V K).
+// With the (p+1)-point rule the mass matrix is M = V^T diag(wJ) V, so
+// V M^{-1} = diag(1/(wJ)) V^{-T}: the inverse mass is diagonal and the
+// volume and face integrals become 1D line operations (weak derivative Sh,
+// boundary lifts l(+-1)/w).  Rotations map Gauss points onto Gauss points,
+// split and combine become small nodal operators.
 // The residual is accumulated in shared memory by directional sweeps; every
 // interior face flux is computed once; the stage combination and, on the
 // last stage, the CFL minimum are fused into the epilogue.
 #pragma once
 
-#include <cstdint>
 #include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
 
 namespace dgf {
 
@@ -40,8 +44,10 @@ struct Tab {
   Real lmw[N];     // l_q(-1) / w_q
   Real lp[N];      // l_q(+1)
   Real lm[N];      // l_q(-1)
-  Real Sm[N][N];   // split to the lower child [l][k]
-  Real Sp[N][N];   // split to the upper child [l][k]
+  Real Sm[N][N];   // split to the lower child [l][k] (modal)
+  Real Sp[N][N];   // split to the upper child [l][k] (modal)
+  Real Snm[N][N];  // nodal split: Snm[i][j] = l_j((x_i - 1)/2), lower child
+  Real Snp[N][N];  // nodal split: Snp[i][j] = l_j((x_i + 1)/2), upper child
 };
 
 // Decoded orientation of a (leaf, face): pi[a] in bits 2a..2a+1, sign bit
@@ -81,48 +87,6 @@ __device__ __forceinline__ void apply_all(const Real (&A)[N][N], Real* a, Real* 
 #pragma unroll
     for (int i = 0; i < ipow(N, D); ++i) a[i] = b[i];
   }
-}
-
-// Trace of a modal cell polynomial on face (AX, side): collapse along AX with
-// P_k(+1) = 1 or P_k(-1) = (-1)^k, then nodal values at the face Gauss points
-// (tangential axes in increasing order).  out has N^(D-1) entries.
-template <int D, int N, int AX, typename Real>
-__device__ __forceinline__ void modal_trace(const Tab<N, Real>& T, const Real* K, int side,
-                                            Real* out) {
-  constexpr int M = ipow(N, D);
-  constexpr int MF = ipow(N, D - 1);
-  constexpr int S = ipow(N, AX);
-  Real c[MF];
-#pragma unroll
-  for (int f = 0; f < MF; ++f) {
-    // f enumerates the tangential multi-index (axes != AX in increasing order)
-    const int lo = f % S;          // axes below AX
-    const int hi = f / S;          // axes above AX
-    const int base = lo + hi * S * N;
-    Real acc = Real(0);
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const Real sgn = (side > 0 || (k & 1) == 0) ? Real(1) : Real(-1);
-      acc += sgn * K[base + k * S];
-    }
-    c[f] = acc;
-  }
-  (void)M;
-  if constexpr (D == 2) {
-    apply_axis<1, N, 0, Real>(T.V, c, out);
-  } else {
-    Real tmp[MF];
-    apply_axis<2, N, 0, Real>(T.V, c, tmp);
-    apply_axis<2, N, 1, Real>(T.V, tmp, out);
-  }
-}
-
-template <int D, int N, typename Real>
-__device__ __forceinline__ void modal_trace_rt(const Tab<N, Real>& T, const Real* K, int axis,
-                                               int side, Real* out) {
-  if (axis == 0) modal_trace<D, N, 0, Real>(T, K, side, out);
-  else if (axis == 1) modal_trace<D, N, 1, Real>(T, K, side, out);
-  else if constexpr (D == 3) modal_trace<D, N, 2, Real>(T, K, side, out);
 }
 
 // --------------------------------------------------------------- geometry
@@ -242,6 +206,10 @@ struct StageArgs {
   const Real* __restrict__ hcell;  // [b][cell]
   const unsigned char* __restrict__ affine;  // [b] 1 if every cell has the same constant metric
   const Real* __restrict__ ameta;  // [b][D*D+1]: rows of J dxi/dx, then 1/J
+  const int* __restrict__ kind;    // [b][f] neighbour kind
+  const int* __restrict__ nbr;     // [b][f][4]
+  const int* __restrict__ orient;  // [b][f] packed decoded orientation
+  const int* __restrict__ qbits;   // [b] pos & 1 bits
   const double* __restrict__ dtp;
   unsigned long long* lam_bits;
   int* status;
@@ -274,170 +242,231 @@ struct StageCfg {
   static constexpr int MINB = (sizeof(Real) == 4 && P <= 2) ? 2 : 1;
 };
 
-// shared-memory footprint of the stage kernel (bytes)
+// shared-memory footprint of the stage kernel (bytes): nodal layer, residual
+// layer, x- and y-face fluxes, carried z-face flux
 template <int D, int P, typename Real>
 __host__ __device__ constexpr size_t stage_smem(int n) {
   constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
-  constexpr int NG = ((1 << D) - 1) * D;
   const size_t ncl = (size_t)n * n;
-  size_t us = NV * Q * ncl, rs = us;
-  size_t fs = (size_t)NV * NFP * (n + 1) * n;
+  size_t us = NV * Q * ncl;
+  size_t rs = us;
+  size_t fx = (size_t)NV * NFP * (n + 1) * n, fy = fx;
   size_t fz = D == 3 ? (size_t)NV * NFP * ncl : 0;
-  size_t gs = (size_t)NG * ncl;
-  return (us + rs + fs + fz + gs) * sizeof(Real);
+  return (us + rs + fx + fy + fz) * sizeof(Real);
 }
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-// metric of one cell: affine blocks use block constants, curvilinear cells
-// their trilinear coefficients (held in registers by the caller)
-template <int D, typename Real>
-struct CellMetric {
-  bool aff;
-  const Real* am;  // shared: rows of J dxi/dx, then 1/J
-  const Real* X;   // shared: trilinear coefficients of the cell, stride ncl
-  int stride;
-  __device__ __forceinline__ void load(bool affine, const Real* amsh, const Real* gs, int ncl, int c) {
-    aff = affine;
-    am = amsh;
-    X = gs + c;
-    stride = ncl;
-  }
-  __device__ __forceinline__ void row(const Real* xi, int dir, Real (&Ja)[D]) const {
-    if (aff) {
+// Metric along a line in direction DIR (coordinate s = xi_DIR) at fixed
+// transverse reference coordinates: for a (bi/tri)linear map the tangents
+// x_a (a != DIR) are affine in s and x_DIR is constant, so
+//   J dxi_DIR/dx (s) = c0 + c1 s + c2 s^2,   J(s) = x_DIR . (J dxi_DIR/dx)(s).
+template <int D, int DIR, typename Real>
+struct LineGeo {
+  Real c0[D], c1[D], c2[D], e[D];
+  __device__ __forceinline__ void init(const Real* __restrict__ X, int stride, const Real* xi) {
+    Real al[D][D], be[D][D];
 #pragma unroll
-      for (int j = 0; j < D; ++j) Ja[j] = am[dir * D + j];
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int j = 0; j < D; ++j) al[a][j] = be[a][j] = Real(0);
+#pragma unroll
+    for (int c = 1; c < (1 << D); ++c) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        if (!((c >> a) & 1)) continue;
+        Real fac = Real(1);
+        bool has_s = false;
+#pragma unroll
+        for (int bb = 0; bb < D; ++bb) {
+          if (bb == a || !((c >> bb) & 1)) continue;
+          if (bb == DIR) has_s = true;
+          else fac *= xi[bb];
+        }
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          const Real x = __ldg(&X[((c - 1) * D + j) * stride]);
+          if (has_s) be[a][j] += x * fac;
+          else al[a][j] += x * fac;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) e[j] = al[DIR][j];
+    if constexpr (D == 2) {
+      const int o = 1 - DIR;
+      const Real sg = DIR == 0 ? Real(1) : Real(-1);
+      // DIR 0: (y_eta, -x_eta); DIR 1: (-y_xi, x_xi)
+      c0[0] = sg * al[o][1];
+      c0[1] = -sg * al[o][0];
+      c1[0] = sg * be[o][1];
+      c1[1] = -sg * be[o][0];
+      c2[0] = c2[1] = Real(0);
     } else {
-      Real tg[D][D];
-      tangents<D, Real>(X, stride, xi, tg);
-      contra_row<D, Real>(tg, dir, Ja);
+      constexpr int i1 = (DIR + 1) % 3, i2 = (DIR + 2) % 3;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+        c0[j] = al[i1][j1] * al[i2][j2] - al[i1][j2] * al[i2][j1];
+        c1[j] = al[i1][j1] * be[i2][j2] - al[i1][j2] * be[i2][j1] + be[i1][j1] * al[i2][j2] -
+                be[i1][j2] * al[i2][j1];
+        c2[j] = be[i1][j1] * be[i2][j2] - be[i1][j2] * be[i2][j1];
+      }
     }
   }
-  // row `dir` and 1/J at one point
-  __device__ __forceinline__ Real row_inv_jac(const Real* xi, int dir, Real (&Ja)[D]) const {
-    if (aff) {
+  __device__ __forceinline__ void at(Real s, Real (&Ja)[D]) const {
 #pragma unroll
-      for (int j = 0; j < D; ++j) Ja[j] = am[dir * D + j];
-      return am[D * D];
-    }
-    Real tg[D][D];
-    tangents<D, Real>(X, stride, xi, tg);
-    contra_row<D, Real>(tg, dir, Ja);
+    for (int j = 0; j < D; ++j) Ja[j] = c0[j] + s * (c1[j] + s * c2[j]);
+  }
+  __device__ __forceinline__ Real jac(const Real (&Ja)[D]) const {
     Real J = Real(0);
 #pragma unroll
-    for (int j = 0; j < D; ++j) J += tg[dir][j] * Ja[j];
-    return Real(1) / J;
+    for (int j = 0; j < D; ++j) J += e[j] * Ja[j];
+    return J;
   }
 };
 
+// J dxi_DIR/dx at one reference point (faces), from the trilinear coefficients
+template <int D, typename Real>
+__device__ __forceinline__ void point_row(const Real* __restrict__ X, int stride, const Real* xi, int dir,
+                                          Real (&Ja)[D]) {
+  Real tg[D][D];
+#define XC(c, j) __ldg(&X[(((c)-1) * D + (j)) * stride])
+  if constexpr (D == 2) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      tg[0][j] = XC(1, j) + XC(3, j) * xi[1];
+      tg[1][j] = XC(2, j) + XC(3, j) * xi[0];
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      if (dir != 0) tg[0][j] = XC(1, j) + XC(3, j) * xi[1] + (XC(5, j) + XC(7, j) * xi[1]) * xi[2];
+      if (dir != 1) tg[1][j] = XC(2, j) + XC(3, j) * xi[0] + (XC(6, j) + XC(7, j) * xi[0]) * xi[2];
+      if (dir != 2) tg[2][j] = XC(4, j) + XC(5, j) * xi[0] + (XC(6, j) + XC(7, j) * xi[0]) * xi[1];
+    }
+  }
+#undef XC
+  contra_row<D, Real>(tg, dir, Ja);
+}
+
+// point index of face point fp (tangential digits, axes != ax in increasing
+// order) with digit qn on the normal axis ax
+template <int D, int N>
+__device__ __forceinline__ int face_point_index(int ax, int fp, int qn) {
+  constexpr int S1 = N, S2 = N * N;
+  if constexpr (D == 2) {
+    return ax == 0 ? qn + fp * S1 : fp + qn * S1;
+  } else {
+    const int a0 = fp % N, a1 = fp / N;
+    if (ax == 0) return qn + a0 * S1 + a1 * S2;
+    if (ax == 1) return a0 + qn * S1 + a1 * S2;
+    return a0 + a1 * S1 + qn * S2;
+  }
+}
+
 // ============================================================ stage kernel
 // Persistent CTAs; work item = (leaf, z-chunk); a CTA sweeps the layers of
-// its chunk.  Per layer: modal -> nodal in shared memory, x and y face
-// fluxes (each face once) and volume terms, z faces carried between layers,
-// 1/J, nodal -> modal, SSP-RK combination, CFL minimum on the last stage.
-template <int D, int P, typename Real>
+// its chunk.  Per layer: nodal values to shared memory; x and y face fluxes
+// (each face once); x volume + lift; y volume + lift (and the halo trace of
+// the next layer); z volume + z faces (carried between layers) and 1/J;
+// SSP-RK combination point by point, with the CFL minimum on the last stage.
+template <int D, int P, int NS, typename Real>
 __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB)
     k_stage(const StageArgs<D, P, Real> A) {
-  constexpr int N = P + 1, NV = D + 2, M = ipow(N, D), Q = M, NFP = ipow(N, D - 1);
+  constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
   constexpr int NG = ((1 << D) - 1) * D;
-  const int n = A.n;
-  const int NCL = n * n;
-  const int nc = D == 3 ? NCL * n : NCL;
-  const int nt = D == 3 ? n * n : n;  // guard cells per face
+  constexpr int n = NS;
+  constexpr int NCL = n * n;
+  constexpr int nc = D == 3 ? NCL * n : NCL;
+  constexpr int nt = D == 3 ? n * n : n;  // guard cells per face
+  constexpr int NF = (n + 1) * n * NFP;   // faces of one direction in a layer
   const auto& T = A.T;
   const Real gamma = A.gamma;
   const Real gm1 = gamma - Real(1);
   const Real dt = Real(*A.dtp);
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x;
+  constexpr int nthr = StageCfg<P, Real>::NT;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Real sx[N];
   __shared__ Real sam[D * D + 1];
+  constexpr int RSZ = NV * Q * NCL;
   Real* us = reinterpret_cast<Real*>(smem_raw);
   Real* rs = us + NV * Q * NCL;
-  Real* fs = rs + NV * Q * NCL;
-  Real* fz = fs + NV * NFP * (n + 1) * n;
-  Real* gs = fz + (D == 3 ? NV * NFP * NCL : 0);
-  Real* tb = fs;  // top/bottom halo traces reuse the in-layer face buffer
+  Real* fx = rs + RSZ;
+  Real* fy = fx + NV * NFP * (n + 1) * n;
+  Real* fz = fy + NV * NFP * (n + 1) * n;
+  Real* tb = fx;   // halo traces reuse the x-face buffer when it is free
   if (tid < N) sx[tid] = T.x[tid];
 
-  const size_t ustride = (size_t)nc;
   Real lam_min = Real(3.0e38);
   bool bad = false;
   const int items = A.nL * A.nchunks;
 
 #define US(v, q, c) us[((v) * Q + (q)) * NCL + (c)]
 #define RS(v, q, c) rs[((v) * Q + (q)) * NCL + (c)]
-#define GS(g, c) gs[(g) * NCL + (c)]
-#define GTR(f, v, fp, t) Tb[(((size_t)(f) * NV + (v)) * NFP + (fp)) * nt + (t)]
 // x faces: [v][fp][row j][face fi]; y faces: [v][fp][face fi][column i]
-#define FX(v, fp, j, fi) fs[(((v) * NFP + (fp)) * n + (j)) * (n + 1) + (fi)]
-#define FY(v, fp, fi, i) fs[(((v) * NFP + (fp)) * (n + 1) + (fi)) * n + (i)]
+#define FX(v, fp, j, fi) fx[(((v) * NFP + (fp)) * n + (j)) * (n + 1) + (fi)]
+#define FY(v, fp, fi, i) fy[(((v) * NFP + (fp)) * (n + 1) + (fi)) * n + (i)]
+#define TB(v, fp, c) tb[((v) * NFP + (fp)) * NCL + (c)]
+#define FZ(v, fp, c) fz[((v) * NFP + (fp)) * NCL + (c)]
+#define GTR(f, v, fp, t) Tb[(((size_t)(f) * NV + (v)) * NFP + (fp)) * nt + (t)]
 
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int b = item / A.nchunks;
-    const int chunk = item % A.nchunks;
+    const int chunk = item - b * A.nchunks;
     const int k0 = D == 3 ? chunk * A.zchunk : 0;
     const int k1 = D == 3 ? min(n, k0 + A.zchunk) : 1;
-    const Real* Ub = A.U + (size_t)b * NV * M * nc;
-    const Real* Unb = A.Un + (size_t)b * NV * M * nc;
-    Real* Ob = A.Uout + (size_t)b * NV * M * nc;
-    const Real* Gb = A.geo + (size_t)b * NG * nc;
-    const Real* Tb = A.gtr + (size_t)b * 2 * D * NV * NFP * nt;
+    const Real* __restrict__ Ub = A.U + (size_t)b * NV * Q * nc;
+    const Real* __restrict__ Unb = A.Un + (size_t)b * NV * Q * nc;
+    Real* __restrict__ Ob = A.Uout + (size_t)b * NV * Q * nc;
+    const Real* __restrict__ Gb = A.geo + (size_t)b * NG * nc;
+    const Real* __restrict__ Tb = A.gtr + (size_t)b * 2 * D * NV * NFP * nt;
     const bool aff = A.affine[b] != 0;
     __syncthreads();  // previous item is done with the shared buffers
     if (aff && tid < D * D + 1) sam[tid] = A.ameta[(size_t)b * (D * D + 1) + tid];
 
     for (int k = k0; k < k1; ++k) {
       const int cbase = D == 3 ? k * NCL : 0;
+      const Real* __restrict__ Gk = Gb + cbase;  // geometry of this layer, stride nc
       // ------------------------------------------- L2 prefetch of what comes next
       {
-        const int lines_per_row = (NCL * (int)sizeof(Real) + 127) / 128;
-        const int rows = NV * M;
-        for (int w = tid; w < rows * lines_per_row; w += nthr) {
-          const int r = w / lines_per_row, l = w % lines_per_row;
-          if (D == 3 && k + 1 < n)
-            prefetch_l2(Ub + (size_t)r * ustride + (k + 1) * NCL + l * (128 / sizeof(Real)));
-          if (A.mode == 0 && A.ca != Real(0)) prefetch_l2(Unb + (size_t)r * ustride + cbase + l * (128 / sizeof(Real)));
+        constexpr int lpr = (NCL * (int)sizeof(Real) + 127) / 128;
+        for (int w = tid; w < NV * Q * lpr; w += nthr) {
+          const int r = w / lpr, l = w - r * lpr;
+          if (D == 3 && k + 1 < n) prefetch_l2(Ub + (size_t)r * nc + (k + 1) * NCL + l * (128 / sizeof(Real)));
+          if (A.mode == 0 && A.ca != Real(0)) prefetch_l2(Unb + (size_t)r * nc + cbase + l * (128 / sizeof(Real)));
         }
       }
-      // ------------------------------------------- load layer k (modal -> nodal)
-      for (int w = tid; w < NCL * NV; w += nthr) {
-        const int c = w % NCL, v = w / NCL;
-        Real a[M], t2[M];
-#pragma unroll
-        for (int m = 0; m < M; ++m) a[m] = Ub[((size_t)v * M + m) * ustride + cbase + c];
-        apply_all<D, N, Real>(T.V, a, t2);
-#pragma unroll
-        for (int q = 0; q < Q; ++q) US(v, q, c) = a[q];
-      }
-      if (!aff) {
-        for (int w = tid; w < NCL * NG; w += nthr) {
-          const int c = w % NCL, g = w / NCL;
-          GS(g, c) = Gb[(size_t)g * nc + cbase + c];
+      // ------------------------------------------- P1: layer k to shared memory
+      {
+        constexpr int VEC = 16 / sizeof(Real);
+        using V4 = typename std::conditional<sizeof(Real) == 4, float4, double2>::type;
+        constexpr int PER_ROW = NCL / VEC;
+        for (int w = tid; w < NV * Q * PER_ROW; w += nthr) {
+          const int r = w / PER_ROW, cv = (w - r * PER_ROW) * VEC;
+          const V4 val = *reinterpret_cast<const V4*>(Ub + (size_t)r * nc + cbase + cv);
+          *reinterpret_cast<V4*>(us + r * NCL + cv) = val;
         }
       }
-      __syncthreads();
-
       if constexpr (D == 3) {
         if (k == k0) {
-          // bottom halo trace of the first layer: guard (z-) or the layer below
-          for (int w = tid; w < NCL * NV; w += nthr) {
-            const int c = w % NCL, v = w / NCL;
-            Real tr[NFP];
+          // halo trace below the first layer: guard (z-) or the layer below
+          for (int w = tid; w < NCL * NV * NFP; w += nthr) {
+            const int c = w % NCL, fp = (w / NCL) % NFP, v = w / (NCL * NFP);
+            Real tr;
             if (k0 == 0) {
-#pragma unroll
-              for (int fp = 0; fp < NFP; ++fp) tr[fp] = GTR(4, v, fp, c);
+              tr = GTR(4, v, fp, c);
             } else {
-              Real K[M];
+              tr = Real(0);
 #pragma unroll
-              for (int m = 0; m < M; ++m) K[m] = Ub[((size_t)v * M + m) * ustride + (k0 - 1) * NCL + c];
-              modal_trace<3, N, 2, Real>(T, K, +1, tr);
+              for (int qz = 0; qz < N; ++qz)
+                tr += T.lp[qz] * Ub[((size_t)v * Q + fp + NFP * qz) * nc + (k0 - 1) * NCL + c];
             }
-#pragma unroll
-            for (int fp = 0; fp < NFP; ++fp) tb[(v * NFP + fp) * NCL + c] = tr[fp];
+            TB(v, fp, c) = tr;
           }
           __syncthreads();
           for (int w = tid; w < NCL * NFP; w += nthr) {
@@ -445,83 +474,133 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
             Real uL[NV], uR[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-              uL[v] = tb[(v * NFP + fp) * NCL + c];
+              uL[v] = TB(v, fp, c);
               Real s = Real(0);
 #pragma unroll
               for (int qz = 0; qz < N; ++qz) s += T.lm[qz] * US(v, fp + NFP * qz, c);
               uR[v] = s;
             }
-            CellMetric<3, Real> cm;
-            cm.load(aff, sam, gs, NCL, c);
-            const Real xi[3] = {sx[fp % N], sx[fp / N], Real(-1)};
             Real Ja[3], Fh[NV];
-            cm.row(xi, 2, Ja);
+            if (aff) {
+#pragma unroll
+              for (int j = 0; j < 3; ++j) Ja[j] = sam[6 + j];
+            } else {
+              const Real xi[3] = {sx[fp % N], sx[fp / N], Real(-1)};
+              point_row<3, Real>(Gk + c, nc, xi, 2, Ja);
+            }
             lf_flux<3, Real>(uL, uR, Ja, gamma, Fh);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) fz[(v * NFP + fp) * NCL + c] = Fh[v];
-          }
-          __syncthreads();
-        }
-      }
-
-      // ------------------------------------------------- x faces
-      for (int w = tid; w < (n + 1) * n * NFP; w += nthr) {
-        const int fi = w % (n + 1);
-        const int j = (w / (n + 1)) % n;
-        const int fp = w / ((n + 1) * n);
-        const int t = D == 3 ? j + n * k : j;
-        Real uL[NV], uR[NV];
-        const int cl = (fi - 1) + n * j, cr = fi + n * j;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          if (fi == 0) {
-            uL[v] = GTR(0, v, fp, t);
-          } else {
-            Real s = Real(0);
-#pragma unroll
-            for (int qx = 0; qx < N; ++qx) s += T.lp[qx] * US(v, qx + N * fp, cl);
-            uL[v] = s;
-          }
-          if (fi == n) {
-            uR[v] = GTR(1, v, fp, t);
-          } else {
-            Real s = Real(0);
-#pragma unroll
-            for (int qx = 0; qx < N; ++qx) s += T.lm[qx] * US(v, qx + N * fp, cr);
-            uR[v] = s;
+            for (int v = 0; v < NV; ++v) FZ(v, fp, c) = Fh[v];
           }
         }
-        CellMetric<D, Real> cm;
-        cm.load(aff, sam, gs, NCL, fi == n ? cl : cr);
-        Real xi[D];
-        xi[0] = fi == n ? Real(1) : Real(-1);
-        xi[1] = sx[fp % N];
-        if constexpr (D == 3) xi[2] = sx[fp / N];
-        Real Ja[D], Fh[NV];
-        cm.row(xi, 0, Ja);
-        lf_flux<D, Real>(uL, uR, Ja, gamma, Fh);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) FX(v, fp, j, fi) = Fh[v];
       }
       __syncthreads();
-      // ------------------------------------------------- x volume + lift
+
+      // ------------------------------------------- P2: x and y face fluxes
+      for (int w = tid; w < 2 * NF; w += nthr) {
+        const bool ydir = w >= NF;
+        const int ww = ydir ? w - NF : w;
+        Real uL[NV], uR[NV], Ja[D], Fh[NV];
+        if (!ydir) {
+          const int fi = ww % (n + 1);
+          const int j = (ww / (n + 1)) % n;
+          const int fp = ww / ((n + 1) * n);
+          const int cl = (fi - 1) + n * j, cr = fi + n * j;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            if (fi == 0) {
+              uL[v] = GTR(0, v, fp, D == 3 ? j + n * k : j);
+            } else {
+              Real s = Real(0);
+#pragma unroll
+              for (int qx = 0; qx < N; ++qx) s += T.lp[qx] * US(v, qx + N * fp, cl);
+              uL[v] = s;
+            }
+            if (fi == n) {
+              uR[v] = GTR(1, v, fp, D == 3 ? j + n * k : j);
+            } else {
+              Real s = Real(0);
+#pragma unroll
+              for (int qx = 0; qx < N; ++qx) s += T.lm[qx] * US(v, qx + N * fp, cr);
+              uR[v] = s;
+            }
+          }
+          if (aff) {
+#pragma unroll
+            for (int jj = 0; jj < D; ++jj) Ja[jj] = sam[jj];
+          } else {
+            Real xi[D];
+            xi[0] = fi == n ? Real(1) : Real(-1);
+            xi[1] = sx[fp % N];
+            if constexpr (D == 3) xi[2] = sx[fp / N];
+            point_row<D, Real>(Gk + (fi == n ? cl : cr), nc, xi, 0, Ja);
+          }
+          lf_flux<D, Real>(uL, uR, Ja, gamma, Fh);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) FX(v, fp, j, fi) = Fh[v];
+        } else {
+          const int i = ww % n;
+          const int fi = (ww / n) % (n + 1);
+          const int fp = ww / ((n + 1) * n);  // qx + N qz
+          const int qx = fp % N, qz = fp / N;
+          const int cl = i + n * (fi - 1), cr = i + n * fi;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            if (fi == 0) {
+              uL[v] = GTR(2, v, fp, D == 3 ? i + n * k : i);
+            } else {
+              Real s = Real(0);
+#pragma unroll
+              for (int qy = 0; qy < N; ++qy) s += T.lp[qy] * US(v, qx + N * qy + N * N * qz, cl);
+              uL[v] = s;
+            }
+            if (fi == n) {
+              uR[v] = GTR(3, v, fp, D == 3 ? i + n * k : i);
+            } else {
+              Real s = Real(0);
+#pragma unroll
+              for (int qy = 0; qy < N; ++qy) s += T.lm[qy] * US(v, qx + N * qy + N * N * qz, cr);
+              uR[v] = s;
+            }
+          }
+          if (aff) {
+#pragma unroll
+            for (int jj = 0; jj < D; ++jj) Ja[jj] = sam[D + jj];
+          } else {
+            Real xi[D];
+            xi[0] = sx[qx];
+            xi[1] = fi == n ? Real(1) : Real(-1);
+            if constexpr (D == 3) xi[2] = sx[qz];
+            point_row<D, Real>(Gk + (fi == n ? cl : cr), nc, xi, 1, Ja);
+          }
+          lf_flux<D, Real>(uL, uR, Ja, gamma, Fh);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) FY(v, fp, fi, i) = Fh[v];
+        }
+      }
+      __syncthreads();
+      // ------------------------------------------- P3: x volume + lift (rs =)
       for (int w = tid; w < NCL * NFP; w += nthr) {
         const int c = w % NCL, fp = w / NCL;
         const int i = c % n, j = c / n;
-        CellMetric<D, Real> cm;
-        cm.load(aff, sam, gs, NCL, c);
         Real xi[D];
+        xi[0] = Real(0);
         xi[1] = sx[fp % N];
         if constexpr (D == 3) xi[2] = sx[fp / N];
+        LineGeo<D, 0, Real> lg;
+        if (!aff) lg.init(Gk + c, nc, xi);
         Real F[N][NV];
 #pragma unroll
         for (int qx = 0; qx < N; ++qx) {
-          Real u[NV];
+          Real u[NV], Ja[D], Fq[NV];
 #pragma unroll
           for (int v = 0; v < NV; ++v) u[v] = US(v, qx + N * fp, c);
-          xi[0] = T.x[qx];
-          Real Ja[D], Fq[NV];
-          cm.row(xi, 0, Ja);
+          if (aff) {
+#pragma unroll
+            for (int jj = 0; jj < D; ++jj) Ja[jj] = sam[jj];
+          } else {
+            lg.at(T.x[qx], Ja);
+          }
           flux_along<D, Real>(u, Ja, gm1, Fq);
 #pragma unroll
           for (int v = 0; v < NV; ++v) F[qx][v] = Fq[v];
@@ -540,149 +619,120 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
         }
       }
       __syncthreads();
-      // ------------------------------------------------- y faces
-      for (int w = tid; w < (n + 1) * n * NFP; w += nthr) {
-        const int i = w % n;
-        const int fi = (w / n) % (n + 1);
-        const int fp = w / ((n + 1) * n);  // qx + N qz
-        const int qx = fp % N, qz = fp / N;
-        const int t = D == 3 ? i + n * k : i;
-        Real uL[NV], uR[NV];
-        const int cl = i + n * (fi - 1), cr = i + n * fi;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          if (fi == 0) {
-            uL[v] = GTR(2, v, fp, t);
-          } else {
-            Real s = Real(0);
-#pragma unroll
-            for (int qy = 0; qy < N; ++qy) s += T.lp[qy] * US(v, qx + N * qy + N * N * qz, cl);
-            uL[v] = s;
-          }
-          if (fi == n) {
-            uR[v] = GTR(3, v, fp, t);
-          } else {
-            Real s = Real(0);
-#pragma unroll
-            for (int qy = 0; qy < N; ++qy) s += T.lm[qy] * US(v, qx + N * qy + N * N * qz, cr);
-            uR[v] = s;
-          }
-        }
-        CellMetric<D, Real> cm;
-        cm.load(aff, sam, gs, NCL, fi == n ? cl : cr);
-        Real xi[D];
-        xi[0] = sx[qx];
-        xi[1] = fi == n ? Real(1) : Real(-1);
-        if constexpr (D == 3) xi[2] = sx[qz];
-        Real Ja[D], Fh[NV];
-        cm.row(xi, 1, Ja);
-        lf_flux<D, Real>(uL, uR, Ja, gamma, Fh);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) FY(v, fp, fi, i) = Fh[v];
-      }
-      __syncthreads();
-      // ------------------------------------------------- y volume + lift
-      for (int w = tid; w < NCL * NFP; w += nthr) {
-        const int c = w % NCL, fp = w / NCL;
-        const int i = c % n, j = c / n;
-        const int qx = fp % N, qz = fp / N;
-        CellMetric<D, Real> cm;
-        cm.load(aff, sam, gs, NCL, c);
-        Real xi[D];
-        xi[0] = sx[qx];
-        if constexpr (D == 3) xi[2] = sx[qz];
-        Real F[N][NV];
-        Real iJ[N];
-#pragma unroll
-        for (int qy = 0; qy < N; ++qy) {
-          Real u[NV];
-          const int q = qx + N * qy + N * N * qz;
-#pragma unroll
-          for (int v = 0; v < NV; ++v) u[v] = US(v, q, c);
-          xi[1] = T.x[qy];
-          Real Ja[D], Fq[NV];
-          if constexpr (D == 2) iJ[qy] = cm.row_inv_jac(xi, 1, Ja);
-          else cm.row(xi, 1, Ja);
-          flux_along<D, Real>(u, Ja, gm1, Fq);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) F[qy][v] = Fq[v];
-        }
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const Real fm = FY(v, fp, j, i);
-          const Real fpl = FY(v, fp, j + 1, i);
+      // ------------------------------------------- P4: y volume + lift (rs +=)
+      //                                            and the halo trace above
+      constexpr int NY = NCL * NFP;
+      constexpr int ny_total = NY + ((D == 3) ? NCL * NV * NFP : 0);
+      for (int w = tid; w < ny_total; w += nthr) {
+        if (w < NY) {
+          const int c = w % NCL, fp = w / NCL;
+          const int i = c % n, j = c / n;
+          const int qx = fp % N, qz = fp / N;
+          Real xi[D];
+          xi[0] = sx[qx];
+          xi[1] = Real(0);
+          if constexpr (D == 3) xi[2] = sx[qz];
+          LineGeo<D, 1, Real> lg;
+          if (!aff) lg.init(Gk + c, nc, xi);
+          Real F[N][NV];
+          Real iJ[N];
 #pragma unroll
           for (int qy = 0; qy < N; ++qy) {
-            Real s = Real(0);
-#pragma unroll
-            for (int jj = 0; jj < N; ++jj) s += T.Sh[qy][jj] * F[jj][v];
+            Real u[NV], Ja[D], Fq[NV];
             const int q = qx + N * qy + N * N * qz;
-            Real r = RS(v, q, c) + s - T.lpw[qy] * fpl + T.lmw[qy] * fm;
-            if constexpr (D == 2) r *= iJ[qy];
-            RS(v, q, c) = r;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) u[v] = US(v, q, c);
+            if (aff) {
+#pragma unroll
+              for (int jj = 0; jj < D; ++jj) Ja[jj] = sam[D + jj];
+              iJ[qy] = sam[D * D];
+            } else {
+              lg.at(T.x[qy], Ja);
+              if constexpr (D == 2) iJ[qy] = Real(1) / lg.jac(Ja);
+            }
+            flux_along<D, Real>(u, Ja, gm1, Fq);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) F[qy][v] = Fq[v];
           }
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const Real fm = FY(v, fp, j, i);
+            const Real fpl = FY(v, fp, j + 1, i);
+#pragma unroll
+            for (int qy = 0; qy < N; ++qy) {
+              Real s = Real(0);
+#pragma unroll
+              for (int jj = 0; jj < N; ++jj) s += T.Sh[qy][jj] * F[jj][v];
+              const int q = qx + N * qy + N * N * qz;
+              Real r = RS(v, q, c) + s - T.lpw[qy] * fpl + T.lmw[qy] * fm;
+              if constexpr (D == 2) r *= iJ[qy];
+              RS(v, q, c) = r;
+            }
+          }
+        } else if constexpr (D == 3) {
+          const int ww = w - NY;
+          const int c = ww % NCL, fp = (ww / NCL) % NFP, v = ww / (NCL * NFP);
+          Real tr;
+          if (k == n - 1) {
+            tr = GTR(5, v, fp, c);
+          } else {
+            tr = Real(0);
+#pragma unroll
+            for (int qz = 0; qz < N; ++qz)
+              tr += T.lm[qz] * Ub[((size_t)v * Q + fp + NFP * qz) * nc + (k + 1) * NCL + c];
+          }
+          TB(v, fp, c) = tr;
         }
       }
       __syncthreads();
 
       if constexpr (D == 3) {
-        // ------------------------------------------- top halo trace of layer k
-        for (int w = tid; w < NCL * NV; w += nthr) {
-          const int c = w % NCL, v = w / NCL;
-          Real tr[NFP];
-          if (k == n - 1) {
-#pragma unroll
-            for (int fp = 0; fp < NFP; ++fp) tr[fp] = GTR(5, v, fp, c);
-          } else {
-            Real K[M];
-#pragma unroll
-            for (int m = 0; m < M; ++m) K[m] = Ub[((size_t)v * M + m) * ustride + (k + 1) * NCL + c];
-            modal_trace<3, N, 2, Real>(T, K, -1, tr);
-          }
-#pragma unroll
-          for (int fp = 0; fp < NFP; ++fp) tb[(v * NFP + fp) * NCL + c] = tr[fp];
-        }
-        __syncthreads();
-        // ------------------------------------------- z volume + z faces, 1/J
+        // ------------------------------------------- P5: z volume + z faces, 1/J
         for (int w = tid; w < NCL * NFP; w += nthr) {
           const int c = w % NCL, fp = w / NCL;
           const int qx = fp % N, qy = fp / N;
-          CellMetric<3, Real> cm;
-          cm.load(aff, sam, gs, NCL, c);
-          Real xi[3] = {sx[qx], sx[qy], Real(0)};
+          const Real xi[3] = {sx[qx], sx[qy], Real(0)};
+          LineGeo<3, 2, Real> lg;
+          if (!aff) lg.init(Gk + c, nc, xi);
           Real F[N][NV];
           Real iJ[N];
 #pragma unroll
           for (int qz = 0; qz < N; ++qz) {
-            Real u[NV];
+            Real u[NV], Ja[3], Fq[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) u[v] = US(v, fp + NFP * qz, c);
-            xi[2] = T.x[qz];
-            Real Ja[3], Fq[NV];
-            iJ[qz] = cm.row_inv_jac(xi, 2, Ja);
+            if (aff) {
+#pragma unroll
+              for (int jj = 0; jj < 3; ++jj) Ja[jj] = sam[6 + jj];
+              iJ[qz] = sam[9];
+            } else {
+              lg.at(T.x[qz], Ja);
+              iJ[qz] = Real(1) / lg.jac(Ja);
+            }
             flux_along<3, Real>(u, Ja, gm1, Fq);
 #pragma unroll
             for (int v = 0; v < NV; ++v) F[qz][v] = Fq[v];
           }
           // top face flux: own top trace vs the halo trace above
-          Real uL[NV], uR[NV], Fh[NV];
+          Real uL[NV], uR[NV], Fh[NV], Ja[3];
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             Real s = Real(0);
 #pragma unroll
             for (int qz = 0; qz < N; ++qz) s += T.lp[qz] * US(v, fp + NFP * qz, c);
             uL[v] = s;
-            uR[v] = tb[(v * NFP + fp) * NCL + c];
+            uR[v] = TB(v, fp, c);
           }
-          {
-            xi[2] = Real(1);
-            Real Ja[3];
-            cm.row(xi, 2, Ja);
-            lf_flux<3, Real>(uL, uR, Ja, gamma, Fh);
+          if (aff) {
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj) Ja[jj] = sam[6 + jj];
+          } else {
+            lg.at(Real(1), Ja);
           }
+          lf_flux<3, Real>(uL, uR, Ja, gamma, Fh);
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
-            const Real fbot = fz[(v * NFP + fp) * NCL + c];
+            const Real fbot = FZ(v, fp, c);
 #pragma unroll
             for (int qz = 0; qz < N; ++qz) {
               Real s = Real(0);
@@ -691,57 +741,43 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
               const int q = fp + NFP * qz;
               RS(v, q, c) = (RS(v, q, c) + s - T.lpw[qz] * Fh[v] + T.lmw[qz] * fbot) * iJ[qz];
             }
-            fz[(v * NFP + fp) * NCL + c] = Fh[v];
+            FZ(v, fp, c) = Fh[v];
           }
         }
         __syncthreads();
       }
 
-      // ------------------------------------------------- epilogue
-      for (int w = tid; w < NCL * NV; w += nthr) {
-        const int c = w % NCL, v = w / NCL;
-        Real a[M], t2[M];
+      // ------------------------------------------- P6: SSP-RK combination (+ CFL)
+      for (int w = tid; w < NCL * Q; w += nthr) {
+        const int c = w % NCL, q = w / NCL;
+        Real o[NV];
 #pragma unroll
-        for (int q = 0; q < Q; ++q) a[q] = RS(v, q, c);
-        apply_all<D, N, Real>(T.Vi, a, t2);  // a = modal L(U)
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-          const size_t gi = ((size_t)v * M + m) * ustride + cbase + c;
-          Real o;
+        for (int v = 0; v < NV; ++v) {
+          const size_t gi = ((size_t)v * Q + q) * nc + cbase + c;
+          const Real r = RS(v, q, c);
+          Real val;
           if (A.mode == 1) {
-            o = a[m];
+            val = r;
           } else {
-            o = A.cb * (Ub[gi] + dt * a[m]);
-            if (A.ca != Real(0)) o += A.ca * Unb[gi];
+            val = A.cb * (Ub[gi] + dt * r);
+            if (A.ca != Real(0)) val += A.ca * Unb[gi];
           }
-          Ob[gi] = o;
-          a[m] = o;
+          Ob[gi] = val;
+          o[v] = val;
         }
         if (A.last) {
-          apply_all<D, N, Real>(T.V, a, t2);
-#pragma unroll
-          for (int q = 0; q < Q; ++q) US(v, q, c) = a[q];
-        }
-      }
-      if (A.last) {
-        __syncthreads();
-        for (int w = tid; w < NCL * Q; w += nthr) {
-          const int c = w % NCL, q = w / NCL;
-          Real u[NV];
-#pragma unroll
-          for (int v = 0; v < NV; ++v) u[v] = US(v, q, c);
-          const Real ri = Real(1) / u[0];
+          const Real ri = Real(1) / o[0];
           Real ke = Real(0), sv = Real(0);
 #pragma unroll
-          for (int j = 0; j < D; ++j) {
-            ke += u[1 + j] * u[1 + j];
-            sv += fabs(u[1 + j]) * ri;
+          for (int jj = 0; jj < D; ++jj) {
+            ke += o[1 + jj] * o[1 + jj];
+            sv += fabs(o[1 + jj]) * ri;
           }
-          const Real p = gm1 * (u[D + 1] - Real(0.5) * ke * ri);
-          if (!(u[0] > Real(0)) || !(p > Real(0)) || !(p < Real(3.0e38))) {
+          const Real pr = gm1 * (o[D + 1] - Real(0.5) * ke * ri);
+          if (!(o[0] > Real(0)) || !(pr > Real(0)) || !(pr < Real(3.0e38))) {
             bad = true;
           } else {
-            const Real lam = sv + Real(D) * sqrt(gamma * p * ri);
+            const Real lam = sv + Real(D) * sqrt(gamma * pr * ri);
             const Real hv = A.hcell[(size_t)b * nc + cbase + c] / lam;
             lam_min = hv < lam_min ? hv : lam_min;
           }
@@ -752,10 +788,11 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
   }
 #undef US
 #undef RS
-#undef GS
-#undef GTR
 #undef FX
 #undef FY
+#undef TB
+#undef FZ
+#undef GTR
 
   if (A.last) {
     // block min of h/lambda -> one atomic per CTA
@@ -783,12 +820,13 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
 }
 
 // ============================================================ guard kernels
-// Sec. 3.5, Eqs. (15)-(17).  The stage kernel needs, for every block face,
-// the guard cell's trace at my face Gauss points in my frame; the ABI's
-// standalone fill needs the guard cells' modal coefficients in my frame.
-// Same-level and coarser neighbours: the trace (or the modes) is computed in
-// the neighbour's frame and scattered into my point (mode) order, so no
-// register array is indexed at run time.  Finer neighbours use k_guard_fine.
+// Sec. 3.5, Eqs. (15)-(17), on nodal values.  The stage kernel needs, for
+// every block face, the guard cell's trace at my face Gauss points in my
+// frame (mode 1); the C ABI's standalone fill needs the guard cells' values
+// at my Gauss points (mode 0, converted to modes afterwards).  Same-level
+// and coarser neighbours: the trace is taken in the neighbour's frame and
+// scattered into my point order (rotations map Gauss points onto Gauss
+// points).  Finer neighbours use k_guard_fine.
 
 // source-frame face point j -> my face point index, for my face axis a and
 // the neighbour's face axis b2 (orientation packed as in opi/osg)
@@ -796,12 +834,11 @@ template <int D, int N>
 __device__ __forceinline__ int map_face_point(int j, int a, int b2, int pk) {
   if constexpr (D == 2) {
     const int t0 = 1 - a;  // my only tangential axis
-    const int q = j;       // source tangential index
-    return osg(pk, t0) > 0 ? q : N - 1 - q;
+    return osg(pk, t0) > 0 ? j : N - 1 - j;
   } else {
     const int u0 = b2 == 0 ? 1 : 0;  // first source tangential axis
     const int qu0 = j % N, qu1 = j / N;
-    const int t0 = a == 0 ? 1 : 0, t1 = a == 2 ? 1 : 2;   // my tangential axes
+    const int t0 = a == 0 ? 1 : 0, t1 = a == 2 ? 1 : 2;  // my tangential axes
     const int s0 = opi(pk, t0) == u0 ? qu0 : qu1;
     const int s1 = opi(pk, t1) == u0 ? qu0 : qu1;
     const int q0 = osg(pk, t0) > 0 ? s0 : N - 1 - s0;
@@ -810,33 +847,23 @@ __device__ __forceinline__ int map_face_point(int j, int a, int b2, int pk) {
   }
 }
 
-// source mode ms (digits in the neighbour's frame) -> my mode and sign
+// source-frame volume point (digits js[]) -> my point index
 template <int D, int N>
-__device__ __forceinline__ int map_mode(int ms, int pk, float* sign) {
-  int k[3] = {0, 0, 0};
-  int r = ms;
-#pragma unroll
-  for (int u = 0; u < D; ++u) {
-    k[u] = r % N;
-    r /= N;
-  }
+__device__ __forceinline__ int map_point(const int* js, int pk) {
   int m = 0, st = 1;
-  float sg = 1.f;
 #pragma unroll
   for (int ax = 0; ax < D; ++ax) {
-    const int ka = k[opi(pk, ax)];
-    m += ka * st;
+    const int d = js[opi(pk, ax)];
+    m += (osg(pk, ax) > 0 ? d : N - 1 - d) * st;
     st *= N;
-    if (osg(pk, ax) < 0 && (ka & 1)) sg = -sg;
   }
-  *sign = sg;
   return m;
 }
 
 // one thread per (leaf, face, guard cell t, var); finer faces are skipped
 template <int D, int P, typename Real>
 __global__ void __launch_bounds__(128) k_guard(const GuardArgs<D, P, Real> A) {
-  constexpr int N = P + 1, NV = D + 2, M = ipow(N, D), NFP = ipow(N, D - 1);
+  constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
   const int n = A.n;
   const int nt = D == 3 ? n * n : n;
   const int nc = D == 3 ? n * n * n : n * n;
@@ -861,53 +888,50 @@ __global__ void __launch_bounds__(128) k_guard(const GuardArgs<D, P, Real> A) {
     }
   }
   const int pk = A.orient[b * 2 * D + f];
-  auto load = [&](int leaf, const int* h, Real* dst) {
+  auto cell_of = [&](const int* h) {
     int c = 0, st = 1;
     for (int ax = 0; ax < D; ++ax) {
       c += h[ax] * st;
       st *= n;
     }
-    const Real* src = A.U + ((size_t)leaf * NV + v) * M * nc + c;
-#pragma unroll
-    for (int m = 0; m < M; ++m) dst[m] = src[(size_t)m * nc];
+    return c;
   };
-  Real* out_modal = A.out + (((size_t)b * 2 * D + f) * NV + v) * M * nt + t;
+  Real* out_vol = A.out + (((size_t)b * 2 * D + f) * NV + v) * Q * nt + t;
   Real* out_trace = A.out + (((size_t)b * 2 * D + f) * NV + v) * NFP * nt + t;
 
   if (kind == 3) {  // outflow: the guard is the mirror image of my face cell
     int h[3] = {g[0], g[1], g[2]};
     h[a] = s ? n - 1 : 0;
-    Real K[M];
-    load(b, h, K);
+    const Real* src = A.U + ((size_t)b * NV + v) * Q * nc + cell_of(h);
     if (A.mode == 0) {
 #pragma unroll
-      for (int m = 0; m < M; ++m) {
-        int ka = m;
-        for (int u = 0; u < a; ++u) ka /= N;
-        out_modal[(size_t)m * nt] = (ka % N) & 1 ? -K[m] : K[m];
+      for (int q = 0; q < Q; ++q) {
+        int d[3] = {q % N, (q / N) % N, q / (N * N)};
+        d[a] = N - 1 - d[a];
+        out_vol[(size_t)q * nt] = src[(size_t)(d[0] + N * d[1] + N * N * d[2]) * nc];
       }
     } else {
-      Real tr[NFP];
-      modal_trace_rt<D, N, Real>(T, K, a, s ? +1 : -1, tr);
 #pragma unroll
-      for (int fp = 0; fp < NFP; ++fp) out_trace[(size_t)fp * nt] = tr[fp];
+      for (int fp = 0; fp < NFP; ++fp) {
+        Real acc = Real(0);
+#pragma unroll
+        for (int qn = 0; qn < N; ++qn)
+          acc += (s ? T.lp[qn] : T.lm[qn]) * src[(size_t)face_point_index<D, N>(a, fp, qn) * nc];
+        out_trace[(size_t)fp * nt] = acc;
+      }
     }
     return;
   }
   const int b2 = opi(pk, a);
   const int s2 = osg(pk, a) > 0 ? 1 - s : s;
-  int h[3] = {0, 0, 0};
-  Real S[M];
+  int h[3] = {0, 0, 0}, e[3] = {0, 0, 0};
   if (kind == 0) {
     for (int ax = 0; ax < D; ++ax) {
       if (ax == a) continue;
       h[opi(pk, ax)] = osg(pk, ax) > 0 ? g[ax] : n - 1 - g[ax];
     }
-    h[b2] = s2 == 0 ? 0 : n - 1;
-    load(A.nbr[(b * 2 * D + f) * 4], h, S);
-  } else {  // coarser: split of Eqs. (11)-(12) in tensor form, neighbour frame
+  } else {  // coarser: my guard is child e of the coarse cell h (neighbour frame)
     const int qb = A.qbits[b];
-    int e[3] = {0, 0, 0};
     for (int ax = 0; ax < D; ++ax) {
       if (ax == a) continue;
       const int G = ((qb >> ax) & 1) * n + g[ax];
@@ -915,51 +939,103 @@ __global__ void __launch_bounds__(128) k_guard(const GuardArgs<D, P, Real> A) {
       h[opi(pk, ax)] = osg(pk, ax) > 0 ? hh : n - 1 - hh;
       e[opi(pk, ax)] = osg(pk, ax) > 0 ? ee : 1 - ee;
     }
-    h[b2] = s2 == 0 ? 0 : n - 1;
     e[b2] = s2 == 0 ? 0 : 1;
-    Real S2[M];
-    load(A.nbr[(b * 2 * D + f) * 4], h, S);
-    if (e[0]) apply_axis<D, N, 0, Real>(T.Sp, S, S2);
-    else apply_axis<D, N, 0, Real>(T.Sm, S, S2);
-    if (e[1]) apply_axis<D, N, 1, Real>(T.Sp, S2, S);
-    else apply_axis<D, N, 1, Real>(T.Sm, S2, S);
-    if constexpr (D == 3) {
-      if (e[2]) apply_axis<D, N, 2, Real>(T.Sp, S, S2);
-      else apply_axis<D, N, 2, Real>(T.Sm, S, S2);
-#pragma unroll
-      for (int m = 0; m < M; ++m) S[m] = S2[m];
-    }
   }
-  if (A.mode == 0) {
-#pragma unroll
-    for (int ms = 0; ms < M; ++ms) {
-      float sg;
-      const int m = map_mode<D, N>(ms, pk, &sg);
-      out_modal[(size_t)m * nt] = sg < 0 ? -S[ms] : S[ms];
-    }
-  } else {
-    // trace on the neighbour's face (b2, s2), then into my point order
+  h[b2] = s2 == 0 ? 0 : n - 1;
+  const Real* src = A.U + ((size_t)A.nbr[(b * 2 * D + f) * 4] * NV + v) * Q * nc + cell_of(h);
+
+  if (A.mode == 1) {
+    // trace on the neighbour's face (b2, s2) at its face points
     Real tr[NFP];
-    modal_trace_rt<D, N, Real>(T, S, b2, s2 ? +1 : -1, tr);
+#pragma unroll
+    for (int j = 0; j < NFP; ++j) {
+      Real acc = Real(0);
+#pragma unroll
+      for (int qn = 0; qn < N; ++qn)
+        acc += (s2 ? T.lp[qn] : T.lm[qn]) * src[(size_t)face_point_index<D, N>(b2, j, qn) * nc];
+      tr[j] = acc;
+    }
+    if (kind == 1) {
+      // split (Eqs. (11)-(12)): interpolate the coarse face trace to the
+      // Gauss points of the child face, along each tangential axis
+      Real t2[NFP];
+      if constexpr (D == 2) {
+        const int u0 = 1 - b2;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          Real acc = Real(0);
+#pragma unroll
+          for (int jj = 0; jj < N; ++jj) acc += (e[u0] ? T.Snp[i][jj] : T.Snm[i][jj]) * tr[jj];
+          t2[i] = acc;
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) tr[i] = t2[i];
+      } else {
+        const int u0 = b2 == 0 ? 1 : 0, u1 = b2 == 2 ? 1 : 2;
+#pragma unroll
+        for (int i1 = 0; i1 < N; ++i1)
+#pragma unroll
+          for (int i0 = 0; i0 < N; ++i0) {
+            Real acc = Real(0);
+#pragma unroll
+            for (int jj = 0; jj < N; ++jj) acc += (e[u0] ? T.Snp[i0][jj] : T.Snm[i0][jj]) * tr[jj + N * i1];
+            t2[i0 + N * i1] = acc;
+          }
+#pragma unroll
+        for (int i1 = 0; i1 < N; ++i1)
+#pragma unroll
+          for (int i0 = 0; i0 < N; ++i0) {
+            Real acc = Real(0);
+#pragma unroll
+            for (int jj = 0; jj < N; ++jj) acc += (e[u1] ? T.Snp[i1][jj] : T.Snm[i1][jj]) * t2[i0 + N * jj];
+            tr[i0 + N * i1] = acc;
+          }
+      }
+    }
 #pragma unroll
     for (int j = 0; j < NFP; ++j) out_trace[(size_t)map_face_point<D, N>(j, a, b2, pk) * nt] = tr[j];
+    return;
+  }
+  // mode 0: full guard cell at my Gauss points
+  Real u[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) u[q] = src[(size_t)q * nc];
+  if (kind == 1) {
+    Real u2[Q];
+    if (e[0]) apply_axis<D, N, 0, Real>(T.Snp, u, u2);
+    else apply_axis<D, N, 0, Real>(T.Snm, u, u2);
+    if (e[1]) apply_axis<D, N, 1, Real>(T.Snp, u2, u);
+    else apply_axis<D, N, 1, Real>(T.Snm, u2, u);
+    if constexpr (D == 3) {
+      if (e[2]) apply_axis<D, N, 2, Real>(T.Snp, u, u2);
+      else apply_axis<D, N, 2, Real>(T.Snm, u, u2);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) u[q] = u2[q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int js[3] = {q % N, (q / N) % N, q / (N * N)};
+    out_vol[(size_t)map_point<D, N>(js, pk) * nt] = u[q];
   }
 }
 
-// Finer neighbours (Eqs. (13)-(14)): one warp per (finer face, guard cell t,
-// var); the 2^D x M fine-cell modes are staged in shared memory and lane m
-// forms output mode m with the precomputed, already rotated operator.
+// Finer neighbours (Eqs. (13)-(14)): one CTA per (finer face, guard cell t,
+// var) with one warp per fine child e; warp e applies child e's columns of
+// the precomputed, already rotated nodal operator, the partial sums are
+// added in fixed child order, and (mode 1) the trace at my face is formed.
 template <int D, int P, typename Real>
-__global__ void __launch_bounds__(128) k_guard_fine(const GuardArgs<D, P, Real> A) {
-  constexpr int N = P + 1, NV = D + 2, M = ipow(N, D), NFP = ipow(N, D - 1);
-  constexpr int KC = (1 << D) * M;
-  __shared__ Real stage[4][KC + M];
+__global__ void __launch_bounds__(32 << D) k_guard_fine(const GuardArgs<D, P, Real> A) {
+  constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
+  constexpr int NW = 1 << D;
+  constexpr int KC = NW * Q;
+  __shared__ Real srcs[NW][Q];
+  __shared__ Real part[NW][Q];
   const int n = A.n;
   const int nt = D == 3 ? n * n : n;
   const int nc = D == 3 ? n * n * n : n * n;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const size_t item = (size_t)blockIdx.x * 4 + wib;
-  if (item >= (size_t)A.nfine * nt * NV) return;
+  const int lane = threadIdx.x & 31, e = threadIdx.x >> 5;
+  const size_t item = blockIdx.x;
   const int t = (int)(item % nt);
   const int v = (int)((item / nt) % NV);
   const int bf = A.fine_list[item / ((size_t)nt * NV)];
@@ -987,85 +1063,83 @@ __global__ void __launch_bounds__(128) k_guard_fine(const GuardArgs<D, P, Real> 
   }
   h[b2] = s2 == 0 ? 0 : n - 1;
   const int fine = A.nbr[bf * 4 + sub];
-  Real* src = stage[wib];
-  Real* K = stage[wib] + KC;
-  for (int i = lane; i < KC; i += 32) {
-    const int e = i / M, k = i % M;
-    int c = 0, st = 1;
-    for (int ax = 0; ax < D; ++ax) {
-      const int cN = (2 * h[ax]) / n;
-      c += (2 * h[ax] + ((e >> ax) & 1) - cN * n) * st;
-      st *= n;
-    }
-    src[i] = A.U[(((size_t)fine * NV + v) * M + k) * nc + c];
+  int c = 0, st = 1;
+  for (int ax = 0; ax < D; ++ax) {
+    const int cN = (2 * h[ax]) / n;
+    c += (2 * h[ax] + ((e >> ax) & 1) - cN * n) * st;
+    st *= n;
   }
+  for (int q = lane; q < Q; q += 32) srcs[e][q] = A.U[(((size_t)fine * NV + v) * Q + q) * nc + c];
   __syncwarp();
-  const Real* op = A.cop + (size_t)(A.copoff[bf] + t) * KC * M;
-  for (int m = lane; m < M; m += 32) {
+  const Real* op = A.cop + (size_t)(A.copoff[bf] + t) * KC * Q + (size_t)e * Q * Q;
+  for (int p = lane; p < Q; p += 32) {
+    Real acc0 = Real(0), acc1 = Real(0);
+#pragma unroll 4
+    for (int q = 0; q + 1 < Q; q += 2) {
+      acc0 += __ldg(&op[(size_t)q * Q + p]) * srcs[e][q];
+      acc1 += __ldg(&op[(size_t)(q + 1) * Q + p]) * srcs[e][q + 1];
+    }
+    if (Q & 1) acc0 += __ldg(&op[(size_t)(Q - 1) * Q + p]) * srcs[e][Q - 1];
+    part[e][p] = acc0 + acc1;
+  }
+  __syncthreads();
+  if (e != 0) return;
+  Real* K = srcs[0];  // reuse: every warp is past its reads of srcs
+  for (int p = lane; p < Q; p += 32) {
     Real acc = Real(0);
-    for (int i = 0; i < KC; ++i) acc += op[(size_t)i * M + m] * src[i];
-    if (A.mode == 0) A.out[((((size_t)b * 2 * D + f) * NV + v) * M + m) * nt + t] = acc;
-    K[m] = acc;
+#pragma unroll
+    for (int ee = 0; ee < NW; ++ee) acc += part[ee][p];
+    if (A.mode == 0) A.out[((((size_t)b * 2 * D + f) * NV + v) * Q + p) * nt + t] = acc;
+    K[p] = acc;
   }
   if (A.mode == 0) return;
   __syncwarp();
   // trace of the guard cell (my frame) on its face touching me: xi_a = -+1
-  const int side = s ? -1 : +1;
   for (int fp = lane; fp < NFP; fp += 32) {
-    int qt[3] = {0, 0, 0}, jj = 0, r = fp;
-    for (int ax = 0; ax < D; ++ax) {
-      if (ax == a) continue;
-      qt[ax] = r % N;
-      r /= N;
-      ++jj;
-    }
     Real acc = Real(0);
-    for (int m = 0; m < M; ++m) {
-      Real ph = Real(1);
-      int rm = m;
-      for (int ax = 0; ax < D; ++ax) {
-        const int k = rm % N;
-        rm /= N;
-        if (ax == a) ph *= (side > 0 || (k & 1) == 0) ? Real(1) : Real(-1);
-        else ph *= T.V[qt[ax]][k];
-      }
-      acc += ph * K[m];
-    }
+    for (int qn = 0; qn < N; ++qn) acc += (s ? T.lm[qn] : T.lp[qn]) * K[face_point_index<D, N>(a, fp, qn)];
     A.out[((((size_t)b * 2 * D + f) * NV + v) * NFP + fp) * nt + t] = acc;
   }
 }
 
+// ============================================================ conversions
+// modal <-> nodal on arrays shaped [outer][var][mode or point][inner],
+// in place (each thread reads all its values before writing)
+template <int D, int P, typename Real>
+__global__ void k_convert(size_t outer, int inner, Real* __restrict__ X, int to_nodal, Tab<P + 1, Real> T) {
+  constexpr int N = P + 1, NV = D + 2, M = ipow(N, D);
+  const size_t total = outer * NV * inner;
+  const size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= total) return;
+  const int c = (int)(w % inner);
+  const size_t ov = w / inner;  // outer * NV + v
+  Real* base = X + ov * M * inner + c;
+  Real a[M], t2[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) a[m] = base[(size_t)m * inner];
+  if (to_nodal) apply_all<D, N, Real>(T.V, a, t2);
+  else apply_all<D, N, Real>(T.Vi, a, t2);
+#pragma unroll
+  for (int m = 0; m < M; ++m) base[(size_t)m * inner] = a[m];
+}
+
 // ============================================================ CFL kernel
-// dt candidates of the current state (used once before the first step).
+// dt candidates of the current (nodal) state, used before the first step.
 template <int D, int P, typename Real>
 __global__ void k_cfl(int nL, int n, const Real* __restrict__ U, const Real* __restrict__ hcell,
-                      Real gamma, unsigned long long* lam_bits, int* status, Tab<P + 1, Real> T) {
-  constexpr int N = P + 1, NV = D + 2, M = ipow(N, D), Q = M;
+                      Real gamma, unsigned long long* lam_bits, int* status) {
+  constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D);
   const int nc = D == 3 ? n * n * n : n * n;
   const size_t total = (size_t)nL * nc * Q;
   const size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   double best = 3.0e38;
   bool bad = false;
   if (w < total) {
-    const int q = (int)(w % Q);
-    const int c = (int)((w / Q) % nc);
+    const int c = (int)(w % nc);
+    const int q = (int)((w / nc) % Q);
     const int b = (int)(w / ((size_t)Q * nc));
     Real u[NV];
-    for (int v = 0; v < NV; ++v) {
-      const Real* src = U + ((size_t)b * NV + v) * M * nc + c;
-      Real s = Real(0);
-      for (int m = 0; m < M; ++m) {
-        Real ph = Real(1);
-        int rq = q, rm = m;
-        for (int ax = 0; ax < D; ++ax) {
-          ph *= T.V[rq % N][rm % N];
-          rq /= N;
-          rm /= N;
-        }
-        s += ph * src[(size_t)m * nc];
-      }
-      u[v] = s;
-    }
+    for (int v = 0; v < NV; ++v) u[v] = U[(((size_t)b * NV + v) * Q + q) * nc + c];
     const Real ri = Real(1) / u[0];
     Real ke = Real(0), sv = Real(0);
     for (int j = 0; j < D; ++j) {
@@ -1086,23 +1160,21 @@ __global__ void k_cfl(int nL, int n, const Real* __restrict__ U, const Real* __r
 }
 
 // ============================================================ projection
-// nodal FP64 values [leaf][cell][q][var] -> modal (interpolation at Gauss
-// points = the (p+1)-point L2 projection).
+// FP64 point values [leaf][cell][q][var] -> nodal state [leaf][var][q][cell]:
+// with the (p+1)-point rule the L2 projection is interpolation at the Gauss
+// points, i.e. the nodal values themselves.
 template <int D, int P, typename Real>
-__global__ void k_project(int nL, int n, const double* __restrict__ vals, Real* __restrict__ U,
-                          Tab<P + 1, double> T) {
-  constexpr int N = P + 1, NV = D + 2, M = ipow(N, D), Q = M;
+__global__ void k_project(int nL, int n, const double* __restrict__ vals, Real* __restrict__ U) {
+  constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D);
   const int nc = D == 3 ? n * n * n : n * n;
-  const size_t total = (size_t)nL * nc * NV;
+  const size_t total = (size_t)nL * nc * Q * NV;
   const size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= total) return;
-  const int v = (int)(w % NV);
-  const int c = (int)((w / NV) % nc);
-  const int b = (int)(w / ((size_t)NV * nc));
-  double a[M], t2[M];
-  for (int q = 0; q < Q; ++q) a[q] = vals[(((size_t)b * nc + c) * Q + q) * NV + v];
-  apply_all<D, N, double>(T.Vi, a, t2);
-  for (int m = 0; m < M; ++m) U[(((size_t)b * NV + v) * M + m) * nc + c] = (Real)a[m];
+  const int c = (int)(w % nc);
+  const int q = (int)((w / nc) % Q);
+  const int v = (int)((w / ((size_t)nc * Q)) % NV);
+  const int b = (int)(w / ((size_t)nc * Q * NV));
+  U[w] = (Real)vals[(((size_t)b * nc + c) * Q + q) * NV + v];
 }
 
 // ============================================================ totals
@@ -1110,8 +1182,7 @@ __global__ void k_project(int nL, int n, const double* __restrict__ vals, Real* 
 template <int D, int P, typename Real>
 __global__ void k_totals(int nL, int n, const Real* __restrict__ U, const double* __restrict__ geo64,
                          double* __restrict__ part, Tab<P + 1, double> T) {
-  constexpr int N = P + 1, NV = D + 2, M = ipow(N, D), Q = M;
-  constexpr int NG = ((1 << D) - 1) * D;
+  constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D);
   const int nc = D == 3 ? n * n * n : n * n;
   const size_t total = (size_t)nL * nc;
   const size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1119,7 +1190,7 @@ __global__ void k_totals(int nL, int n, const Real* __restrict__ U, const double
   const int c = (int)(w % nc);
   const int b = (int)(w / nc);
   double wj[Q];
-  const double* X = geo64 + (size_t)b * NG * nc + c;
+  const double* X = geo64 + (size_t)b * ((1 << D) - 1) * D * nc + c;
   for (int q = 0; q < Q; ++q) {
     double xi[D];
     double wq = 1.0;
@@ -1134,11 +1205,8 @@ __global__ void k_totals(int nL, int n, const Real* __restrict__ U, const double
     wj[q] = wq * jacobian_det<D, double>(tg);
   }
   for (int v = 0; v < NV; ++v) {
-    double a[M], t2[M];
-    for (int m = 0; m < M; ++m) a[m] = (double)U[(((size_t)b * NV + v) * M + m) * nc + c];
-    apply_all<D, N, double>(T.V, a, t2);
     double s = 0.0;
-    for (int q = 0; q < Q; ++q) s += wj[q] * a[q];
+    for (int q = 0; q < Q; ++q) s += wj[q] * (double)U[(((size_t)b * NV + v) * Q + q) * nc + c];
     part[(size_t)v * total + w] = s;
   }
 }

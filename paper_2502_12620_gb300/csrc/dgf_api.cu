@@ -377,32 +377,33 @@ dgf_status build_device(dgf_forest* f) {
             double A[9], Ja[9];
             eval_map(d, cc, xi, nullptr, A);
             const double wj = wq * det_and_cofactor(d, A, Ja);
-            double pp[64], pc[64];
-            for (int m = 0; m < M; ++m) {
-              pp[m] = phi(B, d, m, xp);
-              pc[m] = phi(B, d, m, xi);
-            }
+            double pp[64];
+            for (int m = 0; m < M; ++m) pp[m] = phi(B, d, m, xp);
             for (int m = 0; m < M; ++m) {
               for (int m2 = 0; m2 < M; ++m2) MP[m * M + m2] += wj * pp[m] * pp[m2];
-              for (int k = 0; k < M; ++k) RHS[(size_t)m * KC + e * M + k] += wj * pp[m] * pc[k];
+              // right-hand side acts on child e's values at its Gauss points
+              RHS[(size_t)m * KC + e * M + q] += wj * pp[m];
             }
           }
         }
         if (!chol_solve(M, MP, RHS, KC)) return fail(DGF_EINVAL, "singular combine mass matrix");
-        // rotate rows into my frame: my mode m <- source mode m', sign
+        // evaluate the parent polynomial (neighbour frame) at my Gauss points:
+        // my point p sits at neighbour coordinates xi_{pi[a]} = sigma_a x_{p_a}
         double* dst = &cop[((size_t)copoff[i * nf + fc] + t) * M * KC];
-        for (int m = 0; m < M; ++m) {
-          int ms = 0, rem = m;
-          double sg = 1.0;
+        for (int pt = 0; pt < M; ++pt) {
+          double xs[3] = {0, 0, 0};
+          int rem = pt;
           for (int ax = 0; ax < d; ++ax) {
-            const int ka = rem % N;
+            xs[o.pi[ax]] = o.sg[ax] * B.x[rem % N];
             rem /= N;
-            int st = 1;
-            for (int u = 0; u < o.pi[ax]; ++u) st *= N;
-            ms += ka * st;
-            if (o.sg[ax] < 0 && (ka & 1)) sg = -sg;
           }
-          for (int k = 0; k < KC; ++k) dst[(size_t)k * M + m] = sg * RHS[(size_t)ms * KC + k];
+          double ph[64];
+          for (int m = 0; m < M; ++m) ph[m] = phi(B, d, m, xs);
+          for (int k = 0; k < KC; ++k) {
+            double acc = 0.0;
+            for (int m = 0; m < M; ++m) acc += ph[m] * RHS[(size_t)m * KC + k];
+            dst[(size_t)k * M + pt] = acc;
+          }
         }
       }
     }
@@ -473,6 +474,10 @@ RtStage stage_args(dgf_forest* f, int src, int dst, double ca, double cb, int mo
   r.slots = f->slots;
   r.affine = (const unsigned char*)f->affine.ptr;
   r.ameta = f->ameta.ptr;
+  r.kind = (const int*)f->kind.ptr;
+  r.nbr = (const int*)f->nbr.ptr;
+  r.orient = (const int*)f->orient.ptr;
+  r.qbits = (const int*)f->qbits.ptr;
   r.U = f->U[src].ptr;
   r.Un = f->U[0].ptr;
   r.Uout = f->U[dst].ptr;
@@ -547,6 +552,14 @@ cudaError_t do_project(dgf_forest* f, const RtMisc& r) {
 cudaError_t do_totals(dgf_forest* f, const RtMisc& r) {
   if (f->d == 2) return f->precision == DGF_FP64 ? launch_totals<2, double>(r, f->stream) : launch_totals<2, float>(r, f->stream);
   return f->precision == DGF_FP64 ? launch_totals<3, double>(r, f->stream) : launch_totals<3, float>(r, f->stream);
+}
+
+cudaError_t do_convert(dgf_forest* f, void* X, size_t outer, int inner, int to_nodal) {
+  if (f->d == 2)
+    return f->precision == DGF_FP64 ? launch_convert<2, double>(f->p, outer, inner, X, to_nodal, f->tab, f->stream)
+                                    : launch_convert<2, float>(f->p, outer, inner, X, to_nodal, f->tab, f->stream);
+  return f->precision == DGF_FP64 ? launch_convert<3, double>(f->p, outer, inner, X, to_nodal, f->tab, f->stream)
+                                  : launch_convert<3, float>(f->p, outer, inner, X, to_nodal, f->tab, f->stream);
 }
 
 dgf_status require_device(dgf_forest* f) {
@@ -661,10 +674,16 @@ dgf_status dgf_forest_create(const dgf_forest_desc* desc, const dgf_allocator* a
     T.Sh[i] = f->basis.Sh[i];
     T.Sm[i] = f->basis.Sm[i];
     T.Sp[i] = f->basis.Sp[i];
+    T.Snm[i] = f->basis.Snm[i];
+    T.Snp[i] = f->basis.Snp[i];
   }
   if (allocator) {
     f->alloc = *allocator;
     f->has_alloc = allocator->alloc && allocator->free;
+  }
+  if (f->device >= 0 && f->n != 2 && f->n != 4 && f->n != 8) {
+    delete f;
+    return fail(DGF_EUNSUPPORTED, "the device kernels are instantiated for n_seg in {2, 4, 8}");
   }
   if (f->device >= 0) {
     DeviceGuard dg(f->device);
@@ -839,6 +858,8 @@ dgf_status dgf_set_state(dgf_forest* f, const void* src, int is_device) {
                                              f->stream),
                              "set_state");
   if (st) return st;
+  // the device holds values at the Gauss points: u = V K per (leaf, var, cell)
+  if ((st = cuda_check(do_convert(f, f->U[0].ptr, (size_t)f->nL, f->nc, 1), "to nodal"))) return st;
   f->have_state = true;
   return init_lambda(f);
 }
@@ -849,7 +870,11 @@ dgf_status dgf_get_state(dgf_forest* f, void* dst, int is_device) {
   if (!f->have_state) return fail(DGF_ESTATE, "no state set");
   DeviceGuard dg(f->device);
   const size_t bytes = (size_t)f->nL * f->nv * f->M * f->nc * f->esize;
-  return copy_state(f, dst, f->U[0].ptr, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+  dgf_status st = cuda_check(cudaMemcpyAsync(f->U[1].ptr, f->U[0].ptr, bytes, cudaMemcpyDeviceToDevice, f->stream),
+                             "get_state");
+  if (st) return st;
+  if ((st = cuda_check(do_convert(f, f->U[1].ptr, (size_t)f->nL, f->nc, 0), "to modal"))) return st;
+  return copy_state(f, dst, f->U[1].ptr, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
 }
 
 dgf_status dgf_set_state_nodal(dgf_forest* f, const double* vals, int is_device) {
@@ -882,6 +907,7 @@ dgf_status dgf_fill_guardcells(dgf_forest* f, void* guard, int is_device) {
   if (!ensure(f, f->gmod, bytes)) return fail(DGF_ENOMEM, "guard allocation failed");
   dgf_status st = cuda_check(do_guard(f, guard_args(f, 0, f->gmod.ptr, 0)), "guard");
   if (st) return st;
+  if ((st = cuda_check(do_convert(f, f->gmod.ptr, (size_t)f->nL * 2 * f->d, f->nt, 0), "to modal"))) return st;
   return copy_state(f, guard, f->gmod.ptr, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
 }
 
@@ -893,6 +919,7 @@ dgf_status dgf_dg_residual(dgf_forest* f, void* dst, int is_device) {
   dgf_status st = cuda_check(do_guard(f, guard_args(f, 0, f->gtr.ptr, 1)), "guard");
   if (st) return st;
   if ((st = cuda_check(do_stage(f, stage_args(f, 0, 1, 0.0, 1.0, 1, 0)), "stage"))) return st;
+  if ((st = cuda_check(do_convert(f, f->U[1].ptr, (size_t)f->nL, f->nc, 0), "to modal"))) return st;
   const size_t bytes = (size_t)f->nL * f->nv * f->M * f->nc * f->esize;
   return copy_state(f, dst, f->U[1].ptr, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
 }
@@ -1021,6 +1048,30 @@ dgf_status dgf_kernel_times(dgf_forest* f, double* ms, int64_t* launches, int n_
 }  // extern "C"
 
 // ------------------------------------------------------------- regrid
+// modal <-> nodal on the host, per (leaf, var, cell), FP64
+static void host_convert(dgf_forest* f, std::vector<double>& X, int64_t L, bool to_nodal) {
+  const int d = f->d, N = f->N, M = f->M, nc = f->nc, nv = f->nv;
+  const std::vector<double>& A = to_nodal ? f->basis.V : f->basis.Vi;  // [out][in]
+  std::vector<double> a(M), b(M);
+  for (int64_t i = 0; i < L * nv; ++i) {
+    for (int c = 0; c < nc; ++c) {
+      for (int m = 0; m < M; ++m) a[m] = X[((size_t)i * M + m) * nc + c];
+      int S = 1;
+      for (int ax = 0; ax < d; ++ax) {
+        for (int o = 0; o < M; ++o) {
+          const int qa = (o / S) % N, base = o - qa * S;
+          double acc = 0.0;
+          for (int k = 0; k < N; ++k) acc += A[qa * N + k] * a[base + k * S];
+          b[o] = acc;
+        }
+        std::swap(a, b);
+        S *= N;
+      }
+      for (int m = 0; m < M; ++m) X[((size_t)i * M + m) * nc + c] = a[m];
+    }
+  }
+}
+
 // New leaves get their state from the old ones: copies, splits (Eqs.
 // (11)-(12)) or combines (Eqs. (13)-(14)); done on the host in FP64 from a
 // device snapshot (regrids are rare compared with time increments).
@@ -1043,6 +1094,8 @@ static dgf_status regrid(dgf_forest* f, const std::vector<uint64_t>& old_leaves)
       for (size_t i = 0; i < cnt; ++i) old_state[i] = tmp[i];
     }
   }
+  // the device state is nodal: bring it to modes for the host-side transfer
+  if (carry) host_convert(f, old_state, (int64_t)old_leaves.size(), false);
   dgf_status st = build_device(f);
   if (st) return st;
   if (!carry) return DGF_OK;
@@ -1151,6 +1204,7 @@ static dgf_status regrid(dgf_forest* f, const std::vector<uint64_t>& old_leaves)
         for (int m = 0; m < M; ++m) at(ns, i, v, m, c) = RHS[(size_t)m * nv + v];
     }
   }
+  host_convert(f, ns, L, true);
   DeviceGuard dg(f->device);
   if (f->precision == DGF_FP64) {
     st = copy_state(f, f->U[0].ptr, ns.data(), ns.size() * 8, cudaMemcpyHostToDevice);

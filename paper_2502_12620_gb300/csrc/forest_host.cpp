@@ -93,6 +93,19 @@ void Basis1D::build(int N_) {
       Sm[l * N + k] = 0.5 * (2 * l + 1) * am;
       Sp[l * N + k] = 0.5 * (2 * l + 1) * ap;
     }
+  Snm.assign(N * N, 0.0);
+  Snp.assign(N * N, 0.0);
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      Snm[i * N + j] = lagrange(j, 0.5 * (x[i] - 1.0));
+      Snp[i * N + j] = lagrange(j, 0.5 * (x[i] + 1.0));
+    }
+}
+
+double Basis1D::lagrange(int j, double xi) const {
+  double s = 0.0;
+  for (int k = 0; k < N; ++k) s += Vi[k * N + j] * legendre(k, xi);
+  return s;
 }
 
 // -------------------------------------------------------------- orientation

@@ -38,6 +38,8 @@ struct Basis1D {
   std::vector<double> Sh;     // Sh[q*N+j] = (w_j/w_q) Dn[j*N+q] (weak form)
   std::vector<double> lp, lm; // l_q(+1), l_q(-1)
   std::vector<double> Sm, Sp; // split: S[l*N+k] coefficients of P_k((xi-+1)/2)
+  std::vector<double> Snm, Snp;  // nodal split: Sn[i*N+j] = l_j((x_i -+ 1)/2)
+  double lagrange(int j, double xi) const;  // l_j(xi) of the Gauss points
   void build(int N);
 };
 double legendre(int k, double x);

@@ -23,26 +23,47 @@ static Tab<N, Real> make_tab(const RtTables& r) {
       t.Sh[i][j] = (Real)r.Sh[i * N + j];
       t.Sm[i][j] = (Real)r.Sm[i * N + j];
       t.Sp[i][j] = (Real)r.Sp[i * N + j];
+      t.Snm[i][j] = (Real)r.Snm[i * N + j];
+      t.Snp[i][j] = (Real)r.Snp[i * N + j];
     }
   }
   return t;
 }
 
-template <int D, int P, typename Real>
-static int stage_blocks_per_sm(int n) {
-  const size_t smem = stage_smem<D, P, Real>(n);
+template <int D, int P, int NS, typename Real>
+static int stage_blocks_per_sm_ns() {
+  const size_t smem = stage_smem<D, P, Real>(NS);
   int dev = 0, maxs = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (smem + 1024 > (size_t)maxs) return 0;
-  if (cudaFuncSetAttribute(k_stage<D, P, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (cudaFuncSetAttribute(k_stage<D, P, NS, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage<D, P, Real>, StageCfg<P, Real>::NT, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage<D, P, NS, Real>, StageCfg<P, Real>::NT, smem) !=
       cudaSuccess)
     return 0;
   return nb;
+}
+
+template <int D, int P, typename Real>
+static int stage_blocks_per_sm(int n) {
+  switch (n) {
+    case 2: return stage_blocks_per_sm_ns<D, P, 2, Real>();
+    case 4: return stage_blocks_per_sm_ns<D, P, 4, Real>();
+    case 8: return stage_blocks_per_sm_ns<D, P, 8, Real>();
+  }
+  return 0;  // n_seg other than 2, 4, 8 is not instantiated
+}
+
+template <int D, int P, int NS, typename Real>
+static cudaError_t stage_ns(const StageArgs<D, P, Real>& a, int slots, cudaStream_t s) {
+  const size_t smem = stage_smem<D, P, Real>(NS);
+  const int items = a.nL * a.nchunks;
+  const int grid = items < slots ? items : slots;
+  k_stage<D, P, NS, Real><<<grid, StageCfg<P, Real>::NT, smem, s>>>(a);
+  return cudaGetLastError();
 }
 
 template <int D, int P, typename Real>
@@ -60,6 +81,10 @@ static cudaError_t stage_p(const RtStage& r, cudaStream_t s) {
   a.hcell = (const Real*)r.hcell;
   a.affine = r.affine;
   a.ameta = (const Real*)r.ameta;
+  a.kind = r.kind;
+  a.nbr = r.nbr;
+  a.orient = r.orient;
+  a.qbits = r.qbits;
   a.dtp = r.dtp;
   a.lam_bits = r.lam_bits;
   a.status = r.status;
@@ -69,12 +94,13 @@ static cudaError_t stage_p(const RtStage& r, cudaStream_t s) {
   a.mode = r.mode;
   a.last = r.last;
   a.T = make_tab<P + 1, Real>(r.T);
-  const size_t smem = stage_smem<D, P, Real>(r.n);
   if (r.slots <= 0) return cudaErrorInvalidConfiguration;
-  const int items = a.nL * a.nchunks;
-  const int grid = items < r.slots ? items : r.slots;
-  k_stage<D, P, Real><<<grid, StageCfg<P, Real>::NT, smem, s>>>(a);
-  return cudaGetLastError();
+  switch (r.n) {
+    case 2: return stage_ns<D, P, 2, Real>(a, r.slots, s);
+    case 4: return stage_ns<D, P, 4, Real>(a, r.slots, s);
+    case 8: return stage_ns<D, P, 8, Real>(a, r.slots, s);
+  }
+  return cudaErrorInvalidConfiguration;
 }
 
 template <int D, int P, typename Real>
@@ -100,8 +126,8 @@ static cudaError_t guard_p(const RtGuard& r, cudaStream_t s) {
   k_guard<D, P, Real><<<(unsigned)((total + th - 1) / th), th, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || r.nfine == 0) return e;
-  const size_t warps = (size_t)r.nfine * nt * (D + 2);
-  k_guard_fine<D, P, Real><<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(a);
+  const size_t ctas = (size_t)r.nfine * nt * (D + 2);
+  k_guard_fine<D, P, Real><<<(unsigned)ctas, 32 << D, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -111,18 +137,16 @@ static cudaError_t cfl_p(const RtMisc& r, cudaStream_t s) {
   const size_t total = (size_t)r.nL * nc * ipow(P + 1, D);
   const int th = 256;
   k_cfl<D, P, Real><<<(unsigned)((total + th - 1) / th), th, 0, s>>>(
-      r.nL, r.n, (const Real*)r.U, (const Real*)r.hcell, (Real)r.gamma, r.lam_bits, r.status,
-      make_tab<P + 1, Real>(r.T));
+      r.nL, r.n, (const Real*)r.U, (const Real*)r.hcell, (Real)r.gamma, r.lam_bits, r.status);
   return cudaGetLastError();
 }
 
 template <int D, int P, typename Real>
 static cudaError_t project_p(const RtMisc& r, cudaStream_t s) {
   const int nc = D == 3 ? r.n * r.n * r.n : r.n * r.n;
-  const size_t total = (size_t)r.nL * nc * (D + 2);
-  const int th = 128;
-  k_project<D, P, Real><<<(unsigned)((total + th - 1) / th), th, 0, s>>>(
-      r.nL, r.n, r.vals, (Real*)r.Uout, make_tab<P + 1, double>(r.T));
+  const size_t total = (size_t)r.nL * nc * ipow(P + 1, D) * (D + 2);
+  const int th = 256;
+  k_project<D, P, Real><<<(unsigned)((total + th - 1) / th), th, 0, s>>>(r.nL, r.n, r.vals, (Real*)r.Uout);
   return cudaGetLastError();
 }
 
@@ -133,6 +157,15 @@ static cudaError_t totals_p(const RtMisc& r, cudaStream_t s) {
   const int th = 128;
   k_totals<D, P, Real><<<(unsigned)((total + th - 1) / th), th, 0, s>>>(
       r.nL, r.n, (const Real*)r.U, r.geo64, r.part, make_tab<P + 1, double>(r.T));
+  return cudaGetLastError();
+}
+
+template <int D, int P, typename Real>
+static cudaError_t convert_p(size_t outer, int inner, void* X, int to_nodal, const RtTables& T, cudaStream_t s) {
+  const size_t total = outer * (D + 2) * inner;
+  const int th = 128;
+  k_convert<D, P, Real><<<(unsigned)((total + th - 1) / th), th, 0, s>>>(outer, inner, (Real*)X, to_nodal,
+                                                                       make_tab<P + 1, Real>(T));
   return cudaGetLastError();
 }
 
@@ -175,6 +208,17 @@ static cudaError_t totals_p(const RtMisc& r, cudaStream_t s) {
     constexpr int D = DIM;                                                                  \
     using Real = REAL;                                                                      \
     DGF_DISPATCH_P(totals_p, r, s)                                                          \
+  }                                                                                         \
+  template <>                                                                               \
+  cudaError_t launch_convert<DIM, REAL>(int p, size_t outer, int inner, void* X, int to_nodal, \
+                                        const RtTables& T, cudaStream_t s) {                \
+    switch (p) {                                                                            \
+      case 0: return convert_p<DIM, 0, REAL>(outer, inner, X, to_nodal, T, s);              \
+      case 1: return convert_p<DIM, 1, REAL>(outer, inner, X, to_nodal, T, s);              \
+      case 2: return convert_p<DIM, 2, REAL>(outer, inner, X, to_nodal, T, s);              \
+      case 3: return convert_p<DIM, 3, REAL>(outer, inner, X, to_nodal, T, s);              \
+    }                                                                                       \
+    return cudaErrorInvalidValue;                                                           \
   }                                                                                         \
   template <>                                                                               \
   int stage_occupancy<DIM, REAL>(int p, int n) {                                            \

@@ -10,7 +10,7 @@ namespace dgf {
 // 1D reference tables in FP64, N <= 4 (converted to the kernel precision).
 struct RtTables {
   int N;
-  double x[4], w[4], V[16], Vi[16], Sh[16], lp[4], lm[4], Sm[16], Sp[16];
+  double x[4], w[4], V[16], Vi[16], Sh[16], lp[4], lm[4], Sm[16], Sp[16], Snm[16], Snp[16];
 };
 
 struct RtStage {
@@ -23,6 +23,10 @@ struct RtStage {
   const void* hcell;
   const unsigned char* affine;
   const void* ameta;
+  const int* kind;
+  const int* nbr;
+  const int* orient;
+  const int* qbits;
   const double* dtp;
   unsigned long long* lam_bits;
   int* status;
@@ -72,6 +76,10 @@ template <int D, typename Real>
 cudaError_t launch_project(const RtMisc& r, cudaStream_t s);
 template <int D, typename Real>
 cudaError_t launch_totals(const RtMisc& r, cudaStream_t s);
+// modal <-> nodal in place on [outer][var][mode/point][inner]
+template <int D, typename Real>
+cudaError_t launch_convert(int p, size_t outer, int inner, void* X, int to_nodal, const RtTables& T,
+                           cudaStream_t s);
 template <int D, typename Real>
 size_t stage_smem_bytes(int p, int n);
 // resident stage CTAs per SM (0: does not fit)
