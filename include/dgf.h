@@ -183,6 +183,29 @@ dgf_status dgf_status_word(dgf_forest* f, int32_t* status, int reset);
 dgf_status dgf_set_timing(dgf_forest* f, int on);
 dgf_status dgf_kernel_times(dgf_forest* f, double* ms, int64_t* launches, int n_classes);
 
+/* Residual without any allocation.  The paper has no counterpart: this call
+ * exists for callers that cannot allocate device memory after the forest is
+ * built (code that runs while a CUDA graph is being captured, or a process
+ * whose device memory all comes from a pool it does not own).  It computes
+ * the same L(U) as dgf_dg_residual, but on caller-owned device buffers in
+ * the nodal layout the kernels use, [leaf][var][point][cell] with point
+ * q = sum_a q_a N^a over the (p+1)-point Gauss-Legendre nodes and
+ * u(q) = sum_m K_m phi_m(x_q) (forest element type).
+ *   U_nodal  device, input state, read only;
+ *   L_nodal  device, output, must not alias U_nodal.
+ * The guard traces go to a 16 MiB array compiled into the library (a
+ * file-scope __device__ array; every GPU that loads the library holds it
+ * until the process exits).  Forests whose guard traces need more than
+ * 16 MiB get DGF_EUNSUPPORTED.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress), so make the first call on
+ * each device outside any stream capture.  No cudaMalloc, cudaFree or
+ * allocator callback is made.  All calls share the one array and every call
+ * overwrites what it reads, so nothing needs clearing, but calls whose GPU
+ * work overlaps (several streams, several host threads, several forests on
+ * the same device) race on it: order them on one stream.  Asynchronous on
+ * the forest's stream. */
+dgf_status dgf_dg_residual_noalloc(dgf_forest* f, const void* U_nodal, void* L_nodal);
+
 #ifdef __cplusplus
 }
 #endif

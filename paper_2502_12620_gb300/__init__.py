@@ -74,6 +74,7 @@ _SIGS = {
     "dgf_status_word": [_P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int],
     "dgf_set_timing": [_P, ctypes.c_int],
     "dgf_kernel_times": [_P, _P, _P, ctypes.c_int],
+    "dgf_dg_residual_noalloc": [_P, _P, _P],
 }
 
 

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1214,4 +1215,59 @@ static dgf_status regrid(dgf_forest* f, const std::vector<uint64_t>& old_leaves)
   }
   if (st) return st;
   return init_lambda(f);
+}
+
+// ------------------------------------------------------ residual without allocation
+// For callers that cannot allocate device memory once a forest exists (for
+// example code running inside a CUDA graph capture, or a host process whose
+// memory is handed out by a pool it does not own): the guard traces that
+// dgf_dg_residual keeps in forest-owned scratch live here in a file-scope
+// device array instead.  The array is part of the library image, so every
+// GPU that loads the library holds it until the process exits.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// address of the scratch array on the current device (set up once per device)
+dgf_status noalloc_scratch(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices) return fail(DGF_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_check(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "scratch address");
+    g_noalloc_ptr[device] = p;
+  }
+  *out = g_noalloc_ptr[device];
+  return DGF_OK;
+}
+
+}  // namespace
+
+extern "C" dgf_status dgf_dg_residual_noalloc(dgf_forest* f, const void* U_nodal, void* L_nodal) {
+  if (dgf_status st = require_device(f)) return st;
+  if (!U_nodal || !L_nodal) return fail(DGF_EINVAL, "null state pointer");
+  if (U_nodal == L_nodal) return fail(DGF_EINVAL, "input and output must not alias");
+  DeviceGuard dg(f->device);
+  const size_t need = (size_t)f->nL * 2 * f->d * f->nv * f->NFP * f->nt * f->esize;
+  if (need > kNoAllocScratchBytes)
+    return fail(DGF_EUNSUPPORTED, "dgf_dg_residual_noalloc: the guard traces of this forest need " +
+                                      std::to_string(need) + " bytes, above the 16 MiB static scratch");
+  void* scratch = nullptr;
+  dgf_status st = noalloc_scratch(f->device, &scratch);
+  if (st) return st;
+  RtGuard g = guard_args(f, 0, scratch, 1);
+  g.U = U_nodal;
+  if ((st = cuda_check(do_guard(f, g), "guard"))) return st;
+  RtStage s = stage_args(f, 0, 1, 0.0, 1.0, 1, 0);
+  s.U = U_nodal;
+  s.Un = U_nodal;
+  s.Uout = L_nodal;
+  s.gtr = scratch;
+  return cuda_check(do_stage(f, s), "stage");
 }
