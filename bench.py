@@ -120,6 +120,7 @@ def dist_env():
 
 
 def barrier_max(x, ws):
+    """Max of x over the ranks (the slowest replica sets the job time)."""
     if ws == 1:
         return x
     import torch
@@ -127,6 +128,13 @@ def barrier_max(x, ws):
     t = torch.tensor([float(x)])
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(units_per_rank, ms_local, ws):
+    """Whole-job rate of ws independent replicas: all ranks' units over the
+    max-over-ranks time (replicas do identical work, so units scale by ws)."""
+    ms = barrier_max(ms_local, ws)
+    return units_per_rank * ws / (ms / 1e3), ms
 
 
 # ---------------------------------------------------------------- CPU legs
@@ -237,8 +245,7 @@ def run_ours(args):
         torch.distributed.barrier()
     with Clocks(local) as ck:
         ms = timed_steps(f32, args.steps, stream, flush, torch)
-    ms = barrier_max(ms, ws)
-    value = dof * 3 * args.steps / (ms / 1e3) * ws
+    value, ms = job_throughput(dof * 3 * args.steps, ms, ws)
     status = f32.status_word()
     if args.quick:
         if rank == 0:
