@@ -759,7 +759,7 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
           if (A.mode == 1) {
             val = r;
           } else {
-            val = A.cb * (Ub[gi] + dt * r);
+            val = A.cb * (US(v, q, c) + dt * r);  // the stage input is still in shared memory
             if (A.ca != Real(0)) val += A.ca * Unb[gi];
           }
           Ob[gi] = val;
@@ -1095,6 +1095,200 @@ __global__ void __launch_bounds__(32 << D) k_guard_fine(const GuardArgs<D, P, Re
   if (A.mode == 0) return;
   __syncwarp();
   // trace of the guard cell (my frame) on its face touching me: xi_a = -+1
+  for (int fp = lane; fp < NFP; fp += 32) {
+    Real acc = Real(0);
+    for (int qn = 0; qn < N; ++qn) acc += (s ? T.lm[qn] : T.lp[qn]) * K[face_point_index<D, N>(a, fp, qn)];
+    A.out[((((size_t)b * 2 * D + f) * NV + v) * NFP + fp) * nt + t] = acc;
+  }
+}
+
+// Guard traces for the time step (mode 1), one launch: the first
+// n_fine_blocks blocks run the finer-face combine (one block per finer face,
+// guard cell and var, one warp per fine child), the remaining blocks compute
+// the traces of same-level, coarser and outflow faces, one thread per
+// (leaf, face, guard cell, var) as in k_guard.
+template <int D, int P, typename Real>
+__global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, Real> A, int n_fine_blocks) {
+  constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
+  constexpr int NW = 1 << D;
+  constexpr int KC = NW * Q;
+  constexpr int NTH = 32 << D;
+  __shared__ Real srcs[NW][Q];
+  __shared__ Real part[NW][Q];
+  const int n = A.n;
+  const int nt = D == 3 ? n * n : n;
+  const int nc = D == 3 ? n * n * n : n * n;
+  const auto& T = A.T;
+  if ((int)blockIdx.x >= n_fine_blocks) {
+    const size_t total = (size_t)A.nL * 2 * D * nt * NV;
+    const size_t w = (size_t)(blockIdx.x - n_fine_blocks) * NTH + threadIdx.x;
+    if (w >= total) return;
+    const int t = (int)(w % nt);
+    const int v = (int)((w / nt) % NV);
+    const int f = (int)((w / ((size_t)nt * NV)) % (2 * D));
+    const int b = (int)(w / ((size_t)nt * NV * 2 * D));
+    const int kind = A.kind[b * 2 * D + f];
+    if (kind == 2) return;
+    const int a = f >> 1, s = f & 1;
+    int g[3] = {0, 0, 0};
+    {
+      int j = 0;
+      for (int ax = 0; ax < D; ++ax) {
+        if (ax == a) continue;
+        g[ax] = j == 0 ? (t % n) : (t / n);
+        ++j;
+      }
+    }
+    auto cell_of = [&](const int* h) {
+      int c = 0, st = 1;
+      for (int ax = 0; ax < D; ++ax) {
+        c += h[ax] * st;
+        st *= n;
+      }
+      return c;
+    };
+    Real* out_trace = A.out + (((size_t)b * 2 * D + f) * NV + v) * NFP * nt + t;
+    if (kind == 3) {  // outflow: my own face cell's trace
+      int h[3] = {g[0], g[1], g[2]};
+      h[a] = s ? n - 1 : 0;
+      const Real* src = A.U + ((size_t)b * NV + v) * Q * nc + cell_of(h);
+#pragma unroll
+      for (int fp = 0; fp < NFP; ++fp) {
+        Real acc = Real(0);
+#pragma unroll
+        for (int qn = 0; qn < N; ++qn)
+          acc += (s ? T.lp[qn] : T.lm[qn]) * src[(size_t)face_point_index<D, N>(a, fp, qn) * nc];
+        out_trace[(size_t)fp * nt] = acc;
+      }
+      return;
+    }
+    const int pk = A.orient[b * 2 * D + f];
+    const int b2 = opi(pk, a);
+    const int s2 = osg(pk, a) > 0 ? 1 - s : s;
+    int h[3] = {0, 0, 0}, e[3] = {0, 0, 0};
+    if (kind == 0) {
+      for (int ax = 0; ax < D; ++ax) {
+        if (ax == a) continue;
+        h[opi(pk, ax)] = osg(pk, ax) > 0 ? g[ax] : n - 1 - g[ax];
+      }
+    } else {
+      const int qb = A.qbits[b];
+      for (int ax = 0; ax < D; ++ax) {
+        if (ax == a) continue;
+        const int G = ((qb >> ax) & 1) * n + g[ax];
+        const int hh = G >> 1, ee = G & 1;
+        h[opi(pk, ax)] = osg(pk, ax) > 0 ? hh : n - 1 - hh;
+        e[opi(pk, ax)] = osg(pk, ax) > 0 ? ee : 1 - ee;
+      }
+    }
+    h[b2] = s2 == 0 ? 0 : n - 1;
+    const Real* src = A.U + ((size_t)A.nbr[(b * 2 * D + f) * 4] * NV + v) * Q * nc + cell_of(h);
+    Real tr[NFP];
+#pragma unroll
+    for (int j = 0; j < NFP; ++j) {
+      Real acc = Real(0);
+#pragma unroll
+      for (int qn = 0; qn < N; ++qn)
+        acc += (s2 ? T.lp[qn] : T.lm[qn]) * src[(size_t)face_point_index<D, N>(b2, j, qn) * nc];
+      tr[j] = acc;
+    }
+    if (kind == 1) {  // split (Eqs. (11)-(12)) of the coarse face trace
+      Real t2[NFP];
+      if constexpr (D == 2) {
+        const int u0 = 1 - b2;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          Real acc = Real(0);
+#pragma unroll
+          for (int jj = 0; jj < N; ++jj) acc += (e[u0] ? T.Snp[i][jj] : T.Snm[i][jj]) * tr[jj];
+          t2[i] = acc;
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) tr[i] = t2[i];
+      } else {
+        const int u0 = b2 == 0 ? 1 : 0, u1 = b2 == 2 ? 1 : 2;
+#pragma unroll
+        for (int i1 = 0; i1 < N; ++i1)
+#pragma unroll
+          for (int i0 = 0; i0 < N; ++i0) {
+            Real acc = Real(0);
+#pragma unroll
+            for (int jj = 0; jj < N; ++jj) acc += (e[u0] ? T.Snp[i0][jj] : T.Snm[i0][jj]) * tr[jj + N * i1];
+            t2[i0 + N * i1] = acc;
+          }
+#pragma unroll
+        for (int i1 = 0; i1 < N; ++i1)
+#pragma unroll
+          for (int i0 = 0; i0 < N; ++i0) {
+            Real acc = Real(0);
+#pragma unroll
+            for (int jj = 0; jj < N; ++jj) acc += (e[u1] ? T.Snp[i1][jj] : T.Snm[i1][jj]) * t2[i0 + N * jj];
+            tr[i0 + N * i1] = acc;
+          }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NFP; ++j) out_trace[(size_t)map_face_point<D, N>(j, a, b2, pk) * nt] = tr[j];
+    return;
+  }
+  // ---- finer faces: one block per (finer face, guard cell t, var)
+  const size_t item = blockIdx.x;
+  const int lane = threadIdx.x & 31, e = threadIdx.x >> 5;
+  const int t = (int)(item % nt);
+  const int v = (int)((item / nt) % NV);
+  const int bf = A.fine_list[item / ((size_t)nt * NV)];
+  const int b = bf / (2 * D), f = bf % (2 * D);
+  const int a = f >> 1, s = f & 1;
+  const int pk = A.orient[bf];
+  int g[3] = {0, 0, 0};
+  {
+    int j = 0;
+    for (int ax = 0; ax < D; ++ax) {
+      if (ax == a) continue;
+      g[ax] = j == 0 ? (t % n) : (t / n);
+      ++j;
+    }
+  }
+  const int b2 = opi(pk, a);
+  const int s2 = osg(pk, a) > 0 ? 1 - s : s;
+  int h[3] = {0, 0, 0}, sub = 0, j = 0;
+  for (int ax = 0; ax < D; ++ax) {
+    if (ax == a) continue;
+    h[opi(pk, ax)] = osg(pk, ax) > 0 ? g[ax] : n - 1 - g[ax];
+    if (g[ax] >= n / 2) sub |= 1 << j;
+    ++j;
+  }
+  h[b2] = s2 == 0 ? 0 : n - 1;
+  const int fine = A.nbr[bf * 4 + sub];
+  int c = 0, st = 1;
+  for (int ax = 0; ax < D; ++ax) {
+    const int cN = (2 * h[ax]) / n;
+    c += (2 * h[ax] + ((e >> ax) & 1) - cN * n) * st;
+    st *= n;
+  }
+  for (int q = lane; q < Q; q += 32) srcs[e][q] = A.U[(((size_t)fine * NV + v) * Q + q) * nc + c];
+  __syncwarp();
+  const Real* op = A.cop + (size_t)(A.copoff[bf] + t) * KC * Q + (size_t)e * Q * Q;
+  for (int p = lane; p < Q; p += 32) {
+    Real acc0 = Real(0), acc1 = Real(0);
+#pragma unroll 4
+    for (int q = 0; q + 1 < Q; q += 2) {
+      acc0 += __ldg(&op[(size_t)q * Q + p]) * srcs[e][q];
+      acc1 += __ldg(&op[(size_t)(q + 1) * Q + p]) * srcs[e][q + 1];
+    }
+    if (Q & 1) acc0 += __ldg(&op[(size_t)(Q - 1) * Q + p]) * srcs[e][Q - 1];
+    part[e][p] = acc0 + acc1;
+  }
+  __syncthreads();
+  if (e != 0) return;
+  Real* K = srcs[0];
+  for (int p = lane; p < Q; p += 32) {
+    Real acc = Real(0);
+#pragma unroll
+    for (int ee = 0; ee < NW; ++ee) acc += part[ee][p];
+    K[p] = acc;
+  }
+  __syncwarp();
   for (int fp = lane; fp < NFP; fp += 32) {
     Real acc = Real(0);
     for (int qn = 0; qn < N; ++qn) acc += (s ? T.lm[qn] : T.lp[qn]) * K[face_point_index<D, N>(a, fp, qn)];

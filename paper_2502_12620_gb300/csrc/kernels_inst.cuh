@@ -121,6 +121,15 @@ static cudaError_t guard_p(const RtGuard& r, cudaStream_t s) {
   a.nfine = r.nfine;
   a.T = make_tab<P + 1, Real>(r.T);
   const int nt = D == 3 ? r.n * r.n : r.n;
+  if (r.mode == 1) {
+    // time-step path: traces of every face kind in one launch
+    constexpr int NTH = 32 << D;
+    const size_t items = (size_t)r.nL * 2 * D * (D + 2) * nt;
+    const size_t ntb = (items + NTH - 1) / NTH;
+    const int nfb = r.nfine * nt * (D + 2);
+    k_guard_trace<D, P, Real><<<(unsigned)(ntb + nfb), NTH, 0, s>>>(a, nfb);
+    return cudaGetLastError();
+  }
   const size_t total = (size_t)r.nL * 2 * D * nt * (D + 2);
   const int th = 128;
   k_guard<D, P, Real><<<(unsigned)((total + th - 1) / th), th, 0, s>>>(a);
