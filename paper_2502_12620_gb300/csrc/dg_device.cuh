@@ -229,6 +229,7 @@ struct GuardArgs {
   const int* __restrict__ qbits;   // [b] pos & 1 bits
   const int* __restrict__ copoff;  // [b][f] first combine operator or -1
   const Real* __restrict__ cop;    // [op][2^D M][M]: column k' of the operator is contiguous
+  const Real* __restrict__ ctr;    // [op][2^D M][NFP]: the same operator followed by my face trace
   const int* __restrict__ fine_list;  // [nfine] leaf * 2D + face of every finer-neighbour face
   int nfine;
   Tab<P + 1, Real> T;
@@ -236,9 +237,12 @@ struct GuardArgs {
 
 // threads per CTA and CTAs per SM of the stage kernel (registers and shared
 // memory decide: FP32 up to p=2 runs 2 x 512 threads per SM)
+#ifndef DGF_STAGE_NT_F32
+#define DGF_STAGE_NT_F32 512
+#endif
 template <int P, typename Real>
 struct StageCfg {
-  static constexpr int NT = sizeof(Real) == 4 ? 512 : (P <= 1 ? 512 : 256);
+  static constexpr int NT = sizeof(Real) == 4 ? (P <= 2 ? DGF_STAGE_NT_F32 : 512) : (P <= 1 ? 512 : 256);
   static constexpr int MINB = (sizeof(Real) == 4 && P <= 2) ? 2 : 1;
 };
 
@@ -448,7 +452,7 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
         constexpr int PER_ROW = NCL / VEC;
         for (int w = tid; w < NV * Q * PER_ROW; w += nthr) {
           const int r = w / PER_ROW, cv = (w - r * PER_ROW) * VEC;
-          const V4 val = *reinterpret_cast<const V4*>(Ub + (size_t)r * nc + cbase + cv);
+          const V4 val = __ldcg(reinterpret_cast<const V4*>(Ub + (size_t)r * nc + cbase + cv));
           *reinterpret_cast<V4*>(us + r * NCL + cv) = val;
         }
       }
@@ -464,7 +468,7 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
               tr = Real(0);
 #pragma unroll
               for (int qz = 0; qz < N; ++qz)
-                tr += T.lp[qz] * Ub[((size_t)v * Q + fp + NFP * qz) * nc + (k0 - 1) * NCL + c];
+                tr += T.lp[qz] * __ldcg(&Ub[((size_t)v * Q + fp + NFP * qz) * nc + (k0 - 1) * NCL + c]);
             }
             TB(v, fp, c) = tr;
           }
@@ -679,7 +683,7 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
             tr = Real(0);
 #pragma unroll
             for (int qz = 0; qz < N; ++qz)
-              tr += T.lm[qz] * Ub[((size_t)v * Q + fp + NFP * qz) * nc + (k + 1) * NCL + c];
+              tr += T.lm[qz] * __ldcg(&Ub[((size_t)v * Q + fp + NFP * qz) * nc + (k + 1) * NCL + c]);
           }
           TB(v, fp, c) = tr;
         }
@@ -760,7 +764,7 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
             val = r;
           } else {
             val = A.cb * (US(v, q, c) + dt * r);  // the stage input is still in shared memory
-            if (A.ca != Real(0)) val += A.ca * Unb[gi];
+            if (A.ca != Real(0)) val += A.ca * __ldcg(&Unb[gi]);
           }
           Ob[gi] = val;
           o[v] = val;
@@ -1113,8 +1117,6 @@ __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, R
   constexpr int NW = 1 << D;
   constexpr int KC = NW * Q;
   constexpr int NTH = 32 << D;
-  __shared__ Real srcs[NW][Q];
-  __shared__ Real part[NW][Q];
   const int n = A.n;
   const int nt = D == 3 ? n * n : n;
   const int nc = D == 3 ? n * n * n : n * n;
@@ -1231,12 +1233,15 @@ __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, R
     for (int j = 0; j < NFP; ++j) out_trace[(size_t)map_face_point<D, N>(j, a, b2, pk) * nt] = tr[j];
     return;
   }
-  // ---- finer faces: one block per (finer face, guard cell t, var)
+  // ---- finer faces: one block per (finer face, guard cell t), all vars;
+  // warp e applies fine child e's columns of the trace operator
+  constexpr int NPAIR = NV * NFP;
+  __shared__ Real sv[NW][NV][Q];
+  __shared__ Real pv[NW][NPAIR];
   const size_t item = blockIdx.x;
   const int lane = threadIdx.x & 31, e = threadIdx.x >> 5;
   const int t = (int)(item % nt);
-  const int v = (int)((item / nt) % NV);
-  const int bf = A.fine_list[item / ((size_t)nt * NV)];
+  const int bf = A.fine_list[item / nt];
   const int b = bf / (2 * D), f = bf % (2 * D);
   const int a = f >> 1, s = f & 1;
   const int pk = A.orient[bf];
@@ -1266,32 +1271,29 @@ __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, R
     c += (2 * h[ax] + ((e >> ax) & 1) - cN * n) * st;
     st *= n;
   }
-  for (int q = lane; q < Q; q += 32) srcs[e][q] = A.U[(((size_t)fine * NV + v) * Q + q) * nc + c];
+  for (int i = lane; i < NV * Q; i += 32) {
+    const int v = i / Q, q = i % Q;
+    sv[e][v][q] = A.U[(((size_t)fine * NV + v) * Q + q) * nc + c];
+  }
   __syncwarp();
-  const Real* op = A.cop + (size_t)(A.copoff[bf] + t) * KC * Q + (size_t)e * Q * Q;
-  for (int p = lane; p < Q; p += 32) {
+  const Real* op = A.ctr + (size_t)(A.copoff[bf] + t) * KC * NFP + (size_t)e * Q * NFP;
+  for (int pr = lane; pr < NPAIR; pr += 32) {
+    const int v = pr / NFP, fp = pr % NFP;
     Real acc0 = Real(0), acc1 = Real(0);
 #pragma unroll 4
     for (int q = 0; q + 1 < Q; q += 2) {
-      acc0 += __ldg(&op[(size_t)q * Q + p]) * srcs[e][q];
-      acc1 += __ldg(&op[(size_t)(q + 1) * Q + p]) * srcs[e][q + 1];
+      acc0 += __ldg(&op[(size_t)q * NFP + fp]) * sv[e][v][q];
+      acc1 += __ldg(&op[(size_t)(q + 1) * NFP + fp]) * sv[e][v][q + 1];
     }
-    if (Q & 1) acc0 += __ldg(&op[(size_t)(Q - 1) * Q + p]) * srcs[e][Q - 1];
-    part[e][p] = acc0 + acc1;
+    if (Q & 1) acc0 += __ldg(&op[(size_t)(Q - 1) * NFP + fp]) * sv[e][v][Q - 1];
+    pv[e][pr] = acc0 + acc1;
   }
   __syncthreads();
-  if (e != 0) return;
-  Real* K = srcs[0];
-  for (int p = lane; p < Q; p += 32) {
+  for (int pr = threadIdx.x; pr < NPAIR; pr += NTH) {
     Real acc = Real(0);
 #pragma unroll
-    for (int ee = 0; ee < NW; ++ee) acc += part[ee][p];
-    K[p] = acc;
-  }
-  __syncwarp();
-  for (int fp = lane; fp < NFP; fp += 32) {
-    Real acc = Real(0);
-    for (int qn = 0; qn < N; ++qn) acc += (s ? T.lm[qn] : T.lp[qn]) * K[face_point_index<D, N>(a, fp, qn)];
+    for (int ee = 0; ee < NW; ++ee) acc += pv[ee][pr];
+    const int v = pr / NFP, fp = pr % NFP;
     A.out[((((size_t)b * 2 * D + f) * NV + v) * NFP + fp) * nt + t] = acc;
   }
 }

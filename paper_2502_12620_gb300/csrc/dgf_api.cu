@@ -114,7 +114,7 @@ struct dgf_forest {
     void* ptr = nullptr;
     size_t bytes = 0;
   };
-  Buf U[3], geo, geo64, hcell, gtr, gmod, cop, kind, nbr, orient, qbits, copoff, part, scal, tot,
+  Buf U[3], geo, geo64, hcell, gtr, gmod, cop, ctr, kind, nbr, orient, qbits, copoff, part, scal, tot,
       dtout, nodal, fine, affine, ameta;
   int nfine = 0;
   int slots = 0;
@@ -327,6 +327,8 @@ dgf_status build_device(dgf_forest* f) {
       }
   f->nfine = (int)fine_list.size();
   cop.assign((size_t)nops * M * KC, 0.0);
+  const int NFPh = f->NFP;
+  std::vector<double> ctr((size_t)nops * NFPh * KC, 0.0);
   for (int64_t i = 0; i < L; ++i) {
     for (int fc = 0; fc < nf; ++fc) {
       if (kind[i * nf + fc] != kFiner) continue;
@@ -406,6 +408,27 @@ dgf_status build_device(dgf_forest* f) {
             dst[(size_t)k * M + pt] = acc;
           }
         }
+        // trace operator: the guard cell's values on its face touching me
+        // (xi_a = -1 on my + face, +1 on my - face) at my face points
+        const std::vector<double>& ext = s ? B.lm : B.lp;
+        double* tdst = &ctr[((size_t)copoff[i * nf + fc] + t) * NFPh * KC];
+        for (int fpp = 0; fpp < NFPh; ++fpp) {
+          int dig[3] = {0, 0, 0}, rem = fpp;
+          for (int ax = 0; ax < d; ++ax) {
+            if (ax == a) continue;
+            dig[ax] = rem % N;
+            rem /= N;
+          }
+          for (int qn = 0; qn < N; ++qn) {
+            dig[a] = qn;
+            int pt = 0, st = 1;
+            for (int ax = 0; ax < d; ++ax) {
+              pt += dig[ax] * st;
+              st *= N;
+            }
+            for (int k = 0; k < KC; ++k) tdst[(size_t)k * NFPh + fpp] += ext[qn] * dst[(size_t)k * M + pt];
+          }
+        }
       }
     }
   }
@@ -420,11 +443,13 @@ dgf_status build_device(dgf_forest* f) {
   if ((st = upload(f, f->affine, affine))) return st;
   if (f->precision == DGF_FP64) {
     if ((st = upload(f, f->geo, geo64)) || (st = upload(f, f->hcell, hcell)) || (st = upload(f, f->cop, cop)) ||
+        (st = upload(f, f->ctr, ctr)) ||
         (st = upload(f, f->ameta, ameta)))
       return st;
   } else {
     if ((st = upload(f, f->geo, convert<float>(geo64))) || (st = upload(f, f->hcell, convert<float>(hcell))) ||
-        (st = upload(f, f->cop, convert<float>(cop))) || (st = upload(f, f->ameta, convert<float>(ameta))))
+        (st = upload(f, f->cop, convert<float>(cop))) || (st = upload(f, f->ctr, convert<float>(ctr))) ||
+        (st = upload(f, f->ameta, convert<float>(ameta))))
       return st;
   }
   const size_t sbytes = (size_t)L * f->nv * M * nc * f->esize;
@@ -511,6 +536,7 @@ RtGuard guard_args(dgf_forest* f, int src, void* out, int mode) {
   r.qbits = (const int*)f->qbits.ptr;
   r.copoff = (const int*)f->copoff.ptr;
   r.cop = f->cop.ptr;
+  r.ctr = f->ctr.ptr;
   r.fine_list = (const int*)f->fine.ptr;
   r.nfine = f->nfine;
   r.T = f->tab;
@@ -737,7 +763,7 @@ dgf_status dgf_forest_destroy(dgf_forest* f) {
       cudaEventDestroy(e.b);
     }
     dgf_forest::Buf* bufs[] = {&f->U[0], &f->U[1], &f->U[2], &f->geo, &f->geo64, &f->hcell, &f->gtr,
-                               &f->gmod, &f->cop, &f->kind, &f->nbr, &f->orient, &f->qbits, &f->copoff,
+                               &f->gmod, &f->cop, &f->ctr, &f->kind, &f->nbr, &f->orient, &f->qbits, &f->copoff,
                                &f->part, &f->scal, &f->tot, &f->dtout, &f->nodal, &f->fine, &f->affine, &f->ameta};
     for (auto* b : bufs) dev_free(f, *b);
     if (f->own_stream && f->stream) cudaStreamDestroy(f->stream);

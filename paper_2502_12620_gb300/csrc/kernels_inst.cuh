@@ -117,6 +117,7 @@ static cudaError_t guard_p(const RtGuard& r, cudaStream_t s) {
   a.qbits = r.qbits;
   a.copoff = r.copoff;
   a.cop = (const Real*)r.cop;
+  a.ctr = (const Real*)r.ctr;
   a.fine_list = r.fine_list;
   a.nfine = r.nfine;
   a.T = make_tab<P + 1, Real>(r.T);
@@ -126,7 +127,7 @@ static cudaError_t guard_p(const RtGuard& r, cudaStream_t s) {
     constexpr int NTH = 32 << D;
     const size_t items = (size_t)r.nL * 2 * D * (D + 2) * nt;
     const size_t ntb = (items + NTH - 1) / NTH;
-    const int nfb = r.nfine * nt * (D + 2);
+    const int nfb = r.nfine * nt;
     k_guard_trace<D, P, Real><<<(unsigned)(ntb + nfb), NTH, 0, s>>>(a, nfb);
     return cudaGetLastError();
   }

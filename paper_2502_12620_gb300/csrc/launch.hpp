@@ -45,6 +45,7 @@ struct RtGuard {
   const int* qbits;
   const int* copoff;
   const void* cop;
+  const void* ctr;
   const int* fine_list;
   int nfine;
   RtTables T;
