@@ -285,18 +285,31 @@ def run_ours(args):
     ms64 = barrier_max(timed_steps(f64, k64, stream, flush, torch), ws)
     value64 = dof * 3 * k64 / (ms64 / 1e3) * ws
 
-    # accuracy: FP32 vs FP64 after the same number of steps from the same state
+    # compensated FP32 (FP64 state, FP32 residual and increments)
+    fc = make(pkg.FP32_COMP)
+    for _ in range(max(1, args.warmup // 2)):
+        fc.rk_step()
+    kc = max(2, min(args.steps, 10))
+    msc = barrier_max(timed_steps(fc, kc, stream, flush, torch), ws)
+    valuec = dof * 3 * kc / (msc / 1e3) * ws
+
+    # accuracy: FP32 and compensated FP32 vs FP64 after the same steps from the same state
     f32.set_timing(False)
     a32 = make(pkg.FP32)
     a64 = make(pkg.FP64)
+    ac = make(pkg.FP32_COMP)
     nacc = 20
     for _ in range(nacc):
         a32.rk_step()
         a64.rk_step()
+        ac.rk_step()
     s32 = a32.get_state().astype(np.float64)
     s64 = a64.get_state()
+    sc = ac.get_state()
     l2 = float(np.linalg.norm(s32 - s64) / np.linalg.norm(s64))
     linf = float(np.max(np.abs(s32 - s64)) / np.max(np.abs(s64)))
+    l2c = float(np.linalg.norm(sc - s64) / np.linalg.norm(s64))
+    linfc = float(np.max(np.abs(sc - s64)) / np.max(np.abs(s64)))
 
     # end to end through the public API with host buffers (pinned)
     host = torch.empty(U0.size, dtype=torch.float32).pin_memory().numpy().reshape(U0.shape)
@@ -329,7 +342,9 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}"},
         "roofline": roof,
         "fp64": {"value": value64, "unit": "DOF-updates/s", "ms_per_step": ms64 / k64, "steps": k64},
-        "accuracy": {"steps": nacc, "l2_rel_fp32_vs_fp64": l2, "linf_rel_fp32_vs_fp64": linf},
+        "fp32_comp": {"value": valuec, "unit": "DOF-updates/s", "ms_per_step": msc / kc, "steps": kc},
+        "accuracy": {"steps": nacc, "l2_rel_fp32_vs_fp64": l2, "linf_rel_fp32_vs_fp64": linf,
+                     "l2_rel_fp32_comp_vs_fp64": l2c, "linf_rel_fp32_comp_vs_fp64": linfc},
         "e2e": e2e,
         "clocks": ck.summary(),
         "gpu_launches": int(sum(c for _, c in kt.values())),

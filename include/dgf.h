@@ -33,7 +33,7 @@
  *   - Modal state: tensor Legendre coefficients (unnormalised P_k), SoA
  *     layout [leaf][var][mode][cell], mode m = sum_a k_a N^a, cell
  *     c = sum_a i_a n^a (x fastest), leaves in canonical forest order.
- *     Element type: double for DGF_FP64 forests, float for DGF_FP32.
+ *     Element type: float for DGF_FP32 forests, double otherwise.
  *   - Canonical forest order: root by root, depth first, children
  *     c = sum_a bit_a 2^a.  Face f = 2*axis + side (side 1 = +xi).
  *   - Neighbour kinds: 0 same level, 1 coarser, 2 finer, 3 domain boundary
@@ -66,6 +66,12 @@ typedef int32_t dgf_status;
 
 #define DGF_FP64 0
 #define DGF_FP32 1
+/* Compensated FP32 (SSP-RK3 of Sec. 2 with the state accumulated in FP64):
+ * u^n is kept in FP64, each stage keeps its increment delta^(k) = u^(k) - u^n
+ * in FP32 (delta^(k+1) = b_k (delta^(k) + dt L(u^n + delta^(k))), b = 1, 1/4,
+ * 2/3) and u^(n+1) = u^n + delta^(3) is formed in FP64; the residual runs in
+ * FP32.  The state, residual and guard cells at this ABI are double. */
+#define DGF_FP32_COMP 2
 
 typedef struct dgf_forest dgf_forest;
 
@@ -78,7 +84,7 @@ typedef struct {
   int32_t dim;        /* 2 or 3                                             */
   int32_t n_seg;      /* cells per block edge: even, 2..16                  */
   int32_t p;          /* polynomial degree 0..3                             */
-  int32_t precision;  /* DGF_FP64 or DGF_FP32                               */
+  int32_t precision;  /* DGF_FP64, DGF_FP32 or DGF_FP32_COMP                */
   int32_t device;     /* CUDA device ordinal; -1 = host-only forest that
                          answers topology/geometry queries only             */
   int32_t n_periodic; /* number of periodic translations, 0..3             */

@@ -17,7 +17,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdgf.so")
 
-FP64, FP32 = 0, 1
+FP64, FP32, FP32_COMP = 0, 1, 2
 SAME, COARSER, FINER, BOUNDARY = 0, 1, 2, 3
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE",
           -5: "ETIMEOUT", -6: "EBALANCE", -7: "ESTATE", -8: "EUNSUPPORTED"}
@@ -141,14 +141,15 @@ class Forest:
                  precision=FP64, device=0, gamma=1.4, cfl=0.1, torch_memory=True):
         L = lib()
         self.dim, self.n_seg, self.p = int(dim), int(n_seg), int(p)
-        self.precision = FP32 if precision in (FP32, "fp32", "f32") else FP64
+        self.precision = (FP32 if precision in (FP32, "fp32", "f32") else
+                          FP32_COMP if precision in (FP32_COMP, "fp32_comp") else FP64)
         self.device = int(device)
         self.nv = self.dim + 2
         self.N = self.p + 1
         self.M = self.N ** self.dim
         self.nc = self.n_seg ** self.dim
         self.nt = self.n_seg ** (self.dim - 1)
-        self.dtype = np.float32 if self.precision == FP32 else np.float64
+        self.dtype = np.float32 if self.precision == FP32 else np.float64  # ABI element type
         nodes = np.ascontiguousarray(nodes, np.float64)
         corners = np.ascontiguousarray(root_corners, np.int64)
         cell = None if root_cell_nodes is None else np.ascontiguousarray(root_cell_nodes, np.float64)
@@ -327,4 +328,4 @@ class Forest:
         return {"dt": (ms[0], int(cnt[0])), "guard": (ms[1], int(cnt[1])), "stage": (ms[2], int(cnt[2]))}
 
 
-__all__ = ["Forest", "DgfError", "lib", "FP64", "FP32", "LIB_PATH"]
+__all__ = ["Forest", "DgfError", "lib", "FP64", "FP32", "FP32_COMP", "LIB_PATH"]

@@ -215,13 +215,37 @@ struct StageArgs {
   int* status;
   Real ca, cb, gamma;
   int mode, last;
+  const double* __restrict__ U64;  // compensated form: u^n in FP64 (stage input base)
+  const float* __restrict__ Din;   // compensated form: delta^(k), null at stage 1
+  double* __restrict__ U64out;     // compensated form, last stage: u^(n+1) in FP64
   Tab<P + 1, Real> T;
+};
+
+// Stage input u^(k) at a flat index: one array (plain), or u^n in FP64 plus
+// the FP32 increment delta^(k) (compensated SSP-RK3: the state accumulates
+// in FP64, each stage changes it by an O(dt) increment kept in FP32).
+template <typename Real, bool COMP>
+struct StateIn {
+  const Real* u;
+  const double* u64;
+  const float* d;
+  __device__ __forceinline__ Real operator()(size_t i) const {
+    if constexpr (COMP) {
+      double x = __ldcg(&u64[i]);
+      if (d) x += (double)__ldcg(&d[i]);
+      return (Real)x;
+    } else {
+      return u[i];
+    }
+  }
 };
 
 template <int D, int P, typename Real>
 struct GuardArgs {
   int nL, n, mode;  // mode 0: modal guard cells; 1: traces
   const Real* __restrict__ U;
+  const double* __restrict__ U64;  // compensated form: u^n in FP64
+  const float* __restrict__ Din;   // compensated form: delta^(k), null at stage 1
   Real* __restrict__ out;
   const int* __restrict__ kind;    // [b][f]
   const int* __restrict__ nbr;     // [b][f][4]
@@ -377,7 +401,7 @@ __device__ __forceinline__ int face_point_index(int ax, int fp, int qn) {
 // (each face once); x volume + lift; y volume + lift (and the halo trace of
 // the next layer); z volume + z faces (carried between layers) and 1/J;
 // SSP-RK combination point by point, with the CFL minimum on the last stage.
-template <int D, int P, int NS, typename Real>
+template <int D, int P, int NS, typename Real, bool COMP = false>
 __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB)
     k_stage(const StageArgs<D, P, Real> A) {
   constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
@@ -426,6 +450,9 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
     const int k1 = D == 3 ? min(n, k0 + A.zchunk) : 1;
     const Real* __restrict__ Ub = A.U + (size_t)b * NV * Q * nc;
     const Real* __restrict__ Unb = A.Un + (size_t)b * NV * Q * nc;
+    const size_t boff = (size_t)b * NV * Q * nc;
+    const StateIn<Real, COMP> Sb{A.U + boff, COMP ? A.U64 + boff : nullptr,
+                                 (COMP && A.Din) ? A.Din + boff : nullptr};
     Real* __restrict__ Ob = A.Uout + (size_t)b * NV * Q * nc;
     const Real* __restrict__ Gb = A.geo + (size_t)b * NG * nc;
     const Real* __restrict__ Tb = A.gtr + (size_t)b * 2 * D * NV * NFP * nt;
@@ -441,8 +468,15 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
         constexpr int lpr = (NCL * (int)sizeof(Real) + 127) / 128;
         for (int w = tid; w < NV * Q * lpr; w += nthr) {
           const int r = w / lpr, l = w - r * lpr;
-          if (D == 3 && k + 1 < n) prefetch_l2(Ub + (size_t)r * nc + (k + 1) * NCL + l * (128 / sizeof(Real)));
-          if (A.mode == 0 && A.ca != Real(0)) prefetch_l2(Unb + (size_t)r * nc + cbase + l * (128 / sizeof(Real)));
+          if constexpr (COMP) {
+            if (D == 3 && k + 1 < n) {
+              prefetch_l2(Sb.u64 + (size_t)r * nc + (k + 1) * NCL + l * (128 / sizeof(Real)) / 2);
+              prefetch_l2(Sb.u64 + (size_t)r * nc + (k + 1) * NCL + l * (128 / sizeof(Real)) / 2 + 16);
+            }
+          } else {
+            if (D == 3 && k + 1 < n) prefetch_l2(Ub + (size_t)r * nc + (k + 1) * NCL + l * (128 / sizeof(Real)));
+            if (A.mode == 0 && A.ca != Real(0)) prefetch_l2(Unb + (size_t)r * nc + cbase + l * (128 / sizeof(Real)));
+          }
         }
       }
       // ------------------------------------------- P1: layer k to shared memory
@@ -450,10 +484,17 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
         constexpr int VEC = 16 / sizeof(Real);
         using V4 = typename std::conditional<sizeof(Real) == 4, float4, double2>::type;
         constexpr int PER_ROW = NCL / VEC;
-        for (int w = tid; w < NV * Q * PER_ROW; w += nthr) {
-          const int r = w / PER_ROW, cv = (w - r * PER_ROW) * VEC;
-          const V4 val = __ldcg(reinterpret_cast<const V4*>(Ub + (size_t)r * nc + cbase + cv));
-          *reinterpret_cast<V4*>(us + r * NCL + cv) = val;
+        if constexpr (COMP) {
+          for (int w = tid; w < NV * Q * NCL; w += nthr) {
+            const int r = w / NCL, cc = w - r * NCL;
+            us[r * NCL + cc] = Sb((size_t)r * nc + cbase + cc);
+          }
+        } else {
+          for (int w = tid; w < NV * Q * PER_ROW; w += nthr) {
+            const int r = w / PER_ROW, cv = (w - r * PER_ROW) * VEC;
+            const V4 val = __ldcg(reinterpret_cast<const V4*>(Ub + (size_t)r * nc + cbase + cv));
+            *reinterpret_cast<V4*>(us + r * NCL + cv) = val;
+          }
         }
       }
       if constexpr (D == 3) {
@@ -468,7 +509,7 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
               tr = Real(0);
 #pragma unroll
               for (int qz = 0; qz < N; ++qz)
-                tr += T.lp[qz] * __ldcg(&Ub[((size_t)v * Q + fp + NFP * qz) * nc + (k0 - 1) * NCL + c]);
+                tr += T.lp[qz] * Sb(((size_t)v * Q + fp + NFP * qz) * nc + (k0 - 1) * NCL + c);
             }
             TB(v, fp, c) = tr;
           }
@@ -683,7 +724,7 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
             tr = Real(0);
 #pragma unroll
             for (int qz = 0; qz < N; ++qz)
-              tr += T.lm[qz] * __ldcg(&Ub[((size_t)v * Q + fp + NFP * qz) * nc + (k + 1) * NCL + c]);
+              tr += T.lm[qz] * Sb(((size_t)v * Q + fp + NFP * qz) * nc + (k + 1) * NCL + c);
           }
           TB(v, fp, c) = tr;
         }
@@ -762,11 +803,24 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
           Real val;
           if (A.mode == 1) {
             val = r;
+            Ob[gi] = val;
+          } else if constexpr (COMP) {
+            // delta^(k+1) = b_k (delta^(k) + dt L); last stage: u^(n+1) = u^n + delta^(3) in FP64
+            const Real din = Sb.d ? Sb.d[gi] : Real(0);
+            const Real dout = A.cb * (din + dt * r);
+            if (A.last) {
+              const double un = Sb.u64[gi] + (double)dout;
+              A.U64out[boff + gi] = un;
+              val = (Real)un;
+            } else {
+              Ob[gi] = dout;
+              val = dout;
+            }
           } else {
             val = A.cb * (US(v, q, c) + dt * r);  // the stage input is still in shared memory
             if (A.ca != Real(0)) val += A.ca * __ldcg(&Unb[gi]);
+            Ob[gi] = val;
           }
-          Ob[gi] = val;
           o[v] = val;
         }
         if (A.last) {
@@ -865,8 +919,9 @@ __device__ __forceinline__ int map_point(const int* js, int pk) {
 }
 
 // one thread per (leaf, face, guard cell t, var); finer faces are skipped
-template <int D, int P, typename Real>
+template <int D, int P, typename Real, bool COMP = false>
 __global__ void __launch_bounds__(128) k_guard(const GuardArgs<D, P, Real> A) {
+  const StateIn<Real, COMP> S{A.U, A.U64, A.Din};
   constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
   const int n = A.n;
   const int nt = D == 3 ? n * n : n;
@@ -906,13 +961,13 @@ __global__ void __launch_bounds__(128) k_guard(const GuardArgs<D, P, Real> A) {
   if (kind == 3) {  // outflow: the guard is the mirror image of my face cell
     int h[3] = {g[0], g[1], g[2]};
     h[a] = s ? n - 1 : 0;
-    const Real* src = A.U + ((size_t)b * NV + v) * Q * nc + cell_of(h);
+    const size_t src0 = ((size_t)b * NV + v) * Q * nc + cell_of(h);
     if (A.mode == 0) {
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         int d[3] = {q % N, (q / N) % N, q / (N * N)};
         d[a] = N - 1 - d[a];
-        out_vol[(size_t)q * nt] = src[(size_t)(d[0] + N * d[1] + N * N * d[2]) * nc];
+        out_vol[(size_t)q * nt] = S(src0 + (size_t)(d[0] + N * d[1] + N * N * d[2]) * nc);
       }
     } else {
 #pragma unroll
@@ -920,7 +975,7 @@ __global__ void __launch_bounds__(128) k_guard(const GuardArgs<D, P, Real> A) {
         Real acc = Real(0);
 #pragma unroll
         for (int qn = 0; qn < N; ++qn)
-          acc += (s ? T.lp[qn] : T.lm[qn]) * src[(size_t)face_point_index<D, N>(a, fp, qn) * nc];
+          acc += (s ? T.lp[qn] : T.lm[qn]) * S(src0 + (size_t)face_point_index<D, N>(a, fp, qn) * nc);
         out_trace[(size_t)fp * nt] = acc;
       }
     }
@@ -946,7 +1001,7 @@ __global__ void __launch_bounds__(128) k_guard(const GuardArgs<D, P, Real> A) {
     e[b2] = s2 == 0 ? 0 : 1;
   }
   h[b2] = s2 == 0 ? 0 : n - 1;
-  const Real* src = A.U + ((size_t)A.nbr[(b * 2 * D + f) * 4] * NV + v) * Q * nc + cell_of(h);
+  const size_t src0 = ((size_t)A.nbr[(b * 2 * D + f) * 4] * NV + v) * Q * nc + cell_of(h);
 
   if (A.mode == 1) {
     // trace on the neighbour's face (b2, s2) at its face points
@@ -956,7 +1011,7 @@ __global__ void __launch_bounds__(128) k_guard(const GuardArgs<D, P, Real> A) {
       Real acc = Real(0);
 #pragma unroll
       for (int qn = 0; qn < N; ++qn)
-        acc += (s2 ? T.lp[qn] : T.lm[qn]) * src[(size_t)face_point_index<D, N>(b2, j, qn) * nc];
+        acc += (s2 ? T.lp[qn] : T.lm[qn]) * S(src0 + (size_t)face_point_index<D, N>(b2, j, qn) * nc);
       tr[j] = acc;
     }
     if (kind == 1) {
@@ -1003,7 +1058,7 @@ __global__ void __launch_bounds__(128) k_guard(const GuardArgs<D, P, Real> A) {
   // mode 0: full guard cell at my Gauss points
   Real u[Q];
 #pragma unroll
-  for (int q = 0; q < Q; ++q) u[q] = src[(size_t)q * nc];
+  for (int q = 0; q < Q; ++q) u[q] = S(src0 + (size_t)q * nc);
   if (kind == 1) {
     Real u2[Q];
     if (e[0]) apply_axis<D, N, 0, Real>(T.Snp, u, u2);
@@ -1028,8 +1083,9 @@ __global__ void __launch_bounds__(128) k_guard(const GuardArgs<D, P, Real> A) {
 // var) with one warp per fine child e; warp e applies child e's columns of
 // the precomputed, already rotated nodal operator, the partial sums are
 // added in fixed child order, and (mode 1) the trace at my face is formed.
-template <int D, int P, typename Real>
+template <int D, int P, typename Real, bool COMP = false>
 __global__ void __launch_bounds__(32 << D) k_guard_fine(const GuardArgs<D, P, Real> A) {
+  const StateIn<Real, COMP> S{A.U, A.U64, A.Din};
   constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
   constexpr int NW = 1 << D;
   constexpr int KC = NW * Q;
@@ -1073,7 +1129,7 @@ __global__ void __launch_bounds__(32 << D) k_guard_fine(const GuardArgs<D, P, Re
     c += (2 * h[ax] + ((e >> ax) & 1) - cN * n) * st;
     st *= n;
   }
-  for (int q = lane; q < Q; q += 32) srcs[e][q] = A.U[(((size_t)fine * NV + v) * Q + q) * nc + c];
+  for (int q = lane; q < Q; q += 32) srcs[e][q] = S((((size_t)fine * NV + v) * Q + q) * nc + c);
   __syncwarp();
   const Real* op = A.cop + (size_t)(A.copoff[bf] + t) * KC * Q + (size_t)e * Q * Q;
   for (int p = lane; p < Q; p += 32) {
@@ -1111,8 +1167,9 @@ __global__ void __launch_bounds__(32 << D) k_guard_fine(const GuardArgs<D, P, Re
 // guard cell and var, one warp per fine child), the remaining blocks compute
 // the traces of same-level, coarser and outflow faces, one thread per
 // (leaf, face, guard cell, var) as in k_guard.
-template <int D, int P, typename Real>
+template <int D, int P, typename Real, bool COMP = false>
 __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, Real> A, int n_fine_blocks) {
+  const StateIn<Real, COMP> S{A.U, A.U64, A.Din};
   constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
   constexpr int NW = 1 << D;
   constexpr int KC = NW * Q;
@@ -1153,13 +1210,13 @@ __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, R
     if (kind == 3) {  // outflow: my own face cell's trace
       int h[3] = {g[0], g[1], g[2]};
       h[a] = s ? n - 1 : 0;
-      const Real* src = A.U + ((size_t)b * NV + v) * Q * nc + cell_of(h);
+      const size_t src0 = ((size_t)b * NV + v) * Q * nc + cell_of(h);
 #pragma unroll
       for (int fp = 0; fp < NFP; ++fp) {
         Real acc = Real(0);
 #pragma unroll
         for (int qn = 0; qn < N; ++qn)
-          acc += (s ? T.lp[qn] : T.lm[qn]) * src[(size_t)face_point_index<D, N>(a, fp, qn) * nc];
+          acc += (s ? T.lp[qn] : T.lm[qn]) * S(src0 + (size_t)face_point_index<D, N>(a, fp, qn) * nc);
         out_trace[(size_t)fp * nt] = acc;
       }
       return;
@@ -1184,14 +1241,14 @@ __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, R
       }
     }
     h[b2] = s2 == 0 ? 0 : n - 1;
-    const Real* src = A.U + ((size_t)A.nbr[(b * 2 * D + f) * 4] * NV + v) * Q * nc + cell_of(h);
+    const size_t src0 = ((size_t)A.nbr[(b * 2 * D + f) * 4] * NV + v) * Q * nc + cell_of(h);
     Real tr[NFP];
 #pragma unroll
     for (int j = 0; j < NFP; ++j) {
       Real acc = Real(0);
 #pragma unroll
       for (int qn = 0; qn < N; ++qn)
-        acc += (s2 ? T.lp[qn] : T.lm[qn]) * src[(size_t)face_point_index<D, N>(b2, j, qn) * nc];
+        acc += (s2 ? T.lp[qn] : T.lm[qn]) * S(src0 + (size_t)face_point_index<D, N>(b2, j, qn) * nc);
       tr[j] = acc;
     }
     if (kind == 1) {  // split (Eqs. (11)-(12)) of the coarse face trace
@@ -1273,7 +1330,7 @@ __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, R
   }
   for (int i = lane; i < NV * Q; i += 32) {
     const int v = i / Q, q = i % Q;
-    sv[e][v][q] = A.U[(((size_t)fine * NV + v) * Q + q) * nc + c];
+    sv[e][v][q] = S((((size_t)fine * NV + v) * Q + q) * nc + c);
   }
   __syncwarp();
   const Real* op = A.ctr + (size_t)(A.copoff[bf] + t) * KC * NFP + (size_t)e * Q * NFP;

@@ -59,6 +59,11 @@ __global__ void k_dt(DevScalars* s, double cfl) {
 
 __global__ void k_reset_lam(DevScalars* s) { s->lam_bits = kInfBits; }
 
+__global__ void k_widen(const float* __restrict__ in, double* __restrict__ out, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (double)in[i];
+}
+
 __global__ void k_dt_only(DevScalars* s, double cfl, double* out) {
   const unsigned long long lb = s->lam_bits;
   *out = lb == kInfBits ? 0.0 : cfl * __longlong_as_double((long long)lb);
@@ -104,7 +109,10 @@ struct dgf_forest {
   bool has_alloc = false;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  size_t esize = 8;
+  size_t esize = 8;   // element size of the device compute buffers
+  size_t sesize = 8;  // element size of the state at the C ABI
+  bool comp = false;  // compensated form: u^n in FP64, stage increments in FP32
+  int cur = 0;        // compensated form: which U64 buffer holds u^n
   int d = 0, n = 0, p = 0, N = 0, nv = 0, M = 0, nc = 0, NG = 0, nt = 0, NFP = 0;
   int64_t nL = 0;
   RtTables tab{};
@@ -114,6 +122,8 @@ struct dgf_forest {
     void* ptr = nullptr;
     size_t bytes = 0;
   };
+  Buf U64[2], hcell64, gmod64;
+  cudaGraphExec_t graph_alt = nullptr;  // compensated form: graph of the other u^n buffer
   Buf U[3], geo, geo64, hcell, gtr, gmod, cop, ctr, kind, nbr, orient, qbits, copoff, part, scal, tot,
       dtout, nodal, fine, affine, ameta;
   int nfine = 0;
@@ -440,7 +450,7 @@ dgf_status build_device(dgf_forest* f) {
       (st = upload(f, f->qbits, qbits)) || (st = upload(f, f->copoff, copoff)) || (st = upload(f, f->geo64, geo64)) ||
       (st = upload(f, f->fine, fine_list)))
     return st;
-  if ((st = upload(f, f->affine, affine))) return st;
+  if ((st = upload(f, f->affine, affine)) || (st = upload(f, f->hcell64, hcell))) return st;
   if (f->precision == DGF_FP64) {
     if ((st = upload(f, f->geo, geo64)) || (st = upload(f, f->hcell, hcell)) || (st = upload(f, f->cop, cop)) ||
         (st = upload(f, f->ctr, ctr)) ||
@@ -455,6 +465,10 @@ dgf_status build_device(dgf_forest* f) {
   const size_t sbytes = (size_t)L * f->nv * M * nc * f->esize;
   for (int k = 0; k < 3; ++k)
     if (!ensure(f, f->U[k], sbytes)) return fail(DGF_ENOMEM, "state allocation failed");
+  if (f->comp)
+    for (int k = 0; k < 2; ++k)
+      if (!ensure(f, f->U64[k], (size_t)L * f->nv * M * nc * sizeof(double)))
+        return fail(DGF_ENOMEM, "state allocation failed");
   if (!ensure(f, f->gtr, (size_t)L * nf * f->nv * f->NFP * nt * f->esize) ||
       !ensure(f, f->part, (size_t)L * nc * f->nv * sizeof(double)))
     return fail(DGF_ENOMEM, "scratch allocation failed");
@@ -487,6 +501,10 @@ dgf_status build_device(dgf_forest* f) {
     cudaGraphExecDestroy(f->graph);
     f->graph = nullptr;
   }
+  if (f->graph_alt) {
+    cudaGraphExecDestroy(f->graph_alt);
+    f->graph_alt = nullptr;
+  }
   f->graph_valid = false;
   return DGF_OK;
 }
@@ -518,6 +536,12 @@ RtStage stage_args(dgf_forest* f, int src, int dst, double ca, double cb, int mo
   r.gamma = f->gamma;
   r.mode = mode;
   r.last = last;
+  if (f->comp) {
+    r.comp = 1;
+    r.U64 = (const double*)f->U64[f->cur].ptr;
+    r.Din = src == 0 ? nullptr : (const float*)f->U[src].ptr;
+    r.U64out = (double*)f->U64[1 - f->cur].ptr;
+  }
   r.T = f->tab;
   return r;
 }
@@ -539,18 +563,28 @@ RtGuard guard_args(dgf_forest* f, int src, void* out, int mode) {
   r.ctr = f->ctr.ptr;
   r.fine_list = (const int*)f->fine.ptr;
   r.nfine = f->nfine;
+  if (f->comp) {
+    r.comp = 1;
+    r.U64 = (const double*)f->U64[f->cur].ptr;
+    r.Din = src == 0 ? nullptr : (const float*)f->U[src].ptr;
+  }
   r.T = f->tab;
   return r;
 }
+
+// device state buffer u^n (nodal) and whether it is FP64
+void* state_ptr(dgf_forest* f) { return f->comp ? f->U64[f->cur].ptr : f->U[0].ptr; }
+bool state_f64(dgf_forest* f) { return f->precision != DGF_FP32; }
 
 RtMisc misc_args(dgf_forest* f, int src) {
   RtMisc r{};
   r.p = f->p;
   r.nL = (int)f->nL;
   r.n = f->n;
-  r.U = f->U[src].ptr;
-  r.Uout = f->U[src].ptr;
-  r.hcell = f->hcell.ptr;
+  void* u = src == 0 ? state_ptr(f) : f->U[src].ptr;
+  r.U = u;
+  r.Uout = u;
+  r.hcell = state_f64(f) ? f->hcell64.ptr : f->hcell.ptr;
   r.geo64 = (const double*)f->geo64.ptr;
   r.part = (double*)f->part.ptr;
   r.gamma = f->gamma;
@@ -569,24 +603,31 @@ cudaError_t do_guard(dgf_forest* f, const RtGuard& r) {
   return f->precision == DGF_FP64 ? launch_guard<3, double>(r, f->stream) : launch_guard<3, float>(r, f->stream);
 }
 cudaError_t do_cfl(dgf_forest* f, const RtMisc& r) {
-  if (f->d == 2) return f->precision == DGF_FP64 ? launch_cfl<2, double>(r, f->stream) : launch_cfl<2, float>(r, f->stream);
-  return f->precision == DGF_FP64 ? launch_cfl<3, double>(r, f->stream) : launch_cfl<3, float>(r, f->stream);
+  if (f->d == 2) return state_f64(f) ? launch_cfl<2, double>(r, f->stream) : launch_cfl<2, float>(r, f->stream);
+  return state_f64(f) ? launch_cfl<3, double>(r, f->stream) : launch_cfl<3, float>(r, f->stream);
 }
 cudaError_t do_project(dgf_forest* f, const RtMisc& r) {
-  if (f->d == 2) return f->precision == DGF_FP64 ? launch_project<2, double>(r, f->stream) : launch_project<2, float>(r, f->stream);
-  return f->precision == DGF_FP64 ? launch_project<3, double>(r, f->stream) : launch_project<3, float>(r, f->stream);
+  if (f->d == 2) return state_f64(f) ? launch_project<2, double>(r, f->stream) : launch_project<2, float>(r, f->stream);
+  return state_f64(f) ? launch_project<3, double>(r, f->stream) : launch_project<3, float>(r, f->stream);
 }
 cudaError_t do_totals(dgf_forest* f, const RtMisc& r) {
-  if (f->d == 2) return f->precision == DGF_FP64 ? launch_totals<2, double>(r, f->stream) : launch_totals<2, float>(r, f->stream);
-  return f->precision == DGF_FP64 ? launch_totals<3, double>(r, f->stream) : launch_totals<3, float>(r, f->stream);
+  if (f->d == 2) return state_f64(f) ? launch_totals<2, double>(r, f->stream) : launch_totals<2, float>(r, f->stream);
+  return state_f64(f) ? launch_totals<3, double>(r, f->stream) : launch_totals<3, float>(r, f->stream);
 }
 
-cudaError_t do_convert(dgf_forest* f, void* X, size_t outer, int inner, int to_nodal) {
+// modal <-> nodal in place; dbl selects the element type of X
+cudaError_t do_convert(dgf_forest* f, void* X, size_t outer, int inner, int to_nodal, bool dbl) {
   if (f->d == 2)
-    return f->precision == DGF_FP64 ? launch_convert<2, double>(f->p, outer, inner, X, to_nodal, f->tab, f->stream)
-                                    : launch_convert<2, float>(f->p, outer, inner, X, to_nodal, f->tab, f->stream);
-  return f->precision == DGF_FP64 ? launch_convert<3, double>(f->p, outer, inner, X, to_nodal, f->tab, f->stream)
-                                  : launch_convert<3, float>(f->p, outer, inner, X, to_nodal, f->tab, f->stream);
+    return dbl ? launch_convert<2, double>(f->p, outer, inner, X, to_nodal, f->tab, f->stream)
+               : launch_convert<2, float>(f->p, outer, inner, X, to_nodal, f->tab, f->stream);
+  return dbl ? launch_convert<3, double>(f->p, outer, inner, X, to_nodal, f->tab, f->stream)
+             : launch_convert<3, float>(f->p, outer, inner, X, to_nodal, f->tab, f->stream);
+}
+
+// compute-precision buffer -> state-precision buffer (compensated form: FP32 -> FP64)
+dgf_status widen(dgf_forest* f, const void* in, void* out, size_t count) {
+  k_widen<<<(unsigned)((count + 255) / 256), 256, 0, f->stream>>>((const float*)in, (double*)out, count);
+  return cuda_check(cudaGetLastError(), "widen");
 }
 
 dgf_status require_device(dgf_forest* f) {
@@ -626,7 +667,9 @@ dgf_status enqueue_step(dgf_forest* f) {
     return cudaGetLastError();
   });
   if (st) return st;
-  // Shu-Osher SSP-RK3: (src, dst, a, b): dst = a U^n + b (src + dt L(src))
+  // Shu-Osher SSP-RK3: (src, dst, a, b): dst = a U^n + b (src + dt L(src)).
+  // Compensated form: U[1], U[2] hold the FP32 increments delta^(1), delta^(2)
+  // (delta^(k+1) = b (delta^(k) + dt L)), the last stage writes u^(n+1) in FP64.
   const int src[3] = {0, 1, 2}, dst[3] = {1, 2, 0};
   const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
   for (int k = 0; k < 3; ++k) {
@@ -661,7 +704,8 @@ const char* dgf_last_error(void) { return g_err.c_str(); }
 dgf_status dgf_forest_create(const dgf_forest_desc* desc, const dgf_allocator* allocator, dgf_forest** out) {
   if (!desc || !out) return fail(DGF_EINVAL, "null argument");
   *out = nullptr;
-  if (desc->precision != DGF_FP64 && desc->precision != DGF_FP32) return fail(DGF_EINVAL, "bad precision");
+  if (desc->precision != DGF_FP64 && desc->precision != DGF_FP32 && desc->precision != DGF_FP32_COMP)
+    return fail(DGF_EINVAL, "bad precision");
   if (!(desc->gamma > 1.0) || !(desc->cfl > 0.0)) return fail(DGF_EINVAL, "gamma must be > 1 and cfl > 0");
   dgf_forest* f = new (std::nothrow) dgf_forest();
   if (!f) return fail(DGF_ENOMEM, "host allocation failed");
@@ -676,6 +720,8 @@ dgf_status dgf_forest_create(const dgf_forest_desc* desc, const dgf_allocator* a
   f->gamma = desc->gamma;
   f->cfl = desc->cfl;
   f->esize = desc->precision == DGF_FP64 ? 8 : 4;
+  f->sesize = desc->precision == DGF_FP32 ? 4 : 8;
+  f->comp = desc->precision == DGF_FP32_COMP;
   f->d = desc->dim;
   f->n = desc->n_seg;
   f->p = desc->p;
@@ -758,13 +804,15 @@ dgf_status dgf_forest_destroy(dgf_forest* f) {
     DeviceGuard dg(f->device);
     cudaStreamSynchronize(f->stream);
     if (f->graph) cudaGraphExecDestroy(f->graph);
+    if (f->graph_alt) cudaGraphExecDestroy(f->graph_alt);
     for (auto& e : f->ev) {
       cudaEventDestroy(e.a);
       cudaEventDestroy(e.b);
     }
     dgf_forest::Buf* bufs[] = {&f->U[0], &f->U[1], &f->U[2], &f->geo, &f->geo64, &f->hcell, &f->gtr,
                                &f->gmod, &f->cop, &f->ctr, &f->kind, &f->nbr, &f->orient, &f->qbits, &f->copoff,
-                               &f->part, &f->scal, &f->tot, &f->dtout, &f->nodal, &f->fine, &f->affine, &f->ameta};
+                               &f->part, &f->scal, &f->tot, &f->dtout, &f->nodal, &f->fine, &f->affine, &f->ameta,
+                               &f->U64[0], &f->U64[1], &f->hcell64, &f->gmod64};
     for (auto* b : bufs) dev_free(f, *b);
     if (f->own_stream && f->stream) cudaStreamDestroy(f->stream);
   }
@@ -780,7 +828,9 @@ dgf_status dgf_set_stream(dgf_forest* f, void* stream) {
   f->own_stream = false;
   f->stream = (cudaStream_t)stream;
   if (f->graph) cudaGraphExecDestroy(f->graph);
+  if (f->graph_alt) cudaGraphExecDestroy(f->graph_alt);
   f->graph = nullptr;
+  f->graph_alt = nullptr;
   f->graph_valid = false;
   return DGF_OK;
 }
@@ -879,14 +929,14 @@ dgf_status dgf_set_state(dgf_forest* f, const void* src, int is_device) {
   if (dgf_status st = require_device(f)) return st;
   if (!src) return fail(DGF_EINVAL, "null source");
   DeviceGuard dg(f->device);
-  const size_t bytes = (size_t)f->nL * f->nv * f->M * f->nc * f->esize;
-  dgf_status st = cuda_check(cudaMemcpyAsync(f->U[0].ptr, src, bytes,
-                                             is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                             f->stream),
-                             "set_state");
+  const size_t bytes = (size_t)f->nL * f->nv * f->M * f->nc * f->sesize;
+  void* U = state_ptr(f);
+  dgf_status st = cuda_check(
+      cudaMemcpyAsync(U, src, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, f->stream),
+      "set_state");
   if (st) return st;
   // the device holds values at the Gauss points: u = V K per (leaf, var, cell)
-  if ((st = cuda_check(do_convert(f, f->U[0].ptr, (size_t)f->nL, f->nc, 1), "to nodal"))) return st;
+  if ((st = cuda_check(do_convert(f, U, (size_t)f->nL, f->nc, 1, state_f64(f)), "to nodal"))) return st;
   f->have_state = true;
   return init_lambda(f);
 }
@@ -896,12 +946,13 @@ dgf_status dgf_get_state(dgf_forest* f, void* dst, int is_device) {
   if (!dst) return fail(DGF_EINVAL, "null destination");
   if (!f->have_state) return fail(DGF_ESTATE, "no state set");
   DeviceGuard dg(f->device);
-  const size_t bytes = (size_t)f->nL * f->nv * f->M * f->nc * f->esize;
-  dgf_status st = cuda_check(cudaMemcpyAsync(f->U[1].ptr, f->U[0].ptr, bytes, cudaMemcpyDeviceToDevice, f->stream),
+  const size_t bytes = (size_t)f->nL * f->nv * f->M * f->nc * f->sesize;
+  void* tmp = f->comp ? f->U64[1 - f->cur].ptr : f->U[1].ptr;  // free between time steps
+  dgf_status st = cuda_check(cudaMemcpyAsync(tmp, state_ptr(f), bytes, cudaMemcpyDeviceToDevice, f->stream),
                              "get_state");
   if (st) return st;
-  if ((st = cuda_check(do_convert(f, f->U[1].ptr, (size_t)f->nL, f->nc, 0), "to modal"))) return st;
-  return copy_state(f, dst, f->U[1].ptr, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+  if ((st = cuda_check(do_convert(f, tmp, (size_t)f->nL, f->nc, 0, state_f64(f)), "to modal"))) return st;
+  return copy_state(f, dst, tmp, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
 }
 
 dgf_status dgf_set_state_nodal(dgf_forest* f, const double* vals, int is_device) {
@@ -930,12 +981,19 @@ dgf_status dgf_fill_guardcells(dgf_forest* f, void* guard, int is_device) {
   if (!guard) return fail(DGF_EINVAL, "null destination");
   if (!f->have_state) return fail(DGF_ESTATE, "no state set");
   DeviceGuard dg(f->device);
-  const size_t bytes = (size_t)f->nL * 2 * f->d * f->nv * f->M * f->nt * f->esize;
-  if (!ensure(f, f->gmod, bytes)) return fail(DGF_ENOMEM, "guard allocation failed");
+  const size_t count = (size_t)f->nL * 2 * f->d * f->nv * f->M * f->nt;
+  if (!ensure(f, f->gmod, count * f->esize)) return fail(DGF_ENOMEM, "guard allocation failed");
   dgf_status st = cuda_check(do_guard(f, guard_args(f, 0, f->gmod.ptr, 0)), "guard");
   if (st) return st;
-  if ((st = cuda_check(do_convert(f, f->gmod.ptr, (size_t)f->nL * 2 * f->d, f->nt, 0), "to modal"))) return st;
-  return copy_state(f, guard, f->gmod.ptr, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+  const bool dbl = f->precision == DGF_FP64;
+  if ((st = cuda_check(do_convert(f, f->gmod.ptr, (size_t)f->nL * 2 * f->d, f->nt, 0, dbl), "to modal"))) return st;
+  const void* out = f->gmod.ptr;
+  if (f->comp) {
+    if (!ensure(f, f->gmod64, count * sizeof(double))) return fail(DGF_ENOMEM, "guard allocation failed");
+    if ((st = widen(f, f->gmod.ptr, f->gmod64.ptr, count))) return st;
+    out = f->gmod64.ptr;
+  }
+  return copy_state(f, guard, out, count * f->sesize, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
 }
 
 dgf_status dgf_dg_residual(dgf_forest* f, void* dst, int is_device) {
@@ -946,9 +1004,15 @@ dgf_status dgf_dg_residual(dgf_forest* f, void* dst, int is_device) {
   dgf_status st = cuda_check(do_guard(f, guard_args(f, 0, f->gtr.ptr, 1)), "guard");
   if (st) return st;
   if ((st = cuda_check(do_stage(f, stage_args(f, 0, 1, 0.0, 1.0, 1, 0)), "stage"))) return st;
-  if ((st = cuda_check(do_convert(f, f->U[1].ptr, (size_t)f->nL, f->nc, 0), "to modal"))) return st;
-  const size_t bytes = (size_t)f->nL * f->nv * f->M * f->nc * f->esize;
-  return copy_state(f, dst, f->U[1].ptr, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+  const bool dbl = f->precision == DGF_FP64;
+  if ((st = cuda_check(do_convert(f, f->U[1].ptr, (size_t)f->nL, f->nc, 0, dbl), "to modal"))) return st;
+  const size_t count = (size_t)f->nL * f->nv * f->M * f->nc;
+  const void* out = f->U[1].ptr;
+  if (f->comp) {
+    if ((st = widen(f, f->U[1].ptr, f->U64[1 - f->cur].ptr, count))) return st;
+    out = f->U64[1 - f->cur].ptr;
+  }
+  return copy_state(f, dst, out, count * f->sesize, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
 }
 
 dgf_status dgf_rk_step(dgf_forest* f, double t_end, double* dt_out) {
@@ -960,7 +1024,9 @@ dgf_status dgf_rk_step(dgf_forest* f, double t_end, double* dt_out) {
   if (f->timing) {
     if ((st = enqueue_step(f))) return st;
   } else {
-    if (!f->graph_valid) {
+    // one graph per time increment (two for the compensated form, one per u^n buffer)
+    cudaGraphExec_t& G = (f->comp && f->cur == 1) ? f->graph_alt : f->graph;
+    if (!G) {
       cudaGraph_t g = nullptr;
       if ((st = cuda_check(cudaStreamBeginCapture(f->stream, cudaStreamCaptureModeThreadLocal), "capture")))
         return st;
@@ -971,13 +1037,14 @@ dgf_status dgf_rk_step(dgf_forest* f, double t_end, double* dt_out) {
         return est;
       }
       if ((st = cuda_check(e, "end capture"))) return st;
-      e = cudaGraphInstantiate(&f->graph, g, 0);
+      e = cudaGraphInstantiate(&G, g, 0);
       cudaGraphDestroy(g);
       if ((st = cuda_check(e, "instantiate"))) return st;
       f->graph_valid = true;
     }
-    if ((st = cuda_check(cudaGraphLaunch(f->graph, f->stream), "graph launch"))) return st;
+    if ((st = cuda_check(cudaGraphLaunch(G, f->stream), "graph launch"))) return st;
   }
+  if (f->comp) f->cur ^= 1;  // u^(n+1) was written to the other FP64 buffer
   if (dt_out) {
     DevScalars* s = (DevScalars*)f->scal.ptr;
     if ((st = cuda_check(cudaMemcpyAsync(dt_out, &s->dt, sizeof(double), cudaMemcpyDeviceToHost, f->stream), "dt")))
@@ -1111,8 +1178,8 @@ static dgf_status regrid(dgf_forest* f, const std::vector<uint64_t>& old_leaves)
     DeviceGuard dg(f->device);
     const size_t cnt = (size_t)old_leaves.size() * nv * M * nc;
     old_state.resize(cnt);
-    if (f->precision == DGF_FP64) {
-      dgf_status st = copy_state(f, old_state.data(), f->U[0].ptr, cnt * 8, cudaMemcpyDeviceToHost);
+    if (state_f64(f)) {
+      dgf_status st = copy_state(f, old_state.data(), state_ptr(f), cnt * 8, cudaMemcpyDeviceToHost);
       if (st) return st;
     } else {
       std::vector<float> tmp(cnt);
@@ -1233,8 +1300,8 @@ static dgf_status regrid(dgf_forest* f, const std::vector<uint64_t>& old_leaves)
   }
   host_convert(f, ns, L, true);
   DeviceGuard dg(f->device);
-  if (f->precision == DGF_FP64) {
-    st = copy_state(f, f->U[0].ptr, ns.data(), ns.size() * 8, cudaMemcpyHostToDevice);
+  if (state_f64(f)) {
+    st = copy_state(f, state_ptr(f), ns.data(), ns.size() * 8, cudaMemcpyHostToDevice);
   } else {
     std::vector<float> tmp(ns.begin(), ns.end());
     st = copy_state(f, f->U[0].ptr, tmp.data(), tmp.size() * 4, cudaMemcpyHostToDevice);
@@ -1279,6 +1346,7 @@ extern "C" dgf_status dgf_dg_residual_noalloc(dgf_forest* f, const void* U_nodal
   if (dgf_status st = require_device(f)) return st;
   if (!U_nodal || !L_nodal) return fail(DGF_EINVAL, "null state pointer");
   if (U_nodal == L_nodal) return fail(DGF_EINVAL, "input and output must not alias");
+  if (f->comp) return fail(DGF_EUNSUPPORTED, "dgf_dg_residual_noalloc: compensated forests are not supported");
   DeviceGuard dg(f->device);
   const size_t need = (size_t)f->nL * 2 * f->d * f->nv * f->NFP * f->nt * f->esize;
   if (need > kNoAllocScratchBytes)

@@ -40,6 +40,11 @@ static int stage_blocks_per_sm_ns() {
   if (cudaFuncSetAttribute(k_stage<D, P, NS, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;
+  if constexpr (std::is_same<Real, float>::value) {
+    if (cudaFuncSetAttribute(k_stage<D, P, NS, Real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return 0;
+  }
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage<D, P, NS, Real>, StageCfg<P, Real>::NT, smem) !=
       cudaSuccess)
@@ -58,10 +63,17 @@ static int stage_blocks_per_sm(int n) {
 }
 
 template <int D, int P, int NS, typename Real>
-static cudaError_t stage_ns(const StageArgs<D, P, Real>& a, int slots, cudaStream_t s) {
+static cudaError_t stage_ns(const StageArgs<D, P, Real>& a, int slots, int comp, cudaStream_t s) {
   const size_t smem = stage_smem<D, P, Real>(NS);
   const int items = a.nL * a.nchunks;
   const int grid = items < slots ? items : slots;
+  if constexpr (std::is_same<Real, float>::value) {
+    if (comp) {
+      k_stage<D, P, NS, Real, true><<<grid, StageCfg<P, Real>::NT, smem, s>>>(a);
+      return cudaGetLastError();
+    }
+  }
+  if (comp) return cudaErrorInvalidValue;
   k_stage<D, P, NS, Real><<<grid, StageCfg<P, Real>::NT, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -93,12 +105,15 @@ static cudaError_t stage_p(const RtStage& r, cudaStream_t s) {
   a.gamma = (Real)r.gamma;
   a.mode = r.mode;
   a.last = r.last;
+  a.U64 = r.U64;
+  a.Din = r.Din;
+  a.U64out = r.U64out;
   a.T = make_tab<P + 1, Real>(r.T);
   if (r.slots <= 0) return cudaErrorInvalidConfiguration;
   switch (r.n) {
-    case 2: return stage_ns<D, P, 2, Real>(a, r.slots, s);
-    case 4: return stage_ns<D, P, 4, Real>(a, r.slots, s);
-    case 8: return stage_ns<D, P, 8, Real>(a, r.slots, s);
+    case 2: return stage_ns<D, P, 2, Real>(a, r.slots, r.comp, s);
+    case 4: return stage_ns<D, P, 4, Real>(a, r.slots, r.comp, s);
+    case 8: return stage_ns<D, P, 8, Real>(a, r.slots, r.comp, s);
   }
   return cudaErrorInvalidConfiguration;
 }
@@ -110,6 +125,8 @@ static cudaError_t guard_p(const RtGuard& r, cudaStream_t s) {
   a.n = r.n;
   a.mode = r.mode;
   a.U = (const Real*)r.U;
+  a.U64 = r.U64;
+  a.Din = r.Din;
   a.out = (Real*)r.out;
   a.kind = r.kind;
   a.nbr = r.nbr;
@@ -128,15 +145,30 @@ static cudaError_t guard_p(const RtGuard& r, cudaStream_t s) {
     const size_t items = (size_t)r.nL * 2 * D * (D + 2) * nt;
     const size_t ntb = (items + NTH - 1) / NTH;
     const int nfb = r.nfine * nt;
+    if constexpr (std::is_same<Real, float>::value) {
+      if (r.comp) {
+        k_guard_trace<D, P, Real, true><<<(unsigned)(ntb + nfb), NTH, 0, s>>>(a, nfb);
+        return cudaGetLastError();
+      }
+    }
     k_guard_trace<D, P, Real><<<(unsigned)(ntb + nfb), NTH, 0, s>>>(a, nfb);
     return cudaGetLastError();
   }
   const size_t total = (size_t)r.nL * 2 * D * nt * (D + 2);
   const int th = 128;
+  const size_t ctas = (size_t)r.nfine * nt * (D + 2);
+  if constexpr (std::is_same<Real, float>::value) {
+    if (r.comp) {
+      k_guard<D, P, Real, true><<<(unsigned)((total + th - 1) / th), th, 0, s>>>(a);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess || r.nfine == 0) return e;
+      k_guard_fine<D, P, Real, true><<<(unsigned)ctas, 32 << D, 0, s>>>(a);
+      return cudaGetLastError();
+    }
+  }
   k_guard<D, P, Real><<<(unsigned)((total + th - 1) / th), th, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || r.nfine == 0) return e;
-  const size_t ctas = (size_t)r.nfine * nt * (D + 2);
   k_guard_fine<D, P, Real><<<(unsigned)ctas, 32 << D, 0, s>>>(a);
   return cudaGetLastError();
 }

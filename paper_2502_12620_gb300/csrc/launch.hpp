@@ -32,11 +32,18 @@ struct RtStage {
   int* status;
   double ca, cb, gamma;
   int mode, last;
+  int comp;             // compensated form (FP32 kernels only)
+  const double* U64;    // compensated: u^n
+  const float* Din;     // compensated: delta^(k) or null
+  double* U64out;       // compensated, last stage: u^(n+1)
   RtTables T;
 };
 
 struct RtGuard {
   int p, nL, n, mode;
+  int comp;
+  const double* U64;
+  const float* Din;
   const void* U;
   void* out;
   const int* kind;

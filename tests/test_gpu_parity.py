@@ -205,3 +205,35 @@ def test_nonfinite_state_sets_status_word(dgf):
     assert f.status_word(reset=True) == -4
     f.rk_step()
     assert f.status_word() == -4
+
+
+# ----------------------------------------------------- compensated FP32 form
+@pytest.mark.parametrize("case", ["pair_2d", "jitter_3d_n2"])
+def test_compensated_residual_and_steps_match_oracle(dgf, case):
+    w = _small(case)
+    f, S = _pair(dgf, w, 2, dgf.FP32_COMP, cfl=0.2)
+    U = W.random_modal_state(f.n_leaves, f.dim, f.n_seg, 2, seed=9)
+    f.set_state(U)
+    assert rel(f.get_state(), U) < 1e-15  # the state itself is FP64
+    assert rel(f.dg_residual(), S.residual(U)) < TOL["fp32"]
+    for _ in range(3):
+        U = S.ssp_rk3_step(U, S.dt(U))
+        f.rk_step()
+    assert rel(f.get_state(), U) < TOL["fp32"]
+
+
+def test_compensated_state_drifts_less_than_plain_fp32(dgf):
+    """Over many steps the FP64-accumulated state stays closer to the FP64
+    path than the plain FP32 state does (both run the residual in FP32)."""
+    w = W.lattice_forest(2, 2, 10.0, 8)
+    runs = {}
+    for name, prec in (("fp64", dgf.FP64), ("fp32", dgf.FP32), ("comp", dgf.FP32_COMP)):
+        f = dgf.Forest.from_workload(w, p=2, precision=prec, cfl=0.1)
+        f.project(W.isentropic_vortex)
+        for _ in range(300):
+            f.rk_step()
+        runs[name] = f.get_state().astype(np.float64)
+    e32 = rel(runs["fp32"], runs["fp64"])
+    ec = rel(runs["comp"], runs["fp64"])
+    assert ec < TOL["fp32"] and e32 < TOL["fp32"]
+    assert ec < 0.5 * e32, (ec, e32)
