@@ -11,6 +11,7 @@ on the last stage).  Metric: DG DOF-updates per second per RK stage
 (= DOF x 3 x steps / time).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --serve [--serve-requests R] [--serve-active A]
 
 Timing: CUDA events on the forest's stream around each step, an L2 flush
 (256 MiB write) before every timed step, warm-up steps first, barrier and
@@ -348,10 +349,98 @@ def run_ours(args):
         "e2e": e2e,
         "clocks": ck.summary(),
         "gpu_launches": int(sum(c for _, c in kt.values())),
+        "tuning": f32.tuning(),
         "status_word": status,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- serving
+SERVE_MIX = dict(rate=20.0, seed=0, blocks=(64, 512), degrees=(1, 2, 3), t_end=(0.05, 0.5), t_scale=0.1)
+
+
+def run_serve(args):
+    """Continuous batching: Poisson arrivals of independent solves (blast or
+    vortex, periodic cubes of 64-512 blocks, p in 1..3, FP32), each admitted
+    by its device footprint, built on a worker thread (forest, upload of its
+    initial values, projection on the device) and advanced on its own stream.  Reports the aggregate
+    DOF-update rate over the whole run and p50/p99 time to solution."""
+    import torch
+    import paper_2502_12620_gb300 as pkg
+    from paper_2502_12620_gb300 import serve
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    mix = W.serving_mix(args.serve_requests, **SERVE_MIX)
+    # request payloads, made before the run: each solve's initial values at its
+    # quadrature points (the vortex payload is shared by requests of one shape)
+    t_prep = time.perf_counter()
+    qp, vort = {}, {}
+    for m in mix:
+        key = (m["B"], m["p"])
+        if key not in qp:
+            h = pkg.Forest.from_workload(W.periodic_cube_forest(m["B"], n_seg=m["n_seg"]), p=m["p"], device=-1)
+            qp[key] = h.quad_points()
+            h.close()
+
+    def payload(m):
+        key = (m["B"], m["p"])
+        if m["kind"] == "vortex":
+            if key not in vort:
+                vort[key] = W.serving_initial(m)(qp[key])
+            return vort[key]
+        return W.serving_initial(m)(qp[key])
+
+    from concurrent.futures import ThreadPoolExecutor
+    for m in mix:  # vortex payloads first, once per shape
+        if m["kind"] == "vortex":
+            payload(m)
+    with ThreadPoolExecutor(8) as ex:
+        vals = list(ex.map(payload, mix))
+    qp.clear()
+    t_prep = time.perf_counter() - t_prep
+    reqs = [serve.Request(m["rid"], m["arrival"], W.periodic_cube_forest(m["B"], n_seg=m["n_seg"]), m["p"],
+                          m["t_end"], ("nodal", v), pkg.FP32) for m, v in zip(mix, vals)]
+    # warm-up: one small solve of every degree (module load, allocator pool)
+    warm = [serve.Request(-1 - p, 0.0, W.periodic_cube_forest(2), p, 1e-3, W.smooth_state, pkg.FP32)
+            for p in SERVE_MIX["degrees"]]
+    serve.Server(device=local, max_active=4).run(warm)
+    srv = serve.Server(device=local, max_active=args.serve_active, steps_per_round=8)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as ck:
+        t0 = time.perf_counter()
+        res = srv.run(reqs)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    sm = serve.summarize(res, wall)
+    updates = sum(r.dof * 3 * r.steps for r in res)
+    value, ms = job_throughput(updates, 1e3 * wall, ws)
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "serving: aggregate DG DOF-updates/s per RK stage", "value": value, "unit": "DOF-updates/s",
+        "n_gpus": ws, "steps": len(res), "warmup": len(warm), "ms_per_step": ms / max(1, len(res)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serving-mix-periodic-cubes-64-512-blocks-n8-p1-3-blast-or-vortex",
+                   "requests": len(res), **{k: list(v) if isinstance(v, tuple) else v for k, v in SERVE_MIX.items()},
+                   "max_active": args.serve_active, "hbm_budget_bytes": srv.budget},
+        "serve": {"p50_s": sm["p50_s"], "p99_s": sm["p99_s"], "wall_s": wall,
+                  "peak_active": srv.peak_active, "peak_bytes": srv.peak_bytes,
+                  "failed": sum(1 for r in res if r.status != 0),
+                  "mean_queue_s": float(np.mean([r.admitted - r.arrival for r in res])),
+                  "dof_updates": updates,
+                  "payload": "initial values at the quadrature points, FP64, made before the run",
+                  "payload_prep_s": t_prep},
+        "clocks": ck.summary(),
+    }
     print(json.dumps(line))
     return 0
 
@@ -365,12 +454,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="jitter3d", choices=sorted(WORKLOADS))
     ap.add_argument("--quick", action="store_true", help="FP32 timed steps only (profiling runs)")
+    ap.add_argument("--serve", action="store_true", help="continuous-batching run instead of the step benchmark")
+    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-active", type=int, default=8)
     args = ap.parse_args()
     _SEL[0] = args.workload
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serve(args)
     return run_ours(args)
 
 

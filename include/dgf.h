@@ -167,11 +167,19 @@ dgf_status dgf_dg_residual(dgf_forest* f, void* dst, int is_device);
  * min over cells and quadrature points of h / sum_i(|u_i| + c), clipped so
  * that time does not pass t_end; three stages of guard fill + residual +
  * Shu-Osher combination.  dt stays on the device; if dt_out is non-NULL the
- * call synchronises and returns it. */
+ * call synchronises and returns it.  Once t = t_end the increment is zero and
+ * leaves the state unchanged bit for bit (no stage is evaluated), so a
+ * scheduler may enqueue steps past t_end. */
 dgf_status dgf_rk_step(dgf_forest* f, double t_end, double* dt_out);
-/* Current time (synchronises) / reset it. */
+/* Current time (synchronises) / reset it; dgf_set_time also zeroes the
+ * step count below. */
 dgf_status dgf_get_time(dgf_forest* f, double* t);
 dgf_status dgf_set_time(dgf_forest* f, double t);
+/* Number of time increments taken with dt > 0 since creation or the last
+ * dgf_set_time (increments clipped to dt = 0 at t_end are not counted);
+ * synchronises the forest's stream.  Bookkeeping for schedulers: the paper
+ * has no counterpart. */
+dgf_status dgf_step_count(dgf_forest* f, int64_t* steps);
 /* CFL time increment of the current state (synchronises). */
 dgf_status dgf_compute_dt(dgf_forest* f, double* dt);
 
@@ -181,6 +189,16 @@ dgf_status dgf_conserved_totals(dgf_forest* f, double* totals);
 
 /* Device status word: 0 or DGF_ENONFINITE (synchronises); reset clears it. */
 dgf_status dgf_status_word(dgf_forest* f, int32_t* status, int reset);
+
+/* Tile of the stage kernel: a work item is a z-chunk of zchunk cell layers
+ * of one block (3D), resident_ctas the persistent grid size.  The first
+ * dgf_rk_step of a 3D forest times one residual evaluation for every chunk
+ * length n_seg, n_seg/2, ..., 1 and keeps the fastest; later forests of the
+ * same device, dimension, degree, n_seg, precision and leaf count in the
+ * process reuse that choice (the environment variable DGF_ZCHUNK fixes it
+ * instead).  The chunk length changes no bit of any result.  Not a paper
+ * quantity: the paper's per-block loop (Sec. 4.3) has no tiling. */
+dgf_status dgf_tuning(const dgf_forest* f, int32_t* zchunk, int32_t* resident_ctas);
 
 /* Kernel timing: when on, rk_step launches stage by stage (no graph) with
  * CUDA events around every kernel; dgf_kernel_times synchronises and returns

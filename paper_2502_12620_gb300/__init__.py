@@ -68,11 +68,13 @@ _SIGS = {
     "dgf_dg_residual": [_P, _P, ctypes.c_int],
     "dgf_rk_step": [_P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
     "dgf_get_time": [_P, ctypes.POINTER(ctypes.c_double)],
+    "dgf_step_count": [_P, ctypes.POINTER(ctypes.c_int64)],
     "dgf_set_time": [_P, ctypes.c_double],
     "dgf_compute_dt": [_P, ctypes.POINTER(ctypes.c_double)],
     "dgf_conserved_totals": [_P, _P],
     "dgf_status_word": [_P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int],
     "dgf_set_timing": [_P, ctypes.c_int],
+    "dgf_tuning": [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
     "dgf_kernel_times": [_P, _P, _P, ctypes.c_int],
     "dgf_dg_residual_noalloc": [_P, _P, _P],
 }
@@ -208,6 +210,12 @@ class Forest:
             pass
 
     @property
+    def device_bytes(self):
+        """Device bytes the library holds for this forest (0 when it allocates
+        through CUDA directly)."""
+        return sum(self._alloc.live.values()) if self._alloc is not None else 0
+
+    @property
     def n_leaves(self):
         n = ctypes.c_int64()
         _check(lib().dgf_leaf_count(self.h, ctypes.byref(n)))
@@ -300,6 +308,13 @@ class Forest:
         _check(lib().dgf_get_time(self.h, ctypes.byref(t)))
         return t.value
 
+    @property
+    def step_count(self):
+        """Time increments taken with dt > 0 since creation / set_time."""
+        n = ctypes.c_int64()
+        _check(lib().dgf_step_count(self.h, ctypes.byref(n)))
+        return n.value
+
     def set_time(self, t):
         _check(lib().dgf_set_time(self.h, float(t)))
 
@@ -317,6 +332,12 @@ class Forest:
         s = ctypes.c_int32()
         _check(lib().dgf_status_word(self.h, ctypes.byref(s), int(reset)))
         return s.value
+
+    def tuning(self):
+        z = ctypes.c_int32()
+        c = ctypes.c_int32()
+        _check(lib().dgf_tuning(self.h, ctypes.byref(z), ctypes.byref(c)))
+        return {"zchunk": z.value, "resident_ctas": c.value}
 
     def set_timing(self, on):
         _check(lib().dgf_set_timing(self.h, int(on)))

@@ -64,7 +64,7 @@ def build(verbose=False, ptxas_info=False, jobs=None):
         for out in ex.map(_run, cmds):
             logs.append(out)
     tmp = LIB + ".tmp"
-    _run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
+    _run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"])
     os.replace(tmp, LIB)
     if verbose:
         for l in logs:

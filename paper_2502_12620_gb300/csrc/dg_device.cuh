@@ -417,6 +417,18 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
   const Real dt = Real(*A.dtp);
   const int tid = threadIdx.x;
   constexpr int nthr = StageCfg<P, Real>::NT;
+  if (A.mode == 0 && *A.dtp == 0.0) {
+    // t_end reached: the increment is the identity and no stage is evaluated
+    // (the CFL minimum of the last evaluated stage stays in place)
+    if constexpr (COMP) {
+      if (A.last) {
+        const size_t tot = (size_t)A.nL * NV * Q * nc;
+        for (size_t i = (size_t)blockIdx.x * nthr + tid; i < tot; i += (size_t)gridDim.x * nthr)
+          A.U64out[i] = A.U64[i];
+      }
+    }
+    return;
+  }
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Real sx[N];
@@ -529,9 +541,17 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
             if (aff) {
 #pragma unroll
               for (int j = 0; j < 3; ++j) Ja[j] = sam[6 + j];
-            } else {
+            } else if (k0 == 0) {
               const Real xi[3] = {sx[fp % N], sx[fp / N], Real(-1)};
               point_row<3, Real>(Gk + c, nc, xi, 2, Ja);
+            } else {
+              // the metric of the layer below at its top face, exactly as the
+              // carried flux of an unchunked sweep, so the result does not
+              // depend on the chunk length
+              const Real xi[3] = {sx[fp % N], sx[fp / N], Real(0)};
+              LineGeo<3, 2, Real> lg;
+              lg.init(Gk - NCL + c, nc, xi);
+              lg.at(Real(1), Ja);
             }
             lf_flux<3, Real>(uL, uR, Ja, gamma, Fh);
 #pragma unroll

@@ -10,11 +10,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/dgf.h"
@@ -36,7 +39,7 @@ struct DevScalars {
   double t, dt, t_end;
   unsigned long long lam_bits;  // min over cells of h / lambda, as double bits
   int status;
-  int pad;
+  int steps;  // time increments taken with dt > 0 since creation / dgf_set_time
 };
 
 constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
@@ -54,7 +57,9 @@ __global__ void k_dt(DevScalars* s, double cfl) {
   }
   s->dt = dt;
   s->t = s->t + dt;
-  s->lam_bits = kInfBits;
+  s->steps += dt > 0.0;
+  // a zero increment evaluates no stage, so the CFL minimum is kept for the next
+  if (dt > 0.0) s->lam_bits = kInfBits;
 }
 
 __global__ void k_reset_lam(DevScalars* s) { s->lam_bits = kInfBits; }
@@ -133,6 +138,7 @@ struct dgf_forest {
   cudaGraphExec_t graph = nullptr;
   double t_end_dev = NAN;
   int zchunk = 0;
+  bool tuned = false;  // z-chunk length chosen by timing (first time step)
   bool timing = false;
   struct TEv {
     cudaEvent_t a, b;
@@ -239,6 +245,25 @@ bool chol_solve(int M, std::vector<double>& A, std::vector<double>& B, int nrhs)
 
 // Build every leaf-dependent device array: integer tables, FP64 geometry,
 // cell sizes, combine operators, state and scratch buffers.
+// fn(0 .. n-1) on up to 16 host threads; every index writes its own outputs,
+// so the result does not depend on the schedule
+template <class Fn>
+void parallel_for(int64_t n, Fn&& fn) {
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int64_t nt = std::min<int64_t>(std::min<unsigned>(hw, 16u), n);
+  if (nt <= 1) {
+    for (int64_t i = 0; i < n; ++i) fn(i);
+    return;
+  }
+  std::atomic<int64_t> next{0};
+  std::vector<std::thread> pool;
+  for (int64_t t = 0; t < nt; ++t)
+    pool.emplace_back([&]() {
+      for (int64_t i; (i = next.fetch_add(1)) < n;) fn(i);
+    });
+  for (auto& th : pool) th.join();
+}
+
 dgf_status build_device(dgf_forest* f) {
   Forest& F = f->host;
   const int d = f->d, n = f->n, nf = 2 * d, M = f->M, nc = f->nc, NG = f->NG, N = f->N;
@@ -262,11 +287,13 @@ dgf_status build_device(dgf_forest* f) {
     qbits[i] = q;
   }
 
-  // geometry: per-cell trilinear coefficients (c >= 1) and sizes h
+  // geometry: per-cell trilinear coefficients (c >= 1) and sizes h; the
+  // leaves are independent, so host threads take them in any order
   std::vector<std::vector<double>> coef(L);
   std::vector<double> geo64((size_t)L * NG * nc), hcell((size_t)L * nc);
   const Basis1D& B = f->basis;
-  for (int64_t i = 0; i < L; ++i) {
+  for (int64_t i = 0; i < L; ++i) F.block_nodes(F.leaves[i]);  // fills the node cache; reads only below
+  parallel_for(L, [&](int64_t i) {
     F.cell_coefficients(F.leaves[i], coef[i]);
     for (int g = 0; g < NG; ++g)
       for (int c = 0; c < nc; ++c) geo64[((size_t)i * NG + g) * nc + c] = coef[i][(size_t)(d + g) * nc + c];
@@ -288,7 +315,7 @@ dgf_status build_device(dgf_forest* f) {
       }
       hcell[(size_t)i * nc + c] = std::pow(vol, 1.0 / d);
     }
-  }
+  });
 
   // affine blocks: every cell a congruent parallelogram/parallelepiped ->
   // constant J dxi/dx rows and 1/J per block
@@ -339,9 +366,11 @@ dgf_status build_device(dgf_forest* f) {
   cop.assign((size_t)nops * M * KC, 0.0);
   const int NFPh = f->NFP;
   std::vector<double> ctr((size_t)nops * NFPh * KC, 0.0);
-  for (int64_t i = 0; i < L; ++i) {
-    for (int fc = 0; fc < nf; ++fc) {
-      if (kind[i * nf + fc] != kFiner) continue;
+  std::atomic<bool> singular{false};
+  parallel_for((int64_t)fine_list.size(), [&](int64_t fi) {
+    {
+      const int64_t i = fine_list[fi] / nf;
+      const int fc = fine_list[fi] % nf;
       const Orient o = orient_from_code(T.orient[i * nf + fc], d);
       const int a = fc >> 1, s = fc & 1;
       const int b2 = o.pi[a];
@@ -399,7 +428,10 @@ dgf_status build_device(dgf_forest* f) {
             }
           }
         }
-        if (!chol_solve(M, MP, RHS, KC)) return fail(DGF_EINVAL, "singular combine mass matrix");
+        if (!chol_solve(M, MP, RHS, KC)) {
+          singular = true;
+          return;
+        }
         // evaluate the parent polynomial (neighbour frame) at my Gauss points:
         // my point p sits at neighbour coordinates xi_{pi[a]} = sigma_a x_{p_a}
         double* dst = &cop[((size_t)copoff[i * nf + fc] + t) * M * KC];
@@ -441,7 +473,8 @@ dgf_status build_device(dgf_forest* f) {
         }
       }
     }
-  }
+  });
+  if (singular) return fail(DGF_EINVAL, "singular combine mass matrix");
 
   if (f->device < 0) return DGF_OK;
   DeviceGuard dg(f->device);
@@ -497,6 +530,7 @@ dgf_status build_device(dgf_forest* f) {
       if (const char* zc = getenv("DGF_ZCHUNK")) f->zchunk = std::max(1, std::min(n, atoi(zc)));
     }
   }
+  f->tuned = d != 3 || getenv("DGF_ZCHUNK") != nullptr;
   if (f->graph) {
     cudaGraphExecDestroy(f->graph);
     f->graph = nullptr;
@@ -642,6 +676,62 @@ dgf_status init_lambda(dgf_forest* f) {
   dgf_status st = cuda_check(cudaGetLastError(), "reset");
   if (st) return st;
   return cuda_check(do_cfl(f, misc_args(f, 0)), "cfl");
+}
+
+// Autotuner for the stage kernel's tile: time one residual evaluation (mode 1,
+// written to a scratch stage buffer, the state is untouched) for every
+// z-chunk length n, n/2, ..., 1 and keep the fastest (median of 3 launches).
+// chunk lengths chosen so far, by (device, dim, p, n, precision, leaves): a
+// forest of a shape already timed in this process takes the earlier choice
+std::mutex g_tune_mutex;
+std::map<std::vector<long long>, int> g_tune_cache;
+
+dgf_status autotune(dgf_forest* f) {
+  f->tuned = true;
+  if (f->d != 3 || f->slots <= 0) return DGF_OK;
+  const std::vector<long long> key = {f->device, f->d, f->p, f->n, f->precision, (long long)f->nL};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      f->zchunk = it->second;
+      return DGF_OK;
+    }
+  }
+  dgf_status st = cuda_check(do_guard(f, guard_args(f, 0, f->gtr.ptr, 1)), "guard");
+  if (st) return st;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  int best_z = f->zchunk;
+  float best = 1e30f;
+  for (int z = f->n; z >= 1; z /= 2) {
+    f->zchunk = z;
+    float t[3];
+    for (int r = 0; r < 4; ++r) {
+      cudaEventRecord(a, f->stream);
+      cudaError_t e = do_stage(f, stage_args(f, 0, 1, 0.0, 1.0, 1, 0));
+      cudaEventRecord(b, f->stream);
+      if (e != cudaSuccess) {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return cuda_check(e, "autotune");
+      }
+      cudaEventSynchronize(b);
+      if (r > 0) cudaEventElapsedTime(&t[r - 1], a, b);  // first launch warms up
+    }
+    std::sort(t, t + 3);
+    if (t[1] < best) {
+      best = t[1];
+      best_z = z;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  f->zchunk = best_z;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune_cache[key] = best_z;
+  return DGF_OK;
 }
 
 // enqueue one time increment; timing mode records events around kernels
@@ -1021,6 +1111,7 @@ dgf_status dgf_rk_step(dgf_forest* f, double t_end, double* dt_out) {
   DeviceGuard dg(f->device);
   dgf_status st = set_t_end(f, t_end);
   if (st) return st;
+  if (!f->tuned && (st = autotune(f))) return st;
   if (f->timing) {
     if ((st = enqueue_step(f))) return st;
   } else {
@@ -1067,7 +1158,21 @@ dgf_status dgf_set_time(dgf_forest* f, double t) {
   DeviceGuard dg(f->device);
   DevScalars* s = (DevScalars*)f->scal.ptr;
   double tt = t;
-  return copy_state(f, &s->t, &tt, sizeof(double), cudaMemcpyHostToDevice);
+  dgf_status st = copy_state(f, &s->t, &tt, sizeof(double), cudaMemcpyHostToDevice);
+  if (st) return st;
+  int zero = 0;
+  return copy_state(f, &s->steps, &zero, sizeof(int), cudaMemcpyHostToDevice);
+}
+
+dgf_status dgf_step_count(dgf_forest* f, int64_t* steps) {
+  if (dgf_status st = require_device(f)) return st;
+  if (!steps) return fail(DGF_EINVAL, "null argument");
+  DeviceGuard dg(f->device);
+  DevScalars* s = (DevScalars*)f->scal.ptr;
+  int v = 0;
+  dgf_status st = copy_state(f, &v, &s->steps, sizeof(int), cudaMemcpyDeviceToHost);
+  *steps = v;
+  return st;
 }
 
 dgf_status dgf_compute_dt(dgf_forest* f, double* dt) {
@@ -1108,6 +1213,13 @@ dgf_status dgf_status_word(dgf_forest* f, int32_t* status, int reset) {
     int z = 0;
     return copy_state(f, &s->status, &z, sizeof(int), cudaMemcpyHostToDevice);
   }
+  return DGF_OK;
+}
+
+dgf_status dgf_tuning(const dgf_forest* f, int32_t* zchunk, int32_t* resident_ctas) {
+  if (!f) return fail(DGF_EINVAL, "null forest");
+  if (zchunk) *zchunk = f->zchunk;
+  if (resident_ctas) *resident_ctas = f->slots;
   return DGF_OK;
 }
 

@@ -4,6 +4,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <string>
+#include <unordered_map>
 
 namespace dgf {
 
@@ -230,68 +232,134 @@ bool Forest::match_root_faces() {
   };
   const int nfc = 1 << (d - 1);
   rface.assign(R * nf, RootFace());
+  // exact test of one candidate face, in the rule's order: shared node ids,
+  // then each periodic translation
+  auto try_match = [&](int64_t r, int f, int64_t r2, int f2, int* corr) -> bool {
+    int mine[4], theirs[4];
+    face_corners(f, mine);
+    face_corners(f2, theirs);
+    int64_t a_ids[4], b_ids[4], sa[4], sb[4];
+    for (int i = 0; i < nfc; ++i) {
+      sa[i] = a_ids[i] = root_corners[r * nck + mine[i]];
+      sb[i] = b_ids[i] = root_corners[r2 * nck + theirs[i]];
+    }
+    std::sort(sa, sa + nfc);
+    std::sort(sb, sb + nfc);
+    if (std::equal(sa, sa + nfc, sb)) {
+      for (int i = 0; i < nfc; ++i)
+        for (int j = 0; j < nfc; ++j)
+          if (b_ids[j] == a_ids[i]) corr[mine[i]] = theirs[j];
+      return true;
+    }
+    for (const auto& t : shifts) {
+      bool ok = true;
+      int used[4], nused = 0;
+      for (int i = 0; i < nfc && ok; ++i) {
+        const double* x = &nodes[a_ids[i] * d];
+        int hits = 0, hit = -1;
+        for (int j = 0; j < nfc; ++j) {
+          const double* y = &nodes[b_ids[j] * d];
+          double m = 0.0;
+          for (int c = 0; c < d; ++c) m = std::max(m, std::fabs(x[c] + t[c] - y[c]));
+          if (m <= tol) {
+            ++hits;
+            hit = j;
+          }
+        }
+        if (hits != 1 || std::find(used, used + nused, hit) != used + nused) ok = false;
+        else {
+          used[nused++] = hit;
+          corr[mine[i]] = theirs[hit];
+        }
+      }
+      if (ok) return true;
+    }
+    return false;
+  };
+  // candidate lookup: faces by sorted corner ids, and by face centre on a
+  // grid of cells 8 tol wide.  A face that matches under a translation has
+  // its centre within tol of the translated centre, so every face is filed
+  // under each cell its tol-box touches and one cell is looked up per shift.
+  const double cell = 8.0 * tol;
+  auto face_ids = [&](int64_t r, int f) {
+    int c[4];
+    face_corners(f, c);
+    std::vector<int64_t> ids(nfc);
+    for (int i = 0; i < nfc; ++i) ids[i] = root_corners[r * nck + c[i]];
+    std::sort(ids.begin(), ids.end());
+    return ids;
+  };
+  auto face_centre = [&](int64_t r, int f, double* x) {
+    int c[4];
+    face_corners(f, c);
+    for (int j = 0; j < d; ++j) x[j] = 0.0;
+    for (int i = 0; i < nfc; ++i)
+      for (int j = 0; j < d; ++j) x[j] += nodes[root_corners[r * nck + c[i]] * d + j] / nfc;
+  };
+  auto cell_key = [&](const int64_t* q) {
+    uint64_t h = 1469598103934665603ull;
+    for (int j = 0; j < d; ++j) h = (h ^ (uint64_t)q[j]) * 1099511628211ull;
+    return h;
+  };
+  std::unordered_map<std::string, std::vector<int64_t>> by_ids;
+  std::unordered_map<uint64_t, std::vector<int64_t>> by_cell;
+  for (int64_t r2 = 0; r2 < R; ++r2)
+    for (int f2 = 0; f2 < nf; ++f2) {
+      const std::vector<int64_t> ids = face_ids(r2, f2);
+      by_ids[std::string((const char*)ids.data(), ids.size() * sizeof(int64_t))].push_back(r2 * nf + f2);
+      double x[3];
+      face_centre(r2, f2, x);
+      int64_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+      for (int j = 0; j < d; ++j) {
+        lo[j] = (int64_t)std::floor((x[j] - tol) / cell);
+        hi[j] = (int64_t)std::floor((x[j] + tol) / cell);
+      }
+      for (int o = 0; o < (1 << d); ++o) {
+        int64_t q[3] = {0, 0, 0};
+        bool dup = false;
+        for (int j = 0; j < d; ++j) {
+          q[j] = ((o >> j) & 1) ? hi[j] : lo[j];
+          if (((o >> j) & 1) && hi[j] == lo[j]) dup = true;
+        }
+        if (!dup) by_cell[cell_key(q)].push_back(r2 * nf + f2);
+      }
+    }
   for (int64_t r = 0; r < R; ++r) {
     for (int f = 0; f < nf; ++f) {
-      int mine[4];
-      face_corners(f, mine);
+      std::vector<int64_t> cand;
+      {
+        const std::vector<int64_t> ids = face_ids(r, f);
+        auto it = by_ids.find(std::string((const char*)ids.data(), ids.size() * sizeof(int64_t)));
+        if (it != by_ids.end()) cand.insert(cand.end(), it->second.begin(), it->second.end());
+      }
+      double x[3];
+      face_centre(r, f, x);
+      for (const auto& t : shifts) {
+        int64_t q[3] = {0, 0, 0};
+        for (int j = 0; j < d; ++j) q[j] = (int64_t)std::floor((x[j] + t[j]) / cell);
+        auto it = by_cell.find(cell_key(q));
+        if (it != by_cell.end()) cand.insert(cand.end(), it->second.begin(), it->second.end());
+      }
+      std::sort(cand.begin(), cand.end());
+      cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+      // the first face in (root, face) order that passes the exact test
       bool found = false;
       int corr[8];
       int64_t r2f = -1;
       int f2f = -1;
-      for (int64_t r2 = 0; r2 < R && !found; ++r2) {
-        for (int f2 = 0; f2 < nf && !found; ++f2) {
-          if (r2 == r && f2 == f) continue;
-          int theirs[4];
-          face_corners(f2, theirs);
-          // (1) shared node ids
-          std::vector<int64_t> a_ids(nfc), b_ids(nfc);
-          for (int i = 0; i < nfc; ++i) {
-            a_ids[i] = root_corners[r * nck + mine[i]];
-            b_ids[i] = root_corners[r2 * nck + theirs[i]];
-          }
-          std::vector<int64_t> sa = a_ids, sb = b_ids;
-          std::sort(sa.begin(), sa.end());
-          std::sort(sb.begin(), sb.end());
-          if (sa == sb) {
-            for (int i = 0; i < nfc; ++i)
-              for (int j = 0; j < nfc; ++j)
-                if (b_ids[j] == a_ids[i]) corr[mine[i]] = theirs[j];
-            found = true;
-            r2f = r2;
-            f2f = f2;
-            break;
-          }
-          // (2) periodic translations
-          for (const auto& t : shifts) {
-            bool ok = true;
-            std::vector<int> used;
-            for (int i = 0; i < nfc && ok; ++i) {
-              const double* x = &nodes[a_ids[i] * d];
-              int hits = 0, hit = -1;
-              for (int j = 0; j < nfc; ++j) {
-                const double* y = &nodes[b_ids[j] * d];
-                double m = 0.0;
-                for (int c = 0; c < d; ++c) m = std::max(m, std::fabs(x[c] + t[c] - y[c]));
-                if (m <= tol) {
-                  ++hits;
-                  hit = j;
-                }
-              }
-              if (hits != 1 || std::find(used.begin(), used.end(), hit) != used.end()) ok = false;
-              else {
-                used.push_back(hit);
-                corr[mine[i]] = theirs[hit];
-              }
-            }
-            if (ok) {
-              found = true;
-              r2f = r2;
-              f2f = f2;
-              break;
-            }
-          }
+      for (int64_t code : cand) {
+        const int64_t r2 = code / nf;
+        const int f2 = (int)(code % nf);
+        if (r2 == r && f2 == f) continue;
+        if (try_match(r, f, r2, f2, corr)) {
+          found = true;
+          r2f = r2;
+          f2f = f2;
+          break;
         }
       }
+      int mine[4];
+      face_corners(f, mine);
       if (!found) continue;
       // orientation from the corner correspondence
       RootFace rf;
@@ -591,8 +659,17 @@ const std::vector<double>& Forest::block_nodes(uint64_t k) {
 }
 
 void Forest::cell_coefficients(uint64_t k, std::vector<double>& out) {
-  const std::vector<double> X = block_nodes(k);
+  const std::vector<double>& X = node_cache_.count(k) ? node_cache_.at(k) : block_nodes(k);
   const int nc = (int)std::pow(n, d), nn1 = n + 1, ncor = 1 << d;
+  // sign of corner kap in the coefficient of monomial c: prod over a in c of (+-1)
+  double sgn[8][8];
+  for (int c = 0; c < ncor; ++c)
+    for (int kap = 0; kap < ncor; ++kap) {
+      double s = 1.0;
+      for (int a = 0; a < d; ++a)
+        if ((c >> a) & 1) s *= ((kap >> a) & 1) ? 1.0 : -1.0;
+      sgn[c][kap] = s;
+    }
   out.assign((size_t)ncor * d * nc, 0.0);
   for (int cell = 0; cell < nc; ++cell) {
     int I[3] = {0, 0, 0}, t = cell;
@@ -600,19 +677,21 @@ void Forest::cell_coefficients(uint64_t k, std::vector<double>& out) {
       I[a] = t % n;
       t /= n;
     }
+    double xk[8][3];
     for (int kap = 0; kap < ncor; ++kap) {
       int J = 0, stride = 1;
       for (int a = 0; a < d; ++a) {
         J += (I[a] + ((kap >> a) & 1)) * stride;
         stride *= nn1;
       }
-      for (int c = 0; c < ncor; ++c) {
-        double sgn = 1.0;
-        for (int a = 0; a < d; ++a)
-          if ((c >> a) & 1) sgn *= ((kap >> a) & 1) ? 1.0 : -1.0;
-        for (int j = 0; j < d; ++j) out[((size_t)c * d + j) * nc + cell] += sgn * X[J * d + j] / ncor;
-      }
+      for (int j = 0; j < d; ++j) xk[kap][j] = X[J * d + j];
     }
+    for (int c = 0; c < ncor; ++c)
+      for (int j = 0; j < d; ++j) {
+        double acc = 0.0;
+        for (int kap = 0; kap < ncor; ++kap) acc += sgn[c][kap] * xk[kap][j] / ncor;
+        out[((size_t)c * d + j) * nc + cell] = acc;
+      }
   }
 }
 

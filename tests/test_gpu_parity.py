@@ -237,3 +237,25 @@ def test_compensated_state_drifts_less_than_plain_fp32(dgf):
     ec = rel(runs["comp"], runs["fp64"])
     assert ec < TOL["fp32"] and e32 < TOL["fp32"]
     assert ec < 0.5 * e32, (ec, e32)
+
+
+# ----------------------------------------------------- tiling invariance
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "fp32_comp"])
+def test_chunk_length_does_not_change_bits(dgf, prec, monkeypatch):
+    """The stage kernel's z-chunk length (a tiling choice, tuned by timing)
+    leaves every bit of the residual and of the stepped state unchanged, also
+    with a ragged last chunk, so results are reproducible run to run."""
+    w = W.jitter3d_forest(seed=2)
+    U0 = W.random_modal_state(71, 3, 8, 2, seed=11)
+    out = []
+    for z in (8, 4, 3, 1):
+        monkeypatch.setenv("DGF_ZCHUNK", str(z))
+        f = dgf.Forest.from_workload(w, p=2, precision=prec)
+        assert f.tuning()["zchunk"] == z
+        f.set_state(U0)
+        R = f.dg_residual()
+        f.run(2)
+        out.append((R, f.get_state()))
+        f.close()
+    for R, U in out[1:]:
+        assert np.array_equal(R, out[0][0]) and np.array_equal(U, out[0][1])

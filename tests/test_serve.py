@@ -1,0 +1,216 @@
+"""Continuous batching of independent solves.
+
+Host logic (admission by footprint and slot count, first-come-first-served
+order, step accounting) runs on CPU with stand-in solves; on the GPU every
+solve served in a mix must equal, bit for bit, the same solve run alone, and
+an increment at t = t_end must leave the state unchanged."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from paper_2502_12620_gb300 import FP32, FP32_COMP, FP64
+from paper_2502_12620_gb300.serve import Request, Server, footprint_bytes, summarize
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += max(dt, 1e-4)
+
+
+class FakeSolve:
+    """Advances time by a fixed dt per step; every stream is always idle."""
+    log = []
+
+    def __init__(self, req, clock, dt=0.01, nbytes=None):
+        self.req, self.clock, self.dt = req, clock, dt
+        self.t, self.steps, self.dof = 0.0, 0, 100
+        self.device_bytes = nbytes if nbytes is not None else footprint_bytes(req.workload, req.p, req.precision)
+        FakeSolve.log.append(("admit", req.rid))
+
+    def enqueue(self, k):
+        for _ in range(k):
+            d = min(self.dt, self.req.t_end - self.t)
+            if d > 0:
+                self.t += d
+                self.steps += 1
+        self.clock.t += 1e-3 * k
+
+    def idle(self):
+        return True
+
+    def progress(self):
+        return self.t, self.steps
+
+    def finish(self, keep_state):
+        FakeSolve.log.append(("finish", self.req.rid))
+        return None, 0
+
+
+def _req(rid, arrival, B=2, p=1, t_end=0.1):
+    return Request(rid, arrival, W.periodic_cube_forest(B, n_seg=2), p, t_end, None, FP32)
+
+
+def test_footprint_monotone():
+    fixed = 1 << 20
+    small = footprint_bytes(W.periodic_cube_forest(2, n_seg=8), 1) - fixed
+    big = footprint_bytes(W.periodic_cube_forest(4, n_seg=8), 1) - fixed
+    p3 = footprint_bytes(W.periodic_cube_forest(2, n_seg=8), 3) - fixed
+    assert big == 8 * small  # proportional to the leaf count
+    assert p3 > 6 * small
+    assert footprint_bytes(W.periodic_cube_forest(2, n_seg=8), 1, FP64) - fixed > 1.5 * small
+    # three FP32 copies of 64 roots x 512 cells x 8 modes x 5 variables
+    assert small > 3 * 8 * 512 * 8 * 5 * 4
+
+
+def test_admission_budget_and_order():
+    clock = FakeClock()
+    FakeSolve.log = []
+    reqs = [_req(i, 0.001 * i, t_end=0.05 + 0.01 * (i % 3)) for i in range(10)]
+    one = footprint_bytes(reqs[0].workload, 1)
+    srv = Server(hbm_budget=int(2.5 * one), max_active=8, steps_per_round=3,
+                 build_workers=0, solve_factory=lambda r: FakeSolve(r, clock), clock=clock, sleep=clock.sleep)
+    res = srv.run(reqs)
+    assert srv.peak_active == 2 and srv.peak_bytes <= srv.budget
+    admits = [rid for ev, rid in FakeSolve.log if ev == "admit"]
+    assert admits == list(range(10))  # first come, first served
+    for r, q in zip(res, reqs):
+        assert r.rid == q.rid and abs(r.t - q.t_end) < 1e-12
+        assert r.steps == math.ceil(q.t_end / 0.01 - 1e-9)
+        assert r.finished >= r.admitted >= r.arrival - 1e-12
+    s = summarize(res, clock.t)
+    assert s["requests"] == 10 and s["p99_s"] >= s["p50_s"] > 0
+
+
+def test_slot_limit_and_oversize():
+    clock = FakeClock()
+    FakeSolve.log = []
+    reqs = [_req(i, 0.0) for i in range(6)] + [_req(6, 0.0, B=3)]
+    srv = Server(hbm_budget=10 ** 12, max_active=4, steps_per_round=4,
+                 build_workers=0, solve_factory=lambda r: FakeSolve(r, clock), clock=clock, sleep=clock.sleep)
+    srv.run(reqs)
+    assert srv.peak_active == 4
+    # a request larger than the whole budget is admitted once it is alone
+    clock = FakeClock()
+    FakeSolve.log = []
+    small = footprint_bytes(reqs[0].workload, 1)
+    srv = Server(hbm_budget=small, max_active=4, build_workers=0, solve_factory=lambda r: FakeSolve(r, clock),
+                 clock=clock, sleep=clock.sleep)
+    res = srv.run([_req(0, 0.0), _req(1, 0.0, B=3), _req(2, 0.0)])
+    assert srv.peak_active == 1 and [r.rid for r in res] == [0, 1, 2]
+    ev = FakeSolve.log
+    assert ev.index(("finish", 0)) < ev.index(("admit", 1)) < ev.index(("finish", 1)) < ev.index(("admit", 2))
+
+
+def test_arrivals_wait():
+    clock = FakeClock()
+    FakeSolve.log = []
+    reqs = [_req(0, 0.5), _req(1, 0.2)]
+    srv = Server(hbm_budget=10 ** 12, build_workers=0, solve_factory=lambda r: FakeSolve(r, clock), clock=clock,
+                 sleep=clock.sleep)
+    res = srv.run(reqs)
+    assert [ev for ev in FakeSolve.log if ev[0] == "admit"] == [("admit", 1), ("admit", 0)]
+    assert res[0].admitted >= 0.5 and res[1].admitted >= 0.2
+
+
+def test_serving_mix_recipe():
+    R = W.serving_mix(256, seed=3)
+    arr = np.array([r["arrival"] for r in R])
+    assert np.all(np.diff(arr) > 0)
+    assert 256 / 20.0 * 0.7 < arr[-1] < 256 / 20.0 * 1.3  # Poisson, rate 20/s
+    blocks = np.array([r["B"] ** 3 for r in R])
+    assert blocks.min() >= 27 and blocks.max() <= 21 ** 3
+    assert {r["p"] for r in R} == {1, 2, 3}
+    assert 0.3 < np.mean([r["kind"] == "blast" for r in R]) < 0.7
+    assert all(0.05 <= r["t_end"] <= 0.5 for r in R)
+    again = W.serving_mix(256, seed=3)  # seeded: the same stream every time
+    assert all(a["arrival"] == b["arrival"] and a["B"] == b["B"] and a["p"] == b["p"]
+               and np.array_equal(a["centre"], b["centre"]) for a, b in zip(R, again))
+
+
+# ------------------------------------------------------------------ GPU
+def _gpu_requests():
+    # a mix of dimensions, degrees, precisions and refinement
+    v2 = W.vortex2d_forest()
+    c2 = W.periodic_cube_forest(2, n_seg=4)
+    c3 = W.periodic_cube_forest(3, n_seg=2)
+    j = W.jitter3d_forest(seed=1, n_seg=2)
+    v2i = lambda x: W.isentropic_vortex(x)
+    sm = lambda x: W.smooth_state(x)
+    return [
+        Request(0, 0.0, v2, 2, 0.05, v2i, FP32),
+        Request(1, 0.0, c2, 1, 0.02, sm, FP32),
+        Request(2, 0.0, c2, 3, 0.01, sm, FP32),
+        Request(3, 0.0, j, 2, 0.01, sm, FP32_COMP),
+        Request(4, 0.0, c3, 2, 0.015, sm, FP64),
+        Request(5, 0.0, v2, 1, 0.04, v2i, FP64),
+    ]
+
+
+@pytest.mark.gpu
+def test_mixed_equals_alone():
+    from paper_2502_12620_gb300 import Forest
+    reqs = _gpu_requests()
+    alone = []
+    for q in reqs:
+        f = Forest.from_workload(q.workload, p=q.p, precision=q.precision)
+        f.project(q.init)
+        n = 0
+        while f.time < q.t_end:
+            f.rk_step(q.t_end)
+            n += 1
+            assert n < 10000
+        alone.append((f.get_state(), f.step_count, f.time))
+        f.close()
+    srv = Server(hbm_budget=4 << 30, max_active=6, steps_per_round=5)
+    res = srv.run(reqs, keep_state=True)
+    assert srv.peak_active == 6
+    for r, (U, steps, t) in zip(res, alone):
+        assert r.status == 0
+        assert r.steps == steps and r.t == t
+        assert r.state.dtype == U.dtype and np.array_equal(r.state, U), r.rid
+
+
+@pytest.mark.gpu
+def test_footprint_estimate_matches_allocation():
+    from paper_2502_12620_gb300 import Forest
+    for w, p, prec in [(W.periodic_cube_forest(4, n_seg=8), 1, FP32),
+                       (W.periodic_cube_forest(2, n_seg=8), 3, FP32),
+                       (W.jitter3d_forest(seed=0), 2, FP32_COMP),
+                       (W.periodic_cube_forest(2, n_seg=8), 2, FP64)]:
+        f = Forest.from_workload(w, p=p, precision=prec)
+        f.project(W.smooth_state)
+        f.rk_step()
+        actual = f.device_bytes
+        est = footprint_bytes(w, p, prec)
+        f.close()
+        assert 0.8 * actual < est < 1.25 * actual, (p, prec, est, actual)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", [FP32, FP32_COMP, FP64])
+def test_step_past_t_end_is_identity(prec):
+    from paper_2502_12620_gb300 import Forest
+    f = Forest.from_workload(W.periodic_cube_forest(2, n_seg=4), p=2, precision=prec)
+    f.project(W.smooth_state)
+    t_end = 0.004
+    while f.time < t_end:
+        f.rk_step(t_end)
+    U, n = f.get_state(), f.step_count
+    assert f.time == t_end and n > 0
+    for _ in range(3):
+        assert f.rk_step(t_end, return_dt=True) == 0.0
+    assert np.array_equal(f.get_state(), U) and f.step_count == n and f.time == t_end
+    # the kept CFL minimum lets the march continue past the old end time
+    f.rk_step(2 * t_end)
+    assert f.time > t_end and f.step_count == n + 1 and f.status_word() == 0
+    f.set_time(0.0)
+    assert f.step_count == 0
+    f.close()

@@ -276,6 +276,41 @@ def blast_centre(seed):
 
 
 # --------------------------------------------------------------------------
+# a stream of independent solves (continuous batching)
+# --------------------------------------------------------------------------
+def serving_mix(n_requests, *, rate=20.0, seed=0, blocks=(64, 8192), degrees=(1, 2, 3),
+                t_end=(0.05, 0.5), t_scale=1.0, n_seg=8):
+    """Requests arriving by a Poisson process of `rate` per second.  Each is a
+    3D periodic unit cube of B^3 single-level roots, with the block count
+    drawn log-uniformly in `blocks` and rounded to the nearest cube; the
+    initial condition is a blast or the extruded vortex with probability 1/2
+    each; p is uniform over `degrees`; t_end is uniform in `t_end` times
+    `t_scale`.  Returns plain dicts (no forest is built here)."""
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+    out = []
+    for i in range(n_requests):
+        nb = math.exp(rng.uniform(math.log(blocks[0]), math.log(blocks[1])))
+        B = max(1, int(round(nb ** (1.0 / 3.0))))
+        kind = "blast" if rng.uniform() < 0.5 else "vortex"
+        p = int(degrees[rng.integers(len(degrees))])
+        te = float(rng.uniform(*t_end)) * t_scale
+        centre = rng.uniform(0.4, 0.6, size=3)
+        out.append(dict(rid=i, arrival=float(arrivals[i]), B=B, n_seg=n_seg, p=p, t_end=te,
+                        kind=kind, centre=centre))
+    return out
+
+
+def serving_initial(req):
+    """Initial-condition formula of a serving_mix request: the blast with its
+    interface one cell wide, or the vortex scaled to the unit cube."""
+    if req["kind"] == "blast":
+        width = 1.0 / (req["B"] * req["n_seg"])
+        return lambda x: blast(x, req["centre"], width=width)
+    return lambda x: isentropic_vortex(x, scale=10.0, centre=(5.0, 5.0))
+
+
+# --------------------------------------------------------------------------
 # random valid modal states (for element-wise parity tests)
 # --------------------------------------------------------------------------
 def random_modal_state(n_leaves, d, n_seg, p, seed=0, amp=0.05):
