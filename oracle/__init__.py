@@ -38,6 +38,11 @@ design notes of the repository):
   R6 combine operator C: J-weighted L2 projection whose integrals use each
      child cell's own Gauss rule (so restriction(prolongation(u)) = u).
   R7 rotation: signed axis permutation derived from matching corner nodes.
+  R15 level jumps: the paper's guard scheme (Sec. 3.5) is the default; the
+     paper claims conservation for it (Sec. 6), which does not hold when
+     the two sides evaluate the flux from different data.  The "mortar"
+     option restores it: the fine side's fluxes at its face points are also
+     the coarse side's, integrated against the coarse test functions.
 
 Parity pins: every function here is pinned by the not-gpu tests in
 ``tests/test_oracle_*.py`` against closed forms, invariants and independent

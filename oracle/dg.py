@@ -138,11 +138,16 @@ def _combine(ops, K_children, corners_children):
 class Solver:
     """One forest + degree p: guard fill, residual, SSP-RK3, CFL, totals."""
 
-    def __init__(self, forest, p, gamma=GAMMA, cfl=0.1):
+    def __init__(self, forest, p, gamma=GAMMA, cfl=0.1, nonconforming="paper"):
+        """nonconforming: "paper" (the guard scheme of Sec. 3.5 on both sides
+        of a level jump) or "mortar" (reading R15: the coarse side takes the
+        fine side's fluxes, integrated against its own test functions)."""
+        assert nonconforming in ("paper", "mortar")
         self.F = forest
         self.d, self.n, self.p = forest.d, forest.n, p
         self.ops = Ops(self.d, p)
         self.gamma, self.cfl = gamma, cfl
+        self.nonconforming = nonconforming
         self.nv = self.d + 2
         self._rot_cache = {}
         self.refresh()
@@ -166,6 +171,49 @@ class Solver:
                 _, Jf, Jaf = jacobian(C, xf)
                 per.append(Jaf)
             self.geo_face.append(per)
+        self.kinds = [[self._face_kind(li, f) for f in range(2 * self.d)]
+                      for li in range(len(self.leaves))]
+
+    def _face_kind(self, li, f):
+        """SAME, COARSER, FINER or BOUNDARY for face f of leaf li."""
+        r, lev, pos = self.leaves[li]
+        nb = self.F.neighbour_coords(r, lev, pos, f)
+        if nb is None:
+            return BOUNDARY
+        r2, q, _, _ = nb
+        if (r2, lev, q) in self.F.tree:
+            return SAME if self.F.is_leaf((r2, lev, q)) else FINER
+        return COARSER
+
+    def _coarse_points(self, li, f):
+        """Face f of leaf li has a coarser neighbour (the geometry of Eq. (16)):
+        the coarse leaf index and, per guard index t, the coarse cell across my
+        face cell t and the coarse cell's reference coordinates of my face
+        Gauss points (the fine face is half of the coarse face per tangential
+        axis; my axis a maps to the coarse axis pi[a] with sign sigma[a])."""
+        F, ops, d, n = self.F, self.ops, self.d, self.n
+        r, lev, pos = self.leaves[li]
+        a, s = divmod(f, 2)
+        tang = [t for t in range(d) if t != a]
+        qbits = [x & 1 for x in pos]
+        r2, Q, (pi, sigma), f2 = F.neighbour_coords(r, lev - 1, tuple(x >> 1 for x in pos), f)
+        b2, s2 = divmod(f2, 2)
+        xf = ops.faces[f][0]
+        out = []
+        for t in range(n ** (d - 1)):
+            g = [0] * d
+            for j, tt in enumerate(tang):
+                g[tt] = (t // n ** j) % n
+            h = [0] * d
+            xc = np.zeros((len(xf), d))
+            for tt in tang:
+                G = qbits[tt] * n + g[tt]
+                h[pi[tt]] = (G >> 1) if sigma[tt] > 0 else n - 1 - (G >> 1)
+                xc[:, pi[tt]] = sigma[tt] * 0.5 * (xf[:, tt] + 2 * (G & 1) - 1)
+            h[b2] = 0 if s2 == 0 else n - 1
+            xc[:, b2] = -1.0 if s2 == 0 else 1.0
+            out.append((_cidx(h, n), xc))
+        return self.index[(r2, lev - 1, Q)], out
 
     def _build_nbr_maps(self):
         """Per face: the cell across it inside the block, or the guard index."""
@@ -284,13 +332,22 @@ class Solver:
     # -------------------------------------------------------------- residual
     def residual(self, U, G=None, leaves=None):
         """L(U) = M^{-1} R per cell (Eqs. (3)-(4)); guard cells from Sec. 3.5.
-        ``leaves`` restricts the evaluation to a subset (others stay zero)."""
+        ``leaves`` restricts the evaluation to a subset (others stay zero).
+
+        Mortar mode (reading R15): a face with finer neighbours gets no flux
+        of its own; instead every fine face point's flux F_h (the fine side's
+        Lax-Friedrichs flux, out of the fine cell, per fine reference area)
+        enters the coarse cell's residual as + sum_k w_k phi_m(xi_c(x_k)) F_h,k
+        -- the same surface integral, parametrised by the fine face."""
         ops, d, n, nv = self.ops, self.d, self.n, self.nv
+        mortar = self.nonconforming == "mortar"
+        todo = range(len(self.leaves)) if (leaves is None or mortar) else leaves
         if G is None:
-            G = self.fill_guardcells(U, leaves)
+            G = self.fill_guardcells(U, None if mortar else leaves)
         out = np.zeros_like(U)
         nc = n ** d
-        for li in (range(len(self.leaves)) if leaves is None else leaves):
+        R_all, extra = {}, {}
+        for li in todo:
             K = np.transpose(U[li], (2, 0, 1))                      # (nc, nv, M)
             J, Ja = self.geo_vol[li]
             uq = np.einsum("qm,cvm->cqv", ops.Phi, K)
@@ -310,7 +367,20 @@ class Solver:
                 dS = np.linalg.norm(area, axis=-1)
                 nhat = area / dS[..., None]
                 Fh = lax_friedrichs(uL, uR, nhat, self.gamma) * dS[..., None]
+                if mortar and self.kinds[li][f] == FINER:
+                    Fh[~inside] = 0.0  # the fine side's fluxes arrive below
                 R -= np.einsum("f,fm,cfv->cvm", wf, Pf, Fh, optimize=True)
+                if mortar and self.kinds[li][f] == COARSER:
+                    ci, pts = self._coarse_points(li, f)
+                    Rc = extra.setdefault(ci, np.zeros((nc, nv, ops.M)))
+                    for c in np.nonzero(~inside)[0]:
+                        hc, xc = pts[src[c]]
+                        Pc = B.eval_basis(xc, ops.N)
+                        Rc[hc] += np.einsum("f,fm,fv->vm", wf, Pc, Fh[c])
+            R_all[li] = R
+        for li in (range(len(self.leaves)) if leaves is None else leaves):
+            R = R_all[li] + extra[li] if li in extra else R_all[li]
+            J, _ = self.geo_vol[li]
             Mc = np.einsum("q,cq,qm,qn->cmn", ops.wq, J, ops.Phi, ops.Phi, optimize=True)
             Kdot = np.linalg.solve(Mc[:, None], R[..., None])[..., 0]
             out[li] = np.transpose(Kdot, (1, 2, 0))

@@ -367,6 +367,27 @@ def smooth_x_state(x, Lx=2.0):
     return prim_to_cons(rho, vel, pr)
 
 
+ADVECT_VEL = (0.3, -0.2, 0.1)
+
+
+def advected_polynomial(x, p):
+    """rho a polynomial of total degree p in x, constant velocity ADVECT_VEL
+    and constant pressure 1 (a state whose Euler flux is a polynomial of
+    degree p)."""
+    x = np.asarray(x, float)
+    d = x.shape[-1]
+    X = [x[..., a] for a in range(d)]
+    rho = 1.0 + 0.1 * X[0] + 0.2 * X[1] - (0.15 * X[2] if d == 3 else 0.0)
+    if p >= 2:
+        rho = rho + 0.05 * X[0] * X[1] - 0.04 * X[1] ** 2
+    if p >= 3:
+        rho = rho + 0.02 * X[0] ** 3 - 0.03 * X[0] * X[1] * X[-1]
+    if p == 0:
+        rho = np.full(x.shape[:-1], 1.2)
+    vel = np.broadcast_to(np.array(ADVECT_VEL[:d]), x.shape[:-1] + (d,))
+    return prim_to_cons(rho, vel, np.ones(x.shape[:-1]))
+
+
 def smooth_state(x, extent=1.0):
     """A smooth periodic state varying along every axis."""
     x = np.asarray(x, float)
