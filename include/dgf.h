@@ -73,6 +73,17 @@ typedef int32_t dgf_status;
  * FP32.  The state, residual and guard cells at this ABI are double. */
 #define DGF_FP32_COMP 2
 
+/* Fluxes across a level jump.  DGF_NC_PAPER: each side evaluates the
+ * Lax-Friedrichs flux at its own face points from its guard cells (Sec. 3.5,
+ * Eqs. (16)-(17)); the totals then drift at level jumps, although Sec. 6
+ * claims conservation.  DGF_NC_MORTAR: the fine side's fluxes (computed with
+ * the prolonged coarse trace of Eq. (16)) are also the coarse side's: the
+ * coarse face flux at its point j is (1/w_j) sum_k w_k l_j(xi(x_k)) F_k over
+ * the fine sub-face points, which conserves the totals to round-off.  Not a
+ * paper option: it is the repair of the conservation claim. */
+#define DGF_NC_PAPER 0
+#define DGF_NC_MORTAR 1
+
 typedef struct dgf_forest dgf_forest;
 
 /* Forest description (Sec. 3.1-3.3).  Root blocks are hexahedra (3D) or
@@ -88,6 +99,8 @@ typedef struct {
   int32_t device;     /* CUDA device ordinal; -1 = host-only forest that
                          answers topology/geometry queries only             */
   int32_t n_periodic; /* number of periodic translations, 0..3             */
+  int32_t nonconforming; /* level jumps: DGF_NC_PAPER or DGF_NC_MORTAR       */
+  int32_t reserved;   /* must be 0                                          */
   double gamma;       /* ideal-gas ratio of Eq. (23), e.g. 1.4              */
   double cfl;         /* CFL number of the time increment (Sec. 4.3)        */
   double periodic[9]; /* n_periodic vectors of dim components, packed       */

@@ -18,6 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdgf.so")
 
 FP64, FP32, FP32_COMP = 0, 1, 2
+NC_PAPER, NC_MORTAR = 0, 1  # fluxes across level jumps (include/dgf.h)
 SAME, COARSER, FINER, BOUNDARY = 0, 1, 2, 3
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE",
           -5: "ETIMEOUT", -6: "EBALANCE", -7: "ESTATE", -8: "EUNSUPPORTED"}
@@ -32,7 +33,8 @@ class DgfError(RuntimeError):
 class _Desc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("n_seg", ctypes.c_int32), ("p", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("n_periodic", ctypes.c_int32), ("gamma", ctypes.c_double),
+                ("n_periodic", ctypes.c_int32), ("nonconforming", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("gamma", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("periodic", ctypes.c_double * 9),
                 ("n_nodes", ctypes.c_int64), ("nodes", ctypes.POINTER(ctypes.c_double)),
                 ("n_roots", ctypes.c_int64), ("root_corners", ctypes.POINTER(ctypes.c_int64)),
@@ -140,7 +142,7 @@ class Forest:
     """A block forest with its DG state on one GPU (or host-only, device=-1)."""
 
     def __init__(self, dim, n_seg, p, nodes, root_corners, root_cell_nodes=None, periodic=(),
-                 precision=FP64, device=0, gamma=1.4, cfl=0.1, torch_memory=True):
+                 precision=FP64, device=0, gamma=1.4, cfl=0.1, torch_memory=True, nonconforming="paper"):
         L = lib()
         self.dim, self.n_seg, self.p = int(dim), int(n_seg), int(p)
         self.precision = (FP32 if precision in (FP32, "fp32", "f32") else
@@ -162,6 +164,10 @@ class Forest:
         for i, t in enumerate(per):
             for j in range(self.dim):
                 d.periodic[i * self.dim + j] = float(t[j])
+        if nonconforming not in ("paper", "mortar"):
+            raise ValueError("nonconforming must be 'paper' or 'mortar'")
+        self.nonconforming = nonconforming
+        d.nonconforming = NC_MORTAR if nonconforming == "mortar" else NC_PAPER
         d.gamma, d.cfl = float(gamma), float(cfl)
         d.n_nodes = nodes.shape[0]
         d.nodes = nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -349,4 +355,4 @@ class Forest:
         return {"dt": (ms[0], int(cnt[0])), "guard": (ms[1], int(cnt[1])), "stage": (ms[2], int(cnt[2]))}
 
 
-__all__ = ["Forest", "DgfError", "lib", "FP64", "FP32", "FP32_COMP", "LIB_PATH"]
+__all__ = ["Forest", "DgfError", "lib", "FP64", "FP32", "FP32_COMP", "NC_PAPER", "NC_MORTAR", "LIB_PATH"]

@@ -218,6 +218,7 @@ struct StageArgs {
   const double* __restrict__ U64;  // compensated form: u^n in FP64 (stage input base)
   const float* __restrict__ Din;   // compensated form: delta^(k), null at stage 1
   double* __restrict__ U64out;     // compensated form, last stage: u^(n+1) in FP64
+  const unsigned char* __restrict__ fluxmask;  // [b] bit f: gtr holds face f's flux (mortar), or null
   Tab<P + 1, Real> T;
 };
 
@@ -256,6 +257,15 @@ struct GuardArgs {
   const Real* __restrict__ ctr;    // [op][2^D M][NFP]: the same operator followed by my face trace
   const int* __restrict__ fine_list;  // [nfine] leaf * 2D + face of every finer-neighbour face
   int nfine;
+  // mortar mode (reading R15)
+  const Real* __restrict__ geo;       // [b][g][cell] trilinear coefficients
+  Real gamma;
+  const int* __restrict__ mfine;      // [nmf] leaf * 2D + face of every face with a coarser neighbour
+  int nmf;
+  const int* __restrict__ mcoarse;    // [nmc] leaf * 2D + face of every face with finer neighbours
+  int nmc;
+  const Real* __restrict__ mw;        // [nmc][NFP][2^(D-1) NFP] coarse point <- fine sub-face points
+  const long long* __restrict__ msrc; // [nmc][nt][2^(D-1)] gtr offset of (fine leaf, face, v 0, point 0, t)
   Tab<P + 1, Real> T;
 };
 
@@ -401,7 +411,7 @@ __device__ __forceinline__ int face_point_index(int ax, int fp, int qn) {
 // (each face once); x volume + lift; y volume + lift (and the halo trace of
 // the next layer); z volume + z faces (carried between layers) and 1/J;
 // SSP-RK combination point by point, with the CFL minimum on the last stage.
-template <int D, int P, int NS, typename Real, bool COMP = false>
+template <int D, int P, int NS, typename Real, bool COMP = false, bool MORTAR = false>
 __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB)
     k_stage(const StageArgs<D, P, Real> A) {
   constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
@@ -469,6 +479,7 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
     const Real* __restrict__ Gb = A.geo + (size_t)b * NG * nc;
     const Real* __restrict__ Tb = A.gtr + (size_t)b * 2 * D * NV * NFP * nt;
     const bool aff = A.affine[b] != 0;
+    const int fmask = MORTAR ? A.fluxmask[b] : 0;  // faces whose flux is given (mortar mode)
     __syncthreads();  // previous item is done with the shared buffers
     if (aff && tid < D * D + 1) sam[tid] = A.ameta[(size_t)b * (D * D + 1) + tid];
 
@@ -528,6 +539,11 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
           __syncthreads();
           for (int w = tid; w < NCL * NFP; w += nthr) {
             const int c = w % NCL, fp = w / NCL;
+            if (k0 == 0 && (fmask & 16)) {
+#pragma unroll
+              for (int v = 0; v < NV; ++v) FZ(v, fp, c) = TB(v, fp, c);  // the z- face flux itself
+              continue;
+            }
             Real uL[NV], uR[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
@@ -571,6 +587,11 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
           const int j = (ww / (n + 1)) % n;
           const int fp = ww / ((n + 1) * n);
           const int cl = (fi - 1) + n * j, cr = fi + n * j;
+          if ((fi == 0 && (fmask & 1)) || (fi == n && (fmask & 2))) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) FX(v, fp, j, fi) = GTR(fi == 0 ? 0 : 1, v, fp, D == 3 ? j + n * k : j);
+            continue;
+          }
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             if (fi == 0) {
@@ -609,6 +630,11 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
           const int fp = ww / ((n + 1) * n);  // qx + N qz
           const int qx = fp % N, qz = fp / N;
           const int cl = i + n * (fi - 1), cr = i + n * fi;
+          if ((fi == 0 && (fmask & 4)) || (fi == n && (fmask & 8))) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) FY(v, fp, fi, i) = GTR(fi == 0 ? 2 : 3, v, fp, D == 3 ? i + n * k : i);
+            continue;
+          }
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             if (fi == 0) {
@@ -788,13 +814,18 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
             uL[v] = s;
             uR[v] = TB(v, fp, c);
           }
-          if (aff) {
+          if (k == n - 1 && (fmask & 32)) {
 #pragma unroll
-            for (int jj = 0; jj < 3; ++jj) Ja[jj] = sam[6 + jj];
+            for (int v = 0; v < NV; ++v) Fh[v] = uR[v];  // the z+ face flux itself
           } else {
-            lg.at(Real(1), Ja);
+            if (aff) {
+#pragma unroll
+              for (int jj = 0; jj < 3; ++jj) Ja[jj] = sam[6 + jj];
+            } else {
+              lg.at(Real(1), Ja);
+            }
+            lf_flux<3, Real>(uL, uR, Ja, gamma, Fh);
           }
-          lf_flux<3, Real>(uL, uR, Ja, gamma, Fh);
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             const Real fbot = FZ(v, fp, c);
@@ -1373,6 +1404,91 @@ __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, R
     const int v = pr / NFP, fp = pr % NFP;
     A.out[((((size_t)b * 2 * D + f) * NV + v) * NFP + fp) * nt + t] = acc;
   }
+}
+
+// ============================================================ mortar mode
+// Reading R15.  Fine side: at every face point of a face with a coarser
+// neighbour, the Lax-Friedrichs flux along +xi_a (Eq. (5), reading R3) from
+// my own trace and the prolonged coarse trace already in the guard-trace
+// buffer, with my face metric; it overwrites that trace, and the stage kernel
+// takes it as the face flux.  One thread per (face, guard cell, face point).
+template <int D, int P, typename Real, bool COMP = false>
+__global__ void __launch_bounds__(128) k_mortar_fine(const GuardArgs<D, P, Real> A) {
+  const StateIn<Real, COMP> S{A.U, A.U64, A.Din};
+  constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
+  constexpr int NG = ((1 << D) - 1) * D;
+  const int n = A.n;
+  const int nt = D == 3 ? n * n : n;
+  const int nc = D == 3 ? n * n * n : n * n;
+  const auto& T = A.T;
+  const size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= (size_t)A.nmf * nt * NFP) return;
+  const int fp = (int)(w % NFP);
+  const int t = (int)((w / NFP) % nt);
+  const int bf = A.mfine[w / ((size_t)NFP * nt)];
+  const int b = bf / (2 * D), f = bf % (2 * D);
+  const int a = f >> 1, s = f & 1;
+  int h[3] = {0, 0, 0};
+  Real xi[D];
+  {
+    int j = 0;
+    for (int ax = 0; ax < D; ++ax) {
+      if (ax == a) continue;
+      h[ax] = j == 0 ? (t % n) : (t / n);
+      xi[ax] = T.x[j == 0 ? fp % N : fp / N];
+      ++j;
+    }
+  }
+  h[a] = s ? n - 1 : 0;
+  xi[a] = s ? Real(1) : Real(-1);
+  int cell = 0;
+  for (int ax = 0, st = 1; ax < D; ++ax, st *= n) cell += h[ax] * st;
+  Real own[NV], gst[NV], Ja[D], Fh[NV];
+  Real* slot = A.out + ((size_t)bf * NV * NFP + fp) * nt + t;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const size_t src0 = ((size_t)b * NV + v) * Q * nc + cell;
+    Real acc = Real(0);
+#pragma unroll
+    for (int qn = 0; qn < N; ++qn)
+      acc += (s ? T.lp[qn] : T.lm[qn]) * S(src0 + (size_t)face_point_index<D, N>(a, fp, qn) * nc);
+    own[v] = acc;
+    gst[v] = slot[(size_t)v * NFP * nt];
+  }
+  point_row<D, Real>(A.geo + (size_t)b * NG * nc + cell, nc, xi, a, Ja);
+  if (s) lf_flux<D, Real>(own, gst, Ja, A.gamma, Fh);
+  else lf_flux<D, Real>(gst, own, Ja, A.gamma, Fh);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) slot[(size_t)v * NFP * nt] = Fh[v];
+}
+
+// Coarse side: the flux at my face point j is the fine sub-face fluxes
+// integrated against my face test function l_j and divided by its weight,
+// (1/w_j) sum_sub sum_k w_k l_j(xi(x_k)) F_k, rotated into my frame with the
+// orientation's sign folded into the precomputed weights.  One thread per
+// (face, guard cell, variable, face point).
+template <int D, int P, typename Real>
+__global__ void __launch_bounds__(128) k_mortar_coarse(const GuardArgs<D, P, Real> A) {
+  constexpr int N = P + 1, NV = D + 2, NFP = ipow(N, D - 1);
+  constexpr int NSUB = 1 << (D - 1);
+  const int n = A.n;
+  const int nt = D == 3 ? n * n : n;
+  const size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= (size_t)A.nmc * nt * NV * NFP) return;
+  const int j = (int)(w % NFP);
+  const int v = (int)((w / NFP) % NV);
+  const int t = (int)((w / ((size_t)NFP * NV)) % nt);
+  const int i = (int)(w / ((size_t)NFP * NV * nt));
+  const Real* __restrict__ wt = A.mw + ((size_t)i * NFP + j) * NSUB * NFP;
+  const long long* __restrict__ src = A.msrc + ((size_t)i * nt + t) * NSUB;
+  Real acc = Real(0);
+#pragma unroll
+  for (int e = 0; e < NSUB; ++e) {
+    const Real* __restrict__ F = A.out + src[e] + (size_t)v * NFP * nt;
+#pragma unroll
+    for (int k = 0; k < NFP; ++k) acc += wt[e * NFP + k] * F[(size_t)k * nt];
+  }
+  A.out[(((size_t)A.mcoarse[i] * NV + v) * NFP + j) * nt + t] = acc;
 }
 
 // ============================================================ conversions

@@ -132,6 +132,10 @@ struct dgf_forest {
   Buf U[3], geo, geo64, hcell, gtr, gmod, cop, ctr, kind, nbr, orient, qbits, copoff, part, scal, tot,
       dtout, nodal, fine, affine, ameta;
   int nfine = 0;
+  // mortar treatment of level jumps (reading R15)
+  bool mortar = false;
+  Buf fluxmask, mfine, mcoarse, mw, msrc;
+  int nmf = 0, nmc = 0;
   int slots = 0;
   bool have_state = false;
   bool graph_valid = false;
@@ -476,6 +480,83 @@ dgf_status build_device(dgf_forest* f) {
   });
   if (singular) return fail(DGF_EINVAL, "singular combine mass matrix");
 
+  // mortar tables (reading R15): faces with a coarser neighbour take their
+  // flux from the fine-side pass; faces with finer neighbours integrate those
+  // fluxes against their own face test functions
+  std::vector<unsigned char> fluxmask(L, 0);
+  std::vector<int> mfine, mcoarse;
+  std::vector<double> mw;
+  std::vector<long long> msrc;
+  if (f->mortar) {
+    const int NSUB = 1 << (d - 1), NFPm = f->NFP;
+    for (int64_t i = 0; i < L; ++i)
+      for (int fc = 0; fc < nf; ++fc) {
+        const int k = kind[i * nf + fc];
+        if (k == kCoarser) mfine.push_back((int)(i * nf + fc));
+        if (k == kFiner) mcoarse.push_back((int)(i * nf + fc));
+        if (k == kCoarser || k == kFiner) fluxmask[i] |= (unsigned char)(1 << fc);
+      }
+    mw.assign(mcoarse.size() * NFPm * NSUB * NFPm, 0.0);
+    msrc.assign(mcoarse.size() * nt * NSUB, 0);
+    for (size_t mi = 0; mi < mcoarse.size(); ++mi) {
+      const int64_t i = mcoarse[mi] / nf;
+      const int fc = mcoarse[mi] % nf;
+      const Orient o = orient_from_code(T.orient[i * nf + fc], d);
+      const int a = fc >> 1, s = fc & 1;
+      const int b2 = o.pi[a];
+      const int s2 = o.sg[a] > 0 ? 1 - s : s;
+      const int f2 = 2 * b2 + s2;
+      const double sgn = -(s ? 1.0 : -1.0) * (s2 ? 1.0 : -1.0);
+      int mt[2] = {0, 0}, ut[2] = {0, 0}, nmt = 0, nut = 0;  // my / the neighbour's tangential axes
+      for (int ax = 0; ax < d; ++ax) {
+        if (ax != a) mt[nmt++] = ax;
+        if (ax != b2) ut[nut++] = ax;
+      }
+      // weights: my point j <- sub-face esub (bits over ut), its point k (digits over ut)
+      for (int j = 0; j < NFPm; ++j)
+        for (int es = 0; es < NSUB; ++es)
+          for (int k = 0; k < NFPm; ++k) {
+            int jd[3] = {0, 0, 0}, kd[3] = {0, 0, 0}, ed[3] = {0, 0, 0};
+            for (int q = 0, rj = j, rk = k; q < d - 1; ++q, rj /= N, rk /= N) {
+              jd[mt[q]] = rj % N;
+              kd[ut[q]] = rk % N;
+              ed[ut[q]] = (es >> q) & 1;
+            }
+            double wgt = sgn;
+            for (int q = 0; q < d - 1; ++q) {
+              const int ax = mt[q], u = o.pi[ax];
+              const double xi = o.sg[ax] * 0.5 * (B.x[kd[u]] + 2.0 * ed[u] - 1.0);
+              wgt *= B.w[kd[u]] * B.lagrange(jd[ax], xi) / B.w[jd[ax]];
+            }
+            mw[((mi * NFPm + j) * NSUB + es) * NFPm + k] = wgt;
+          }
+      // sources: per guard cell t, the fine leaf and its guard index per sub-face
+      for (int t = 0; t < nt; ++t) {
+        int g[3] = {0, 0, 0}, h[3] = {0, 0, 0}, sub = 0;
+        for (int q = 0; q < d - 1; ++q) g[mt[q]] = q == 0 ? t % n : t / n;
+        for (int q = 0; q < d - 1; ++q) {
+          const int ax = mt[q];
+          h[o.pi[ax]] = o.sg[ax] > 0 ? g[ax] : n - 1 - g[ax];
+          if (g[ax] >= n / 2) sub |= 1 << q;
+        }
+        h[b2] = s2 == 0 ? 0 : n - 1;
+        const int64_t fine = T.nbr[(i * nf + fc) * 4 + sub];
+        for (int es = 0; es < NSUB; ++es) {
+          int tf = 0;
+          for (int q = 0, st = 1; q < d - 1; ++q, st *= n) {
+            const int u = ut[q];
+            const int H = 2 * h[u] + ((es >> q) & 1);
+            tf += (H - (2 * h[u] / n) * n) * st;
+          }
+          msrc[((size_t)mi * nt + t) * NSUB + es] =
+              ((long long)fine * nf + f2) * f->nv * NFPm * nt + tf;
+        }
+      }
+    }
+  }
+  f->nmf = (int)mfine.size();
+  f->nmc = (int)mcoarse.size();
+
   if (f->device < 0) return DGF_OK;
   DeviceGuard dg(f->device);
   dgf_status st;
@@ -484,12 +565,17 @@ dgf_status build_device(dgf_forest* f) {
       (st = upload(f, f->fine, fine_list)))
     return st;
   if ((st = upload(f, f->affine, affine)) || (st = upload(f, f->hcell64, hcell))) return st;
+  if (f->mortar && ((st = upload(f, f->fluxmask, fluxmask)) || (st = upload(f, f->mfine, mfine)) ||
+                    (st = upload(f, f->mcoarse, mcoarse)) || (st = upload(f, f->msrc, msrc))))
+    return st;
   if (f->precision == DGF_FP64) {
     if ((st = upload(f, f->geo, geo64)) || (st = upload(f, f->hcell, hcell)) || (st = upload(f, f->cop, cop)) ||
         (st = upload(f, f->ctr, ctr)) ||
         (st = upload(f, f->ameta, ameta)))
       return st;
+    if (f->mortar && (st = upload(f, f->mw, mw))) return st;
   } else {
+    if (f->mortar && (st = upload(f, f->mw, convert<float>(mw)))) return st;
     if ((st = upload(f, f->geo, convert<float>(geo64))) || (st = upload(f, f->hcell, convert<float>(hcell))) ||
         (st = upload(f, f->cop, convert<float>(cop))) || (st = upload(f, f->ctr, convert<float>(ctr))) ||
         (st = upload(f, f->ameta, convert<float>(ameta))))
@@ -576,6 +662,7 @@ RtStage stage_args(dgf_forest* f, int src, int dst, double ca, double cb, int mo
     r.Din = src == 0 ? nullptr : (const float*)f->U[src].ptr;
     r.U64out = (double*)f->U64[1 - f->cur].ptr;
   }
+  if (f->mortar) r.fluxmask = (const unsigned char*)f->fluxmask.ptr;
   r.T = f->tab;
   return r;
 }
@@ -597,6 +684,17 @@ RtGuard guard_args(dgf_forest* f, int src, void* out, int mode) {
   r.ctr = f->ctr.ptr;
   r.fine_list = (const int*)f->fine.ptr;
   r.nfine = f->nfine;
+  r.geo = f->geo.ptr;
+  r.gamma = f->gamma;
+  if (f->mortar && mode == 1) {
+    r.nfine = 0;  // the coarse side's flux comes from the mortar passes
+    r.mfine = (const int*)f->mfine.ptr;
+    r.nmf = f->nmf;
+    r.mcoarse = (const int*)f->mcoarse.ptr;
+    r.nmc = f->nmc;
+    r.mw = f->mw.ptr;
+    r.msrc = (const long long*)f->msrc.ptr;
+  }
   if (f->comp) {
     r.comp = 1;
     r.U64 = (const double*)f->U64[f->cur].ptr;
@@ -797,6 +895,8 @@ dgf_status dgf_forest_create(const dgf_forest_desc* desc, const dgf_allocator* a
   if (desc->precision != DGF_FP64 && desc->precision != DGF_FP32 && desc->precision != DGF_FP32_COMP)
     return fail(DGF_EINVAL, "bad precision");
   if (!(desc->gamma > 1.0) || !(desc->cfl > 0.0)) return fail(DGF_EINVAL, "gamma must be > 1 and cfl > 0");
+  if ((desc->nonconforming != DGF_NC_PAPER && desc->nonconforming != DGF_NC_MORTAR) || desc->reserved != 0)
+    return fail(DGF_EINVAL, "nonconforming must be DGF_NC_PAPER or DGF_NC_MORTAR (reserved 0)");
   dgf_forest* f = new (std::nothrow) dgf_forest();
   if (!f) return fail(DGF_ENOMEM, "host allocation failed");
   if (!f->host.init(desc->dim, desc->n_seg, desc->p, desc->n_nodes, desc->nodes, desc->n_roots,
@@ -812,6 +912,7 @@ dgf_status dgf_forest_create(const dgf_forest_desc* desc, const dgf_allocator* a
   f->esize = desc->precision == DGF_FP64 ? 8 : 4;
   f->sesize = desc->precision == DGF_FP32 ? 4 : 8;
   f->comp = desc->precision == DGF_FP32_COMP;
+  f->mortar = desc->nonconforming == DGF_NC_MORTAR;
   f->d = desc->dim;
   f->n = desc->n_seg;
   f->p = desc->p;
@@ -902,7 +1003,8 @@ dgf_status dgf_forest_destroy(dgf_forest* f) {
     dgf_forest::Buf* bufs[] = {&f->U[0], &f->U[1], &f->U[2], &f->geo, &f->geo64, &f->hcell, &f->gtr,
                                &f->gmod, &f->cop, &f->ctr, &f->kind, &f->nbr, &f->orient, &f->qbits, &f->copoff,
                                &f->part, &f->scal, &f->tot, &f->dtout, &f->nodal, &f->fine, &f->affine, &f->ameta,
-                               &f->U64[0], &f->U64[1], &f->hcell64, &f->gmod64};
+                               &f->U64[0], &f->U64[1], &f->hcell64, &f->gmod64, &f->fluxmask,
+                               &f->mfine, &f->mcoarse, &f->mw, &f->msrc};
     for (auto* b : bufs) dev_free(f, *b);
     if (f->own_stream && f->stream) cudaStreamDestroy(f->stream);
   }

@@ -30,6 +30,49 @@ static Tab<N, Real> make_tab(const RtTables& r) {
   return t;
 }
 
+// The mortar variants of the stage kernel (faces whose flux the mortar passes
+// give) live in their own translation units (k_<dim>_<prec>_mortar.cu).
+template <int D, int P, int NS, typename Real>
+cudaError_t stage_mortar_launch(const StageArgs<D, P, Real>& a, int grid, size_t smem, int comp, cudaStream_t s);
+template <int D, int P, int NS, typename Real>
+bool stage_mortar_prepare(size_t smem);
+
+#define DGF_INSTANTIATE_MORTAR_NS(DIM, P, NS, REAL)                                                   \
+  template <>                                                                                         \
+  cudaError_t stage_mortar_launch<DIM, P, NS, REAL>(const StageArgs<DIM, P, REAL>& a, int grid,       \
+                                                    size_t smem, int comp, cudaStream_t s) {          \
+    if constexpr (std::is_same<REAL, float>::value) {                                                 \
+      if (comp) {                                                                                     \
+        k_stage<DIM, P, NS, REAL, true, true><<<grid, StageCfg<P, REAL>::NT, smem, s>>>(a);           \
+        return cudaGetLastError();                                                                    \
+      }                                                                                               \
+    }                                                                                                 \
+    if (comp) return cudaErrorInvalidValue;                                                           \
+    k_stage<DIM, P, NS, REAL, false, true><<<grid, StageCfg<P, REAL>::NT, smem, s>>>(a);              \
+    return cudaGetLastError();                                                                        \
+  }                                                                                                   \
+  template <>                                                                                         \
+  bool stage_mortar_prepare<DIM, P, NS, REAL>(size_t smem) {                                          \
+    if (cudaFuncSetAttribute(k_stage<DIM, P, NS, REAL, false, true>,                                  \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)  \
+      return false;                                                                                   \
+    if constexpr (std::is_same<REAL, float>::value) {                                                 \
+      if (cudaFuncSetAttribute(k_stage<DIM, P, NS, REAL, true, true>,                                 \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) \
+        return false;                                                                                 \
+    }                                                                                                 \
+    return true;                                                                                      \
+  }
+#define DGF_INSTANTIATE_MORTAR_P(DIM, P, REAL) \
+  DGF_INSTANTIATE_MORTAR_NS(DIM, P, 2, REAL)   \
+  DGF_INSTANTIATE_MORTAR_NS(DIM, P, 4, REAL)   \
+  DGF_INSTANTIATE_MORTAR_NS(DIM, P, 8, REAL)
+#define DGF_INSTANTIATE_MORTAR(DIM, REAL) \
+  DGF_INSTANTIATE_MORTAR_P(DIM, 0, REAL)  \
+  DGF_INSTANTIATE_MORTAR_P(DIM, 1, REAL)  \
+  DGF_INSTANTIATE_MORTAR_P(DIM, 2, REAL)  \
+  DGF_INSTANTIATE_MORTAR_P(DIM, 3, REAL)
+
 template <int D, int P, int NS, typename Real>
 static int stage_blocks_per_sm_ns() {
   const size_t smem = stage_smem<D, P, Real>(NS);
@@ -45,6 +88,7 @@ static int stage_blocks_per_sm_ns() {
                              (int)smem) != cudaSuccess)
       return 0;
   }
+  if (!stage_mortar_prepare<D, P, NS, Real>(smem)) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage<D, P, NS, Real>, StageCfg<P, Real>::NT, smem) !=
       cudaSuccess)
@@ -67,6 +111,7 @@ static cudaError_t stage_ns(const StageArgs<D, P, Real>& a, int slots, int comp,
   const size_t smem = stage_smem<D, P, Real>(NS);
   const int items = a.nL * a.nchunks;
   const int grid = items < slots ? items : slots;
+  if (a.fluxmask) return stage_mortar_launch<D, P, NS, Real>(a, grid, smem, comp, s);
   if constexpr (std::is_same<Real, float>::value) {
     if (comp) {
       k_stage<D, P, NS, Real, true><<<grid, StageCfg<P, Real>::NT, smem, s>>>(a);
@@ -108,6 +153,7 @@ static cudaError_t stage_p(const RtStage& r, cudaStream_t s) {
   a.U64 = r.U64;
   a.Din = r.Din;
   a.U64out = r.U64out;
+  a.fluxmask = r.fluxmask;
   a.T = make_tab<P + 1, Real>(r.T);
   if (r.slots <= 0) return cudaErrorInvalidConfiguration;
   switch (r.n) {
@@ -137,22 +183,45 @@ static cudaError_t guard_p(const RtGuard& r, cudaStream_t s) {
   a.ctr = (const Real*)r.ctr;
   a.fine_list = r.fine_list;
   a.nfine = r.nfine;
+  a.geo = (const Real*)r.geo;
+  a.gamma = (Real)r.gamma;
+  a.mfine = r.mfine;
+  a.nmf = r.nmf;
+  a.mcoarse = r.mcoarse;
+  a.nmc = r.nmc;
+  a.mw = (const Real*)r.mw;
+  a.msrc = r.msrc;
   a.T = make_tab<P + 1, Real>(r.T);
   const int nt = D == 3 ? r.n * r.n : r.n;
   if (r.mode == 1) {
-    // time-step path: traces of every face kind in one launch
+    // time-step path: traces of every face kind in one launch (finer faces
+    // by the combine blocks unless the mortar passes replace them)
     constexpr int NTH = 32 << D;
     const size_t items = (size_t)r.nL * 2 * D * (D + 2) * nt;
     const size_t ntb = (items + NTH - 1) / NTH;
     const int nfb = r.nfine * nt;
+    const bool comp = std::is_same<Real, float>::value && r.comp;
     if constexpr (std::is_same<Real, float>::value) {
-      if (r.comp) {
-        k_guard_trace<D, P, Real, true><<<(unsigned)(ntb + nfb), NTH, 0, s>>>(a, nfb);
-        return cudaGetLastError();
-      }
+      if (comp) k_guard_trace<D, P, Real, true><<<(unsigned)(ntb + nfb), NTH, 0, s>>>(a, nfb);
     }
-    k_guard_trace<D, P, Real><<<(unsigned)(ntb + nfb), NTH, 0, s>>>(a, nfb);
-    return cudaGetLastError();
+    if (!comp) k_guard_trace<D, P, Real><<<(unsigned)(ntb + nfb), NTH, 0, s>>>(a, nfb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    constexpr int NFP = ipow(P + 1, D - 1);
+    if (r.nmf > 0) {
+      const size_t tot = (size_t)r.nmf * nt * NFP;
+      if constexpr (std::is_same<Real, float>::value) {
+        if (comp) k_mortar_fine<D, P, Real, true><<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(a);
+      }
+      if (!comp) k_mortar_fine<D, P, Real><<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(a);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (r.nmc > 0) {
+      const size_t tot = (size_t)r.nmc * nt * (D + 2) * NFP;
+      k_mortar_coarse<D, P, Real><<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(a);
+      e = cudaGetLastError();
+    }
+    return e;
   }
   const size_t total = (size_t)r.nL * 2 * D * nt * (D + 2);
   const int th = 128;

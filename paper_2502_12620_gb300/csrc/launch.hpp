@@ -36,6 +36,7 @@ struct RtStage {
   const double* U64;    // compensated: u^n
   const float* Din;     // compensated: delta^(k) or null
   double* U64out;       // compensated, last stage: u^(n+1)
+  const unsigned char* fluxmask;  // mortar mode: per block, faces whose flux is in gtr
   RtTables T;
 };
 
@@ -55,6 +56,15 @@ struct RtGuard {
   const void* ctr;
   const int* fine_list;
   int nfine;
+  // mortar mode: fine-side and coarse-side faces, coarse-side weights/sources
+  const void* geo;
+  double gamma;
+  const int* mfine;
+  int nmf;
+  const int* mcoarse;
+  int nmc;
+  const void* mw;
+  const long long* msrc;
   RtTables T;
 };
 

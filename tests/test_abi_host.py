@@ -146,3 +146,28 @@ def test_bad_descriptions_are_rejected(dgf):
     bad[0, 0] = 99
     with pytest.raises(dgf.DgfError):
         dgf.Forest(2, 2, 2, w["nodes"], bad, device=-1, torch_memory=False)
+
+
+def test_nonconforming_option_is_checked(dgf):
+    import ctypes
+    w = W.rotated_pair_2d()
+    f = dgf.Forest(2, 2, 2, w["nodes"], w["root_corners"], device=-1, torch_memory=False,
+                   nonconforming="mortar")
+    f.close()
+    with pytest.raises(ValueError):
+        dgf.Forest(2, 2, 2, w["nodes"], w["root_corners"], device=-1, torch_memory=False,
+                   nonconforming="other")
+    # the descriptor field itself: only DGF_NC_PAPER / DGF_NC_MORTAR, reserved 0
+    d = dgf._Desc()
+    nodes = np.ascontiguousarray(w["nodes"], np.float64)
+    corners = np.ascontiguousarray(w["root_corners"], np.int64)
+    d.dim, d.n_seg, d.p, d.precision, d.device = 2, 2, 1, dgf.FP64, -1
+    d.gamma, d.cfl = 1.4, 0.1
+    d.n_nodes, d.nodes = nodes.shape[0], nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.n_roots, d.root_corners = corners.shape[0], corners.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    h = ctypes.c_void_p()
+    for nc, rs, want in ((dgf.NC_MORTAR, 0, 0), (2, 0, -1), (dgf.NC_PAPER, 1, -1)):
+        d.nonconforming, d.reserved = nc, rs
+        assert dgf.lib().dgf_forest_create(ctypes.byref(d), None, ctypes.byref(h)) == want
+        if want == 0:
+            dgf.lib().dgf_forest_destroy(h)

@@ -259,3 +259,55 @@ def test_chunk_length_does_not_change_bits(dgf, prec, monkeypatch):
         f.close()
     for R, U in out[1:]:
         assert np.array_equal(R, out[0][0]) and np.array_equal(U, out[0][1])
+
+
+# ----------------------------------------------------- mortar mode (R15)
+@pytest.mark.parametrize("case", sorted(SMALL))
+@pytest.mark.parametrize("p", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_comp"])
+def test_mortar_residual_matches_oracle(dgf, case, p, prec):
+    w = _small(case)
+    if w["dim"] == 3 and p == 3 and prec == "fp64":
+        pytest.skip("FP64 p=3 3D exceeds the per-CTA shared memory of the layer kernel")
+    if prec == "fp32_comp" and p != 2:
+        pytest.skip("compensated form: p = 2 covers the mortar path")
+    pr = {"fp64": dgf.FP64, "fp32": dgf.FP32, "fp32_comp": dgf.FP32_COMP}[prec]
+    f = dgf.Forest.from_workload(w, p=p, precision=pr, nonconforming="mortar")
+    S = dg.Solver(FO.build(w), p, nonconforming="mortar")
+    U = W.random_modal_state(f.n_leaves, f.dim, f.n_seg, p, seed=p + 21)
+    f.set_state(U)
+    L = f.dg_residual()
+    Lo = S.residual(U.astype(f.dtype).astype(np.float64))
+    assert rel(L, Lo) < TOL["fp32" if prec != "fp64" else "fp64"], rel(L, Lo)
+
+
+@pytest.mark.parametrize("case", ["pair_2d", "jitter_3d_n4"])
+def test_mortar_steps_conserve_totals(dgf, case):
+    """Mortar mode: the totals stay constant to round-off across level jumps
+    on the GPU (FP64), the paper's scheme drifts, and the steps follow the
+    oracle."""
+    w = _small(case)
+    drift = {}
+    for mode in ("mortar", "paper"):
+        f = dgf.Forest.from_workload(w, p=2, precision=dgf.FP64, cfl=0.2, nonconforming=mode)
+        U = W.random_modal_state(f.n_leaves, f.dim, f.n_seg, 2, seed=5)
+        f.set_state(U)
+        T0 = f.conserved_totals()
+        for _ in range(4):
+            f.rk_step()
+        drift[mode] = np.max(np.abs(f.conserved_totals() - T0)) / np.max(np.abs(T0))
+        if mode == "mortar":
+            S = dg.Solver(FO.build(w), 2, cfl=0.2, nonconforming="mortar")
+            Uo = U
+            for _ in range(4):
+                Uo = S.ssp_rk3_step(Uo, S.dt(Uo))
+            assert rel(f.get_state(), Uo) < TOL["fp64"]
+    assert drift["mortar"] < 1e-14 and drift["paper"] > 1e-10, drift
+
+
+def test_mortar_free_stream(dgf):
+    w = W.jitter3d_forest(seed=2, n_seg=4)
+    for prec, tol in ((dgf.FP64, 1e-11), (dgf.FP32, 2e-4)):
+        f = dgf.Forest.from_workload(w, p=2, precision=prec, nonconforming="mortar")
+        f.project(W.free_stream)
+        assert np.max(np.abs(f.dg_residual())) < tol * (1.0 / (0.25 / 4 / 2))  # |F| / h_min
