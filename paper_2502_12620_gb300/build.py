@@ -49,6 +49,10 @@ def build(verbose=False, ptxas_info=False, jobs=None):
         objs.append(o)
         c = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
              "--expt-relaxed-constexpr", "-c", os.path.join(CSRC, f), "-o", o]
+        if "_f32" in f:
+            # FP32 kernels: hardware-approximate divide and square root (a few
+            # ulp, far inside the FP32 parity bar; denormals are kept)
+            c[1:1] = ["-prec-div=false", "-prec-sqrt=false"]
         # extra -D flags for tuning sweeps (e.g. DGF_NVCC_DEFINES="-DDGF_STAGE_NT_F32=576")
         c[1:1] = os.environ.get("DGF_NVCC_DEFINES", "").split()
         if ptxas_info:
