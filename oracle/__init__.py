@@ -43,6 +43,11 @@ design notes of the repository):
      the two sides evaluate the flux from different data.  The "mortar"
      option restores it: the fine side's fluxes at its face points are also
      the coarse side's, integrated against the coarse test functions.
+  R16 adaptation (the paper gives no indicator formula): per cell
+     g = 2 |(K_e1, .., K_ed)| / K_0 of the density modes, block indicator the
+     maximum over its cells; refine above a threshold (with 2:1 closure),
+     then one pass in canonical leaf order coarsening sibling groups below a
+     threshold where 2:1 balance allows (``adapt.py``).
 
 Parity pins: every function here is pinned by the not-gpu tests in
 ``tests/test_oracle_*.py`` against closed forms, invariants and independent
