@@ -137,13 +137,39 @@ dgf_status dgf_set_stream(dgf_forest* f, void* stream);
 /* Refinement (Sec. 3.1, 3.3, 3.4): refine the given leaves (ids in the
  * current canonical order), then refine coarser leaves until every face
  * joins leaves at most one level apart.  A state set before the call is
- * carried over: new children by the split of Eqs. (11)-(12).  Leaf ids are
- * renumbered afterwards. */
+ * carried over on the device: new children by the split of Eqs. (11)-(12).
+ * Leaf ids are renumbered afterwards. */
 dgf_status dgf_block_refine(dgf_forest* f, const int64_t* leaf_ids, int64_t n);
 /* Coarsen the parents of the given leaves (all 2^d children of each parent
  * must be leaves).  DGF_EBALANCE (forest unchanged) if 2:1 balance would
- * break.  A state is carried over by the combine of Eqs. (13)-(14). */
+ * break.  A state is carried over on the device by the combine of Eqs.
+ * (13)-(14). */
 dgf_status dgf_block_coarsen(dgf_forest* f, const int64_t* leaf_ids, int64_t n);
+
+/* Refinement indicator per leaf (the paper refines by thresholds on cell
+ * quantities, Sec. 5-6, without a formula): per cell
+ * g = 2 |(K_e1, .., K_ed)| / K_0 of the density's Legendre modes (mean K_0,
+ * degree-one modes K_ea; h |grad rho| / rho_mean on a cube cell of edge h),
+ * the leaf's value the largest over its cells; 0 for p = 0; NaN when a cell
+ * has a non-positive mean density.  Computed on the device in the forest's
+ * precision.  out: host, n_leaves doubles.  Synchronises. */
+dgf_status dgf_indicator(dgf_forest* f, double* out);
+/* One adaptation (Sec. 3.4 for the data): leaves with indicator above
+ * refine_above and level below max_level are refined (2:1 closure may refine
+ * more); then, visiting the leaves in canonical order, each sibling group of
+ * leaves all below coarsen_below is coarsened when its first child (all
+ * position bits even) is met, unless 2:1 face balance forbids it.  The state
+ * follows on the device: copy, split (Eqs. (11)-(12)), combine (Eqs.
+ * (13)-(14), J-weighted).  n_refined: leaves refined by the threshold (not
+ * counting the closure); n_coarsened: parents restored (both nullable).
+ * Leaf ids change.  DGF_ENONFINITE if an indicator is NaN. */
+dgf_status dgf_adapt(dgf_forest* f, double refine_above, double coarsen_below, int32_t max_level,
+                     int64_t* n_refined, int64_t* n_coarsened);
+/* The same adaptation with a caller-supplied indicator (host, n_leaves
+ * doubles, e.g. from dgf_indicator or a criterion of the caller's own).
+ * Works on host-only forests (topology only). */
+dgf_status dgf_adapt_with(dgf_forest* f, const double* indicator, double refine_above, double coarsen_below,
+                          int32_t max_level, int64_t* n_refined, int64_t* n_coarsened);
 
 /* Number of leaf blocks. */
 dgf_status dgf_leaf_count(const dgf_forest* f, int64_t* n_leaves);

@@ -44,10 +44,12 @@ def indicator(S, U):
     return out
 
 
-def adapt(S, U, refine_above, coarsen_below, max_level):
+def adapt(S, U, refine_above, coarsen_below, max_level, g=None):
     """One adaptation; returns (new solver, new state, blocks refined by the
-    flags, parents coarsened)."""
-    g = indicator(S, U)
+    flags, parents coarsened).  g: per-leaf indicator (default indicator(S, U));
+    U may be None for a topology-only step (the state returned is then None)."""
+    if g is None:
+        g = indicator(S, U)
     F = copy.deepcopy(S.F)
     flagged = [k for i, k in enumerate(S.leaves) if g[i] > refine_above and k[1] < max_level]
     if flagged:
@@ -72,7 +74,7 @@ def adapt(S, U, refine_above, coarsen_below, max_level):
         except BalanceError:
             pass
     S2 = Solver(F, S.p, gamma=S.gamma, cfl=S.cfl, nonconforming=S.nonconforming)
-    return S2, S2.regrid_state(S, U), len(flagged), n_coarse
+    return S2, None if U is None else S2.regrid_state(S, U), len(flagged), n_coarse
 
 
 __all__ = ["indicator", "adapt"]

@@ -70,6 +70,11 @@ _SIGS = {
     "dgf_dg_residual": [_P, _P, ctypes.c_int],
     "dgf_rk_step": [_P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
     "dgf_get_time": [_P, ctypes.POINTER(ctypes.c_double)],
+    "dgf_indicator": [_P, ctypes.POINTER(ctypes.c_double)],
+    "dgf_adapt": [_P, ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                  ctypes.POINTER(ctypes.c_int64)],
+    "dgf_adapt_with": [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "dgf_step_count": [_P, ctypes.POINTER(ctypes.c_int64)],
     "dgf_set_time": [_P, ctypes.c_double],
     "dgf_compute_dt": [_P, ctypes.POINTER(ctypes.c_double)],
@@ -244,6 +249,28 @@ class Forest:
     def coarsen(self, leaf_ids):
         ids = np.ascontiguousarray(leaf_ids, np.int64)
         _check(lib().dgf_block_coarsen(self.h, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(ids)))
+
+    def indicator(self):
+        """Refinement indicator per leaf (see dgf_indicator)."""
+        out = np.zeros(self.n_leaves)
+        _check(lib().dgf_indicator(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def adapt(self, refine_above, coarsen_below, max_level, indicator=None):
+        """One adaptation step (indicator: per-leaf values, default the
+        device's own); returns (leaves refined by the threshold, parents
+        coarsened)."""
+        nr, nc = ctypes.c_int64(), ctypes.c_int64()
+        if indicator is None:
+            _check(lib().dgf_adapt(self.h, float(refine_above), float(coarsen_below), int(max_level),
+                                   ctypes.byref(nr), ctypes.byref(nc)))
+        else:
+            g = np.ascontiguousarray(indicator, np.float64)
+            assert g.shape == (self.n_leaves,)
+            _check(lib().dgf_adapt_with(self.h, g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        float(refine_above), float(coarsen_below), int(max_level),
+                                        ctypes.byref(nr), ctypes.byref(nc)))
+        return nr.value, nc.value
 
     def quad_points(self):
         out = np.zeros((self.n_leaves, self.nc, self.M, self.dim))

@@ -1491,6 +1491,137 @@ __global__ void __launch_bounds__(128) k_mortar_coarse(const GuardArgs<D, P, Rea
   A.out[(((size_t)A.mcoarse[i] * NV + v) * NFP + j) * nt + t] = acc;
 }
 
+// ============================================================ adaptation
+// Refinement indicator (reading R16): per cell g = 2 |(K_e1, .., K_eD)| / K_0
+// of the density's Legendre modes (K = V^{-1} u from the Gauss-point values);
+// the block keeps the maximum as the bits of a non-negative double.  One
+// thread per (leaf, cell).
+template <int D, int P, typename Real>
+__global__ void k_indicator(int nL, int n, const Real* __restrict__ U, unsigned long long* __restrict__ gmax,
+                            Tab<P + 1, Real> T) {
+  constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D);
+  const int nc = D == 3 ? n * n * n : n * n;
+  const size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= (size_t)nL * nc) return;
+  const int b = (int)(w / nc), c = (int)(w % nc);
+  const Real* u = U + (size_t)b * NV * Q * nc + c;
+  Real k0 = Real(0), ke[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) ke[a] = Real(0);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const Real x = u[(size_t)q * nc];
+    Real w0 = Real(1);
+    int r = q;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      w0 *= T.Vi[0][r % N];
+      r /= N;
+    }
+    k0 += w0 * x;
+    if constexpr (N > 1) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        Real wa = Real(1);
+        int rr = q;
+#pragma unroll
+        for (int bb = 0; bb < D; ++bb) {
+          wa *= T.Vi[bb == a ? 1 : 0][rr % N];
+          rr /= N;
+        }
+        ke[a] += wa * x;
+      }
+    }
+  }
+  Real g2 = Real(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) g2 += ke[a] * ke[a];
+  const double g = N > 1 ? 2.0 * sqrt((double)g2) / (double)k0 : 0.0;
+  if (g >= 0.0) atomicMax(&gmax[b], (unsigned long long)__double_as_longlong(g));
+  else atomicMax(&gmax[b], 0x7FF8000000000000ull);  // NaN or a non-positive mean: flag as huge
+}
+
+// State transfer after a regrid (Sec. 3.4): new leaf i copies an old leaf,
+// splits its old parent (Eqs. (11)-(12): the parent polynomial at the
+// child's Gauss points) or combines its old children (Eqs. (13)-(14): the
+// J-weighted projection by a host-built nodal operator: a shared one where
+// the children's Jacobian is one constant, else one per cell).  One thread
+// per (new leaf, variable, cell).
+template <int D, int P, typename Real>
+__global__ void k_transfer(int nL, int n, const Real* __restrict__ old, Real* __restrict__ out,
+                           const int* __restrict__ mode, const int* __restrict__ src,
+                           const int* __restrict__ kids, const long long* __restrict__ opoff,
+                           const long long* __restrict__ cellop, const Real* __restrict__ ops,
+                           Tab<P + 1, Real> T) {
+  constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NW = 1 << D;
+  const int nc = D == 3 ? n * n * n : n * n;
+  const size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= (size_t)nL * NV * nc) return;
+  const int c = (int)(w % nc);
+  const int v = (int)((w / nc) % NV);
+  const int i = (int)(w / ((size_t)nc * NV));
+  Real* o = out + ((size_t)i * NV + v) * Q * nc + c;
+  const int m = mode[i];
+  int I[3] = {0, 0, 0};
+  for (int a = 0, r = c; a < D; ++a, r /= n) I[a] = r % n;
+  if (m == 0) {
+    const Real* s = old + ((size_t)src[i] * NV + v) * Q * nc + c;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) o[(size_t)q * nc] = s[(size_t)q * nc];
+    return;
+  }
+  if (m == 1) {
+    const int bits = kids[(size_t)i * NW];  // child position bits
+    int pc = 0, e[3] = {0, 0, 0};
+    for (int a = 0, st = 1; a < D; ++a, st *= n) {
+      const int H = ((bits >> a) & 1) * n + I[a];
+      pc += (H >> 1) * st;
+      e[a] = H & 1;
+    }
+    const Real* s = old + ((size_t)src[i] * NV + v) * Q * nc + pc;
+    Real a0[Q], a1[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) a0[q] = s[(size_t)q * nc];
+    if (e[0]) apply_axis<D, N, 0, Real>(T.Snp, a0, a1);
+    else apply_axis<D, N, 0, Real>(T.Snm, a0, a1);
+    if constexpr (D == 2) {
+      if (e[1]) apply_axis<D, N, 1, Real>(T.Snp, a1, a0);
+      else apply_axis<D, N, 1, Real>(T.Snm, a1, a0);
+    } else {
+      if (e[1]) apply_axis<D, N, 1, Real>(T.Snp, a1, a0);
+      else apply_axis<D, N, 1, Real>(T.Snm, a1, a0);
+      if (e[2]) apply_axis<D, N, 2, Real>(T.Snp, a0, a1);
+      else apply_axis<D, N, 2, Real>(T.Snm, a0, a1);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) a0[q] = a1[q];
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) o[(size_t)q * nc] = a0[q];
+    return;
+  }
+  // combine: the 2^D old child cells under this cell, in child order e
+  const Real* op = ops + (size_t)cellop[(size_t)opoff[i] + c];
+  Real acc[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) acc[q] = Real(0);
+  for (int e = 0; e < NW; ++e) {
+    int cb = 0, cc = 0;
+    for (int a = 0, st = 1; a < D; ++a, st *= n) {
+      const int H = 2 * I[a] + ((e >> a) & 1);
+      cb |= (H / n) << a;
+      cc += (H % n) * st;
+    }
+    const Real* s = old + ((size_t)kids[(size_t)i * NW + cb] * NV + v) * Q * nc + cc;
+    for (int k = 0; k < Q; ++k) {
+      const Real x = s[(size_t)k * nc];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) acc[q] += op[(size_t)q * NW * Q + e * Q + k] * x;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) o[(size_t)q * nc] = acc[q];
+}
+
 // ============================================================ conversions
 // modal <-> nodal on arrays shaped [outer][var][mode or point][inner],
 // in place (each thread reads all its values before writing)

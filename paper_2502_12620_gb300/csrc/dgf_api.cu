@@ -746,6 +746,14 @@ cudaError_t do_totals(dgf_forest* f, const RtMisc& r) {
   if (f->d == 2) return state_f64(f) ? launch_totals<2, double>(r, f->stream) : launch_totals<2, float>(r, f->stream);
   return state_f64(f) ? launch_totals<3, double>(r, f->stream) : launch_totals<3, float>(r, f->stream);
 }
+cudaError_t do_indicator(dgf_forest* f, const RtMisc& r) {
+  if (f->d == 2) return state_f64(f) ? launch_indicator<2, double>(r, f->stream) : launch_indicator<2, float>(r, f->stream);
+  return state_f64(f) ? launch_indicator<3, double>(r, f->stream) : launch_indicator<3, float>(r, f->stream);
+}
+cudaError_t do_transfer(dgf_forest* f, const RtTransfer& r) {
+  if (f->d == 2) return state_f64(f) ? launch_transfer<2, double>(r, f->stream) : launch_transfer<2, float>(r, f->stream);
+  return state_f64(f) ? launch_transfer<3, double>(r, f->stream) : launch_transfer<3, float>(r, f->stream);
+}
 
 // modal <-> nodal in place; dbl selects the element type of X
 cudaError_t do_convert(dgf_forest* f, void* X, size_t outer, int inner, int to_nodal, bool dbl) {
@@ -1068,6 +1076,70 @@ dgf_status dgf_block_coarsen(dgf_forest* f, const int64_t* ids, int64_t n) {
   return regrid(f, old);
 }
 
+// per-leaf refinement indicator into host memory (synchronises)
+static dgf_status indicator_host(dgf_forest* f, std::vector<double>& g) {
+  if (dgf_status st = require_device(f)) return st;
+  if (!f->have_state) return fail(DGF_ESTATE, "no state set");
+  DeviceGuard dg(f->device);
+  const int64_t L = f->nL;
+  dgf_forest::Buf gb;
+  if (!ensure(f, gb, sizeof(unsigned long long) * std::max<int64_t>(L, 1)))
+    return fail(DGF_ENOMEM, "device allocation failed");
+  dgf_status st = cuda_check(cudaMemsetAsync(gb.ptr, 0, sizeof(unsigned long long) * L, f->stream), "memset");
+  RtMisc r = misc_args(f, 0);
+  r.gmax = (unsigned long long*)gb.ptr;
+  if (!st) st = cuda_check(do_indicator(f, r), "indicator");
+  g.assign(L, 0.0);
+  if (!st) st = copy_state(f, g.data(), gb.ptr, sizeof(double) * L, cudaMemcpyDeviceToHost);
+  cudaStreamSynchronize(f->stream);
+  dev_free(f, gb);
+  return st;
+}
+
+dgf_status dgf_indicator(dgf_forest* f, double* out) {
+  if (!f || !out) return fail(DGF_EINVAL, "null argument");
+  std::vector<double> g;
+  dgf_status st = indicator_host(f, g);
+  if (st) return st;
+  std::memcpy(out, g.data(), sizeof(double) * g.size());
+  return DGF_OK;
+}
+
+dgf_status dgf_adapt_with(dgf_forest* f, const double* g, double refine_above, double coarsen_below,
+                          int32_t max_level, int64_t* n_refined, int64_t* n_coarsened) {
+  if (!f || !g) return fail(DGF_EINVAL, "null argument");
+  if (max_level < 1 || max_level > 12) return fail(DGF_EINVAL, "max_level must be in [1, 12]");
+  const int64_t L = f->host.n_leaves();
+  for (int64_t i = 0; i < L; ++i)
+    if (std::isnan(g[i])) return fail(DGF_ENONFINITE, "indicator: non-positive mean density or NaN");
+  std::vector<uint64_t> refine_keys, low;
+  for (int64_t i = 0; i < L; ++i) {
+    const uint64_t k = f->host.leaves[i];
+    int64_t r;
+    int lev, pos[3];
+    Forest::unkey(k, &r, &lev, pos);
+    if (g[i] > refine_above && lev < max_level) refine_keys.push_back(k);
+    if (g[i] < coarsen_below) low.push_back(k);
+  }
+  std::sort(low.begin(), low.end());
+  std::vector<uint64_t> old = f->host.leaves;
+  const int64_t nc = f->host.adapt(refine_keys, low);
+  if (n_refined) *n_refined = (int64_t)refine_keys.size();
+  if (n_coarsened) *n_coarsened = nc;
+  if (refine_keys.empty() && nc == 0) return DGF_OK;
+  return regrid(f, old);
+}
+
+dgf_status dgf_adapt(dgf_forest* f, double refine_above, double coarsen_below, int32_t max_level,
+                     int64_t* n_refined, int64_t* n_coarsened) {
+  if (!f) return fail(DGF_EINVAL, "null argument");
+  if (max_level < 1 || max_level > 12) return fail(DGF_EINVAL, "max_level must be in [1, 12]");
+  std::vector<double> g;
+  dgf_status st = indicator_host(f, g);
+  if (st) return st;
+  return dgf_adapt_with(f, g.data(), refine_above, coarsen_below, max_level, n_refined, n_coarsened);
+}
+
 dgf_status dgf_leaf_count(const dgf_forest* f, int64_t* n) {
   if (!f || !n) return fail(DGF_EINVAL, "null argument");
   *n = f->host.n_leaves();
@@ -1356,71 +1428,80 @@ dgf_status dgf_kernel_times(dgf_forest* f, double* ms, int64_t* launches, int n_
 }  // extern "C"
 
 // ------------------------------------------------------------- regrid
-// modal <-> nodal on the host, per (leaf, var, cell), FP64
-static void host_convert(dgf_forest* f, std::vector<double>& X, int64_t L, bool to_nodal) {
-  const int d = f->d, N = f->N, M = f->M, nc = f->nc, nv = f->nv;
-  const std::vector<double>& A = to_nodal ? f->basis.V : f->basis.Vi;  // [out][in]
-  std::vector<double> a(M), b(M);
-  for (int64_t i = 0; i < L * nv; ++i) {
-    for (int c = 0; c < nc; ++c) {
-      for (int m = 0; m < M; ++m) a[m] = X[((size_t)i * M + m) * nc + c];
-      int S = 1;
-      for (int ax = 0; ax < d; ++ax) {
-        for (int o = 0; o < M; ++o) {
-          const int qa = (o / S) % N, base = o - qa * S;
-          double acc = 0.0;
-          for (int k = 0; k < N; ++k) acc += A[qa * N + k] * a[base + k * S];
-          b[o] = acc;
-        }
-        std::swap(a, b);
-        S *= N;
+// Nodal combine operator of one parent cell (Eqs. (13)-(14), reading R6):
+// u_P(x_q) = sum_e sum_k op[q][e Q + k] u_e(x_k), the J-weighted L2
+// projection onto the parent cell's polynomials of its 2^d children, every
+// integral by the child's own Gauss rule, evaluated at the parent's points.
+static bool combine_op_cell(dgf_forest* f, const double* const* child_coef, double* op) {
+  const int d = f->d, N = f->N, M = f->M, NW = 1 << d, KC = NW * M;
+  const Basis1D& B = f->basis;
+  std::vector<double> MP((size_t)M * M, 0.0), R((size_t)M * KC, 0.0);
+  for (int e = 0; e < NW; ++e) {
+    for (int q = 0; q < M; ++q) {
+      double xi[3], xp[3], wq = 1.0;
+      int rq = q;
+      for (int a = 0; a < d; ++a) {
+        xi[a] = B.x[rq % N];
+        wq *= B.w[rq % N];
+        xp[a] = 0.5 * (xi[a] + (((e >> a) & 1) ? 1.0 : -1.0));
+        rq /= N;
       }
-      for (int m = 0; m < M; ++m) X[((size_t)i * M + m) * nc + c] = a[m];
+      double A[9], Ja[9];
+      eval_map(d, child_coef[e], xi, nullptr, A);
+      const double wj = wq * det_and_cofactor(d, A, Ja);
+      double ph[64];
+      for (int m = 0; m < M; ++m) ph[m] = phi(B, d, m, xp);
+      for (int m = 0; m < M; ++m) {
+        for (int m2 = 0; m2 < M; ++m2) MP[(size_t)m * M + m2] += wj * ph[m] * ph[m2];
+        R[(size_t)m * KC + e * M + q] += wj * ph[m];
+      }
     }
   }
+  if (!chol_solve(M, MP, R, KC)) return false;
+  for (int q = 0; q < M; ++q) {
+    double xq[3];
+    for (int a = 0, rq = q; a < d; ++a, rq /= N) xq[a] = B.x[rq % N];
+    double ph[64];
+    for (int m = 0; m < M; ++m) ph[m] = phi(B, d, m, xq);
+    for (int k = 0; k < KC; ++k) {
+      double acc = 0.0;
+      for (int m = 0; m < M; ++m) acc += ph[m] * R[(size_t)m * KC + k];
+      op[(size_t)q * KC + k] = acc;
+    }
+  }
+  return true;
 }
 
-// New leaves get their state from the old ones: copies, splits (Eqs.
-// (11)-(12)) or combines (Eqs. (13)-(14)); done on the host in FP64 from a
-// device snapshot (regrids are rare compared with time increments).
+// New leaves get their state from the old ones on the device: copies,
+// splits (Eqs. (11)-(12)) or combines (Eqs. (13)-(14)), Sec. 3.4; the old
+// state buffer is kept until the transfer kernel has run.
 static dgf_status regrid(dgf_forest* f, const std::vector<uint64_t>& old_leaves) {
-  const int d = f->d, n = f->n, M = f->M, nc = f->nc, nv = f->nv, N = f->N;
-  std::vector<double> old_state;
   const bool carry = f->device >= 0 && f->have_state;
-  std::vector<std::vector<double>> old_coef;
-  if (carry) {
-    DeviceGuard dg(f->device);
-    const size_t cnt = (size_t)old_leaves.size() * nv * M * nc;
-    old_state.resize(cnt);
-    if (state_f64(f)) {
-      dgf_status st = copy_state(f, old_state.data(), state_ptr(f), cnt * 8, cudaMemcpyDeviceToHost);
-      if (st) return st;
-    } else {
-      std::vector<float> tmp(cnt);
-      dgf_status st = copy_state(f, tmp.data(), f->U[0].ptr, cnt * 4, cudaMemcpyDeviceToHost);
-      if (st) return st;
-      for (size_t i = 0; i < cnt; ++i) old_state[i] = tmp[i];
-    }
-  }
-  // the device state is nodal: bring it to modes for the host-side transfer
-  if (carry) host_convert(f, old_state, (int64_t)old_leaves.size(), false);
+  if (!carry) return build_device(f);
+  const int d = f->d, n = f->n, N = f->N, M = f->M, nc = f->nc, NW = 1 << d;
+  DeviceGuard dg(f->device);
+  cudaStreamSynchronize(f->stream);
+  dgf_forest::Buf old;
+  dgf_forest::Buf& live = f->comp ? f->U64[f->cur] : f->U[0];
+  old = live;
+  live = dgf_forest::Buf();
   dgf_status st = build_device(f);
-  if (st) return st;
-  if (!carry) return DGF_OK;
+  if (st) {
+    dev_free(f, old);
+    f->have_state = false;
+    return st;
+  }
   std::unordered_map<uint64_t, int64_t> old_index;
   for (size_t i = 0; i < old_leaves.size(); ++i) old_index[old_leaves[i]] = (int64_t)i;
-  const Basis1D& B = f->basis;
   const int64_t L = f->host.n_leaves();
-  std::vector<double> ns((size_t)L * nv * M * nc, 0.0);
-  auto at = [&](std::vector<double>& s, int64_t leaf, int v, int m, int c) -> double& {
-    return s[(((size_t)leaf * nv + v) * M + m) * nc + c];
-  };
-  std::vector<double> coef;
+  std::vector<int> mode(L, 0), src(L, 0), kids((size_t)L * NW, 0);
+  std::vector<long long> opoff(L, 0);  // combine leaves: first entry in cellop
+  std::vector<int64_t> combine_leaves;
   for (int64_t i = 0; i < L; ++i) {
     const uint64_t k = f->host.leaves[i];
     auto it = old_index.find(k);
     if (it != old_index.end()) {
-      std::memcpy(&at(ns, i, 0, 0, 0), &at(old_state, it->second, 0, 0, 0), sizeof(double) * nv * M * nc);
+      src[i] = (int)it->second;
       continue;
     }
     int64_t r;
@@ -1429,98 +1510,142 @@ static dgf_status regrid(dgf_forest* f, const std::vector<uint64_t>& old_leaves)
     int pp[3] = {pos[0] >> 1, pos[1] >> 1, pos[2] >> 1};
     auto pit = old_index.find(Forest::key(r, lev - 1, pp));
     if (pit != old_index.end()) {
-      // split each parent cell to this child's cells (tensor form, exact)
-      for (int c = 0; c < nc; ++c) {
-        int I[3] = {0, 0, 0}, tt = c, Pc = 0, st = 1, e[3] = {0, 0, 0};
-        for (int a = 0; a < d; ++a) {
-          I[a] = tt % n;
-          tt /= n;
-          const int H = (pos[a] & 1) * n + I[a];
-          Pc += (H >> 1) * st;
-          e[a] = H & 1;
-          st *= n;
-        }
-        for (int v = 0; v < nv; ++v) {
-          for (int m = 0; m < M; ++m) {
-            double acc = 0.0;
-            for (int kk = 0; kk < M; ++kk) {
-              double w = 1.0;
-              int rm = m, rk = kk;
-              for (int a = 0; a < d; ++a) {
-                const std::vector<double>& S = e[a] ? B.Sp : B.Sm;
-                w *= S[(rm % N) * N + (rk % N)];
-                rm /= N;
-                rk /= N;
-              }
-              acc += w * at(old_state, pit->second, v, kk, Pc);
-            }
-            at(ns, i, v, m, c) = acc;
-          }
-        }
-      }
+      mode[i] = 1;
+      src[i] = (int)pit->second;
+      int bits = 0;
+      for (int a = 0; a < d; ++a) bits |= (pos[a] & 1) << a;
+      kids[(size_t)i * NW] = bits;
       continue;
     }
-    // combine: this leaf is a new parent of old leaves
-    for (int c = 0; c < nc; ++c) {
-      int I[3] = {0, 0, 0}, tt = c;
-      for (int a = 0; a < d; ++a) {
-        I[a] = tt % n;
-        tt /= n;
+    mode[i] = 2;
+    for (int c = 0; c < NW; ++c) {
+      int kp[3] = {0, 0, 0};
+      for (int a = 0; a < d; ++a) kp[a] = 2 * pos[a] + ((c >> a) & 1);
+      auto kt = old_index.find(Forest::key(r, lev + 1, kp));
+      if (kt == old_index.end()) {
+        dev_free(f, old);
+        f->have_state = false;
+        return fail(DGF_EINVAL, "regrid: a new block is neither kept, split nor combined");
       }
-      const int KC = (1 << d) * M;
-      std::vector<double> MP(M * M, 0.0), RHS((size_t)M * nv, 0.0);
-      for (int e = 0; e < (1 << d); ++e) {
-        int cb[3] = {0, 0, 0}, cc = 0, st = 1;
-        for (int a = 0; a < d; ++a) {
-          const int H = 2 * I[a] + ((e >> a) & 1);
-          cb[a] = H / n;
-          cc += (H - cb[a] * n) * st;
-          st *= n;
-        }
-        int kp[3] = {0, 0, 0};
-        for (int a = 0; a < d; ++a) kp[a] = 2 * pos[a] + cb[a];
-        const int64_t kid = old_index.at(Forest::key(r, lev + 1, kp));
-        f->host.cell_coefficients(Forest::key(r, lev + 1, kp), coef);
-        double ccoef[24];
-        for (int kk = 0; kk < (1 << d) * d; ++kk) ccoef[kk] = coef[(size_t)kk * nc + cc];
-        for (int q = 0; q < M; ++q) {
-          double xi[3], xp[3], wq = 1.0;
-          int rq = q;
-          for (int a = 0; a < d; ++a) {
-            xi[a] = B.x[rq % N];
-            wq *= B.w[rq % N];
-            xp[a] = 0.5 * (xi[a] + (((e >> a) & 1) ? 1.0 : -1.0));
-            rq /= N;
-          }
-          double A[9], Ja[9];
-          eval_map(d, ccoef, xi, nullptr, A);
-          const double wj = wq * det_and_cofactor(d, A, Ja);
-          double pp2[64];
-          for (int m = 0; m < M; ++m) pp2[m] = phi(B, d, m, xp);
-          for (int v = 0; v < nv; ++v) {
-            double u = 0.0;
-            for (int kk = 0; kk < M; ++kk) u += phi(B, d, kk, xi) * at(old_state, kid, v, kk, cc);
-            for (int m = 0; m < M; ++m) RHS[(size_t)m * nv + v] += wj * pp2[m] * u;
-          }
-          for (int m = 0; m < M; ++m)
-            for (int m2 = 0; m2 < M; ++m2) MP[m * M + m2] += wj * pp2[m] * pp2[m2];
-        }
-        (void)KC;
-      }
-      if (!chol_solve(M, MP, RHS, nv)) return fail(DGF_EINVAL, "singular combine mass matrix");
-      for (int v = 0; v < nv; ++v)
-        for (int m = 0; m < M; ++m) at(ns, i, v, m, c) = RHS[(size_t)m * nv + v];
+      kids[(size_t)i * NW + c] = (int)kt->second;
+    }
+    opoff[i] = (long long)combine_leaves.size() * nc;
+    combine_leaves.push_back(i);
+  }
+  // combine operators (host, FP64): a parent cell whose children all have
+  // the same constant Jacobian uses the shared reference operator (stored
+  // first); any other cell gets its own
+  const size_t opsz = (size_t)M * NW * M;
+  std::vector<std::vector<double>> ccoef((size_t)combine_leaves.size() * NW);
+  for (size_t j = 0; j < combine_leaves.size(); ++j) {
+    int64_t r;
+    int lev, pos[3];
+    Forest::unkey(f->host.leaves[combine_leaves[j]], &r, &lev, pos);
+    for (int c = 0; c < NW; ++c) {
+      int kp[3] = {0, 0, 0};
+      for (int a = 0; a < d; ++a) kp[a] = 2 * pos[a] + ((c >> a) & 1);
+      f->host.cell_coefficients(Forest::key(r, lev + 1, kp), ccoef[j * NW + c]);
     }
   }
-  host_convert(f, ns, L, true);
-  DeviceGuard dg(f->device);
-  if (state_f64(f)) {
-    st = copy_state(f, state_ptr(f), ns.data(), ns.size() * 8, cudaMemcpyHostToDevice);
-  } else {
-    std::vector<float> tmp(ns.begin(), ns.end());
-    st = copy_state(f, f->U[0].ptr, tmp.data(), tmp.size() * 4, cudaMemcpyHostToDevice);
+  const int64_t ncomb = (int64_t)combine_leaves.size() * nc;
+  auto child_cells = [&](int64_t jc, double (*cc)[24]) {
+    const size_t j = (size_t)(jc / nc);
+    const int c = (int)(jc % nc);
+    int I[3] = {0, 0, 0};
+    for (int a = 0, rr = c; a < d; ++a, rr /= n) I[a] = rr % n;
+    for (int e = 0; e < NW; ++e) {
+      int cb = 0, cell = 0;
+      for (int a = 0, st2 = 1; a < d; ++a, st2 *= n) {
+        const int H = 2 * I[a] + ((e >> a) & 1);
+        cb |= (H / n) << a;
+        cell += (H % n) * st2;
+      }
+      const std::vector<double>& C = ccoef[j * NW + cb];
+      for (int kk = 0; kk < NW * d; ++kk) cc[e][kk] = C[(size_t)kk * nc + cell];
+    }
+  };
+  // which cells need their own operator
+  std::vector<unsigned char> own(ncomb, 0);
+  parallel_for(ncomb, [&](int64_t jc) {
+    double cc[8][24];
+    child_cells(jc, cc);
+    double J0 = 0.0;
+    for (int e = 0; e < NW && !own[jc]; ++e)
+      for (int q = 0; q < M; ++q) {
+        double xi[3];
+        for (int a = 0, rq = q; a < d; ++a, rq /= N) xi[a] = f->basis.x[rq % N];
+        double A[9], Ja[9];
+        eval_map(d, cc[e], xi, nullptr, A);
+        const double J = det_and_cofactor(d, A, Ja);
+        if (e == 0 && q == 0) J0 = J;
+        if (std::fabs(J - J0) > 1e-12 * std::fabs(J0)) {
+          own[jc] = 1;
+          break;
+        }
+      }
+  });
+  std::vector<long long> cellop(std::max<int64_t>(ncomb, 1), 0);
+  size_t nops = ncomb > 0 ? 1 : 0;
+  for (int64_t jc = 0; jc < ncomb; ++jc)
+    if (own[jc]) cellop[jc] = (long long)(opsz * nops++);
+  std::vector<double> ops(opsz * nops, 0.0);
+  std::atomic<bool> singular{false};
+  if (ncomb > 0) {
+    // the reference operator: children of a unit cube cell
+    double cc[8][24];
+    const double* cp[8];
+    for (int e = 0; e < NW; ++e) {
+      for (int kk = 0; kk < NW * d; ++kk) cc[e][kk] = 0.0;
+      for (int a = 0; a < d; ++a) cc[e][((1 << a)) * d + a] = 0.25;  // x_a = xi_a / 4 (any constant J)
+      cp[e] = cc[e];
+    }
+    if (!combine_op_cell(f, cp, &ops[0])) singular = true;
   }
-  if (st) return st;
+  parallel_for(ncomb, [&](int64_t jc) {
+    if (!own[jc]) return;
+    double cc[8][24];
+    const double* cp[8];
+    child_cells(jc, cc);
+    for (int e = 0; e < NW; ++e) cp[e] = cc[e];
+    if (!combine_op_cell(f, cp, &ops[(size_t)cellop[jc]])) singular = true;
+  });
+  if (singular) {
+    dev_free(f, old);
+    f->have_state = false;
+    return fail(DGF_EINVAL, "singular combine mass matrix");
+  }
+  dgf_forest::Buf bm, bs, bk, bo, bc, bops;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(f->stream);
+    dgf_forest::Buf* all[] = {&old, &bm, &bs, &bk, &bo, &bc, &bops};
+    for (auto* b : all) dev_free(f, *b);
+  };
+  if ((st = upload(f, bm, mode)) || (st = upload(f, bs, src)) || (st = upload(f, bk, kids)) ||
+      (st = upload(f, bo, opoff)) || (st = upload(f, bc, cellop)) ||
+      (st = state_f64(f) ? upload(f, bops, ops) : upload(f, bops, convert<float>(ops)))) {
+    cleanup();
+    f->have_state = false;
+    return st;
+  }
+  RtTransfer tr{};
+  tr.p = f->p;
+  tr.nL = (int)L;
+  tr.n = n;
+  tr.old = old.ptr;
+  tr.out = state_ptr(f);
+  tr.mode = (const int*)bm.ptr;
+  tr.src = (const int*)bs.ptr;
+  tr.kids = (const int*)bk.ptr;
+  tr.opoff = (const long long*)bo.ptr;
+  tr.cellop = (const long long*)bc.ptr;
+  tr.ops = bops.ptr;
+  tr.T = f->tab;
+  st = cuda_check(do_transfer(f, tr), "transfer");
+  cleanup();
+  if (st) {
+    f->have_state = false;
+    return st;
+  }
   return init_lambda(f);
 }
 

@@ -560,6 +560,73 @@ bool Forest::coarsen(const std::vector<uint64_t>& parents, bool* balance_violati
   return true;
 }
 
+bool Forest::can_coarsen(uint64_t parent) const {
+  auto it = tree.find(parent);
+  if (it == tree.end() || it->second) return false;
+  int64_t r;
+  int lev, pos[3];
+  unkey(parent, &r, &lev, pos);
+  for (int c = 0; c < (1 << d); ++c) {
+    int cp[3] = {0, 0, 0};
+    for (int a = 0; a < d; ++a) cp[a] = 2 * pos[a] + ((c >> a) & 1);
+    auto jt = tree.find(key(r, lev + 1, cp));
+    if (jt == tree.end() || !jt->second) return false;
+  }
+  // a face neighbour region at the parent's level that is refined, with a
+  // refined child on the shared face, holds leaves two levels finer
+  for (int f = 0; f < 2 * d; ++f) {
+    int64_t r2;
+    int q[3], f2;
+    Orient o;
+    if (!neighbour(r, lev, pos, f, &r2, q, &o, &f2)) continue;
+    auto nt = tree.find(key(r2, lev, q));
+    if (nt == tree.end() || nt->second) continue;
+    const int b2 = f2 >> 1, s2 = f2 & 1;
+    for (int c = 0; c < (1 << d); ++c) {
+      if (((c >> b2) & 1) != s2) continue;
+      int cp[3] = {0, 0, 0};
+      for (int a = 0; a < d; ++a) cp[a] = 2 * q[a] + ((c >> a) & 1);
+      auto ct = tree.find(key(r2, lev + 1, cp));
+      if (ct != tree.end() && !ct->second) return false;
+    }
+  }
+  return true;
+}
+
+int64_t Forest::adapt(const std::vector<uint64_t>& refine_keys, const std::vector<uint64_t>& low_sorted) {
+  if (!refine_keys.empty()) refine(refine_keys);
+  const std::vector<uint64_t> snapshot = leaves;
+  int64_t n = 0;
+  for (uint64_t k : snapshot) {
+    int64_t r;
+    int lev, pos[3];
+    unkey(k, &r, &lev, pos);
+    bool first = lev > 1;
+    for (int a = 0; a < d; ++a) first = first && (pos[a] & 1) == 0;
+    if (!first) continue;
+    auto it = tree.find(k);
+    if (it == tree.end() || !it->second) continue;
+    int pp[3] = {pos[0] >> 1, pos[1] >> 1, pos[2] >> 1};
+    const uint64_t parent = key(r, lev - 1, pp);
+    bool low = true;
+    for (int c = 0; c < (1 << d) && low; ++c) {
+      int cp[3] = {0, 0, 0};
+      for (int a = 0; a < d; ++a) cp[a] = 2 * pp[a] + ((c >> a) & 1);
+      low = std::binary_search(low_sorted.begin(), low_sorted.end(), key(r, lev, cp));
+    }
+    if (!low || !can_coarsen(parent)) continue;
+    for (int c = 0; c < (1 << d); ++c) {
+      int cp[3] = {0, 0, 0};
+      for (int a = 0; a < d; ++a) cp[a] = 2 * pp[a] + ((c >> a) & 1);
+      tree.erase(key(r, lev, cp));
+    }
+    tree[parent] = 1;
+    ++n;
+  }
+  order_leaves();
+  return n;
+}
+
 Forest::Tables Forest::tables() const {
   Tables T;
   const int64_t L = n_leaves();

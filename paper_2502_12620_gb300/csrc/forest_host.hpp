@@ -85,6 +85,11 @@ class Forest {
   bool refine(const std::vector<uint64_t>& keys);
   // coarsen parents; false (unchanged) with error on violation
   bool coarsen(const std::vector<uint64_t>& parents, bool* balance_violation);
+  // one adaptation pass (refine the given leaves with closure, then visit
+  // the leaves in canonical order and coarsen each sibling group whose
+  // members all satisfy low(key) where balance allows); returns the number
+  // of parents coarsened
+  int64_t adapt(const std::vector<uint64_t>& refine_keys, const std::vector<uint64_t>& low_sorted);
 
   void order_leaves();
   int64_t n_leaves() const { return (int64_t)leaves.size(); }
@@ -109,6 +114,9 @@ class Forest {
   bool find_containing_leaf(int64_t root, int level, const int* pos, uint64_t* out,
                             int* out_level) const;
   std::vector<uint64_t> violations() const;
+  // parent's children are all leaves and making it a leaf keeps 2:1 face
+  // balance (no leaf two levels finer would touch it)
+  bool can_coarsen(uint64_t parent) const;
 };
 
 // x(xi), dx/dxi and (J, J dxi_i/dx_j) from trilinear coefficients of one

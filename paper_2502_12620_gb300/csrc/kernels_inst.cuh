@@ -272,6 +272,29 @@ static cudaError_t totals_p(const RtMisc& r, cudaStream_t s) {
 }
 
 template <int D, int P, typename Real>
+static cudaError_t indicator_p(const RtMisc& r, cudaStream_t s) {
+  const int nc = D == 3 ? r.n * r.n * r.n : r.n * r.n;
+  const size_t total = (size_t)r.nL * nc;
+  const int th = 128;
+  if (total == 0) return cudaSuccess;
+  k_indicator<D, P, Real><<<(unsigned)((total + th - 1) / th), th, 0, s>>>(
+      r.nL, r.n, (const Real*)r.U, r.gmax, make_tab<P + 1, Real>(r.T));
+  return cudaGetLastError();
+}
+
+template <int D, int P, typename Real>
+static cudaError_t transfer_p(const RtTransfer& r, cudaStream_t s) {
+  const int nc = D == 3 ? r.n * r.n * r.n : r.n * r.n;
+  const size_t total = (size_t)r.nL * (D + 2) * nc;
+  const int th = 128;
+  if (total == 0) return cudaSuccess;
+  k_transfer<D, P, Real><<<(unsigned)((total + th - 1) / th), th, 0, s>>>(
+      r.nL, r.n, (const Real*)r.old, (Real*)r.out, r.mode, r.src, r.kids, r.opoff, r.cellop, (const Real*)r.ops,
+      make_tab<P + 1, Real>(r.T));
+  return cudaGetLastError();
+}
+
+template <int D, int P, typename Real>
 static cudaError_t convert_p(size_t outer, int inner, void* X, int to_nodal, const RtTables& T, cudaStream_t s) {
   const size_t total = outer * (D + 2) * inner;
   const int th = 128;
@@ -319,6 +342,18 @@ static cudaError_t convert_p(size_t outer, int inner, void* X, int to_nodal, con
     constexpr int D = DIM;                                                                  \
     using Real = REAL;                                                                      \
     DGF_DISPATCH_P(totals_p, r, s)                                                          \
+  }                                                                                         \
+  template <>                                                                               \
+  cudaError_t launch_indicator<DIM, REAL>(const RtMisc& r, cudaStream_t s) {                \
+    constexpr int D = DIM;                                                                  \
+    using Real = REAL;                                                                      \
+    DGF_DISPATCH_P(indicator_p, r, s)                                                       \
+  }                                                                                         \
+  template <>                                                                               \
+  cudaError_t launch_transfer<DIM, REAL>(const RtTransfer& r, cudaStream_t s) {             \
+    constexpr int D = DIM;                                                                  \
+    using Real = REAL;                                                                      \
+    DGF_DISPATCH_P(transfer_p, r, s)                                                        \
   }                                                                                         \
   template <>                                                                               \
   cudaError_t launch_convert<DIM, REAL>(int p, size_t outer, int inner, void* X, int to_nodal, \

@@ -68,6 +68,20 @@ struct RtGuard {
   RtTables T;
 };
 
+// state transfer after a regrid (new leaves from old ones)
+struct RtTransfer {
+  int p, nL, n;
+  const void* old;
+  void* out;
+  const int* mode;        // [new leaf] 0 copy, 1 split, 2 combine
+  const int* src;         // [new leaf] old leaf (copy, split)
+  const int* kids;        // [new leaf][2^d] old children (combine); [0] = position bits (split)
+  const long long* opoff; // [new leaf] combine leaves: first entry of its cells in cellop
+  const long long* cellop; // [combine cell] element offset of its operator in ops
+  const void* ops;        // [op][Q][2^d Q]; op 0 = the reference (constant-Jacobian) operator
+  RtTables T;
+};
+
 struct RtMisc {
   int p, nL, n;
   const void* U;
@@ -79,6 +93,7 @@ struct RtMisc {
   double gamma;
   unsigned long long* lam_bits;
   int* status;
+  unsigned long long* gmax;  // refinement indicator per leaf (double bits)
   RtTables T;
 };
 
@@ -94,6 +109,10 @@ template <int D, typename Real>
 cudaError_t launch_project(const RtMisc& r, cudaStream_t s);
 template <int D, typename Real>
 cudaError_t launch_totals(const RtMisc& r, cudaStream_t s);
+template <int D, typename Real>
+cudaError_t launch_indicator(const RtMisc& r, cudaStream_t s);
+template <int D, typename Real>
+cudaError_t launch_transfer(const RtTransfer& r, cudaStream_t s);
 // modal <-> nodal in place on [outer][var][mode/point][inner]
 template <int D, typename Real>
 cudaError_t launch_convert(int p, size_t outer, int inner, void* X, int to_nodal, const RtTables& T,

@@ -171,3 +171,31 @@ def test_nonconforming_option_is_checked(dgf):
         assert dgf.lib().dgf_forest_create(ctypes.byref(d), None, ctypes.byref(h)) == want
         if want == 0:
             dgf.lib().dgf_forest_destroy(h)
+
+
+@pytest.mark.parametrize("case,seed", [("lattice3d", 0), ("lattice3d", 1), ("pair2d", 2), ("jitter3d", 3)])
+def test_adapt_topology_matches_oracle(dgf, case, seed):
+    """Several adaptation passes with the same random per-leaf indicator on
+    both sides: refinement with closure and the canonical-order coarsening
+    pass (local 2:1 check here, global check in the oracle) give the same
+    leaves, tables and counts bit for bit."""
+    from oracle import adapt as A
+    from oracle import dg
+    w = {"lattice3d": lambda: W.lattice_forest(3, 2, 1.0, 2, rotate_roots=True, seed=seed),
+         "pair2d": lambda: W.rotated_pair_2d(n_seg=2),
+         "jitter3d": lambda: W.jitter3d_forest(seed=seed, n_seg=2)}[case]()
+    f = _host_forest(dgf, w, p=1)
+    S = dg.Solver(FO.build(w), 1)
+    rng = np.random.default_rng(seed)
+    done = np.zeros(2, int)
+    for it in range(5):
+        g = rng.uniform(0.0, 1.0, size=f.n_leaves)
+        ra, cb = (0.8, 0.5) if it % 2 == 0 else (0.95, 0.9)
+        counts = f.adapt(ra, cb, 4, indicator=g)
+        S, _, nr, nc = A.adapt(S, None, ra, cb, 4, g=g)
+        assert counts == (nr, nc), it
+        done += counts
+        T, O = f.leaf_table(), S.F.leaf_table()
+        for k in ("root", "level", "pos", "kind", "nbr", "orient"):
+            assert np.array_equal(T[k].astype(np.int64), O[k].astype(np.int64)), (it, k)
+    assert done[0] > 0 and done[1] > 0, done  # both rules were exercised
