@@ -48,6 +48,9 @@ design notes of the repository):
      maximum over its cells; refine above a threshold (with 2:1 closure),
      then one pass in canonical leaf order coarsening sibling groups below a
      threshold where 2:1 balance allows (``adapt.py``).
+  R17 positivity: optional scaling limiter of Zhang & Shu (2010) after every
+     RK stage, toward the J-weighted cell mean, checked at the volume and
+     face Gauss points (``limiter.py``).
 
 Parity pins: every function here is pinned by the not-gpu tests in
 ``tests/test_oracle_*.py`` against closed forms, invariants and independent

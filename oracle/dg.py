@@ -138,16 +138,19 @@ def _combine(ops, K_children, corners_children):
 class Solver:
     """One forest + degree p: guard fill, residual, SSP-RK3, CFL, totals."""
 
-    def __init__(self, forest, p, gamma=GAMMA, cfl=0.1, nonconforming="paper"):
+    def __init__(self, forest, p, gamma=GAMMA, cfl=0.1, nonconforming="paper", limiter=None):
         """nonconforming: "paper" (the guard scheme of Sec. 3.5 on both sides
         of a level jump) or "mortar" (reading R15: the coarse side takes the
-        fine side's fluxes, integrated against its own test functions)."""
+        fine side's fluxes, integrated against its own test functions).
+        limiter: None, or eps of the positivity limiter (reading R17) applied
+        after every Runge-Kutta stage."""
         assert nonconforming in ("paper", "mortar")
         self.F = forest
         self.d, self.n, self.p = forest.d, forest.n, p
         self.ops = Ops(self.d, p)
         self.gamma, self.cfl = gamma, cfl
         self.nonconforming = nonconforming
+        self.limiter = limiter
         self.nv = self.d + 2
         self._rot_cache = {}
         self.refresh()
@@ -402,11 +405,18 @@ class Solver:
             best = min(best, float(np.min(h[:, None] / lam)))
         return self.cfl * best
 
+    def _limit(self, U):
+        if self.limiter is None:
+            return U
+        from .limiter import positivity_limit
+        return positivity_limit(self, U, self.limiter)[0]
+
     def ssp_rk3_step(self, U, dt):
-        """Shu-Osher SSP-RK3 (Sec. 2, last paragraph; reading R4)."""
-        u1 = U + dt * self.residual(U)
-        u2 = 0.75 * U + 0.25 * (u1 + dt * self.residual(u1))
-        return U / 3.0 + 2.0 / 3.0 * (u2 + dt * self.residual(u2))
+        """Shu-Osher SSP-RK3 (Sec. 2, last paragraph; reading R4), with the
+        positivity limiter after every stage when enabled (reading R17)."""
+        u1 = self._limit(U + dt * self.residual(U))
+        u2 = self._limit(0.75 * U + 0.25 * (u1 + dt * self.residual(u1)))
+        return self._limit(U / 3.0 + 2.0 / 3.0 * (u2 + dt * self.residual(u2)))
 
     def run(self, U, steps, t_end=np.inf):
         t = 0.0
