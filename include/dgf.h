@@ -226,6 +226,20 @@ dgf_status dgf_compute_dt(dgf_forest* f, double* dt);
  * reduction; totals[nv] host (synchronises). */
 dgf_status dgf_conserved_totals(dgf_forest* f, double* totals);
 
+/* Positivity-preserving limiter (the paper uses limiters for its cylinder
+ * case, Sec. 6, without details; this is the scaling limiter of Zhang & Shu,
+ * J. Comput. Phys. 229 (2010)): after every RK stage each cell is scaled
+ * toward its J-weighted mean u_bar so that rho >= eps rho_bar and
+ * p >= eps p(u_bar) at every volume and face Gauss point (density first,
+ * then pressure through a quadratic in the scaling factor); the mean is
+ * kept.  eps in (0, 1) turns it on, 0 off.  A cell whose mean is not
+ * admissible sets DGF_ENONFINITE in the status word.  dt of the next step is
+ * taken from the unlimited last stage.  DGF_EUNSUPPORTED for
+ * DGF_FP32_COMP forests.  dgf_limit applies it once to the current state
+ * (for initial data). */
+dgf_status dgf_set_limiter(dgf_forest* f, double eps);
+dgf_status dgf_limit(dgf_forest* f);
+
 /* Device status word: 0 or DGF_ENONFINITE (synchronises); reset clears it. */
 dgf_status dgf_status_word(dgf_forest* f, int32_t* status, int reset);
 

@@ -71,6 +71,8 @@ _SIGS = {
     "dgf_rk_step": [_P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
     "dgf_get_time": [_P, ctypes.POINTER(ctypes.c_double)],
     "dgf_indicator": [_P, ctypes.POINTER(ctypes.c_double)],
+    "dgf_set_limiter": [_P, ctypes.c_double],
+    "dgf_limit": [_P],
     "dgf_adapt": [_P, ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
                   ctypes.POINTER(ctypes.c_int64)],
     "dgf_adapt_with": [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_double, ctypes.c_int32,
@@ -360,6 +362,14 @@ class Forest:
         T = np.zeros(self.nv)
         _check(lib().dgf_conserved_totals(self.h, _ptr(T)))
         return T
+
+    def set_limiter(self, eps):
+        """Positivity limiter after every RK stage (eps > 0), or off (0)."""
+        _check(lib().dgf_set_limiter(self.h, float(eps)))
+
+    def limit(self):
+        """Apply the positivity limiter to the current state once."""
+        _check(lib().dgf_limit(self.h))
 
     def status_word(self, reset=False):
         s = ctypes.c_int32()

@@ -189,7 +189,9 @@ __device__ __forceinline__ void lf_flux(const Real (&uL)[D + 2], const Real (&uR
   const Real an = sqrt(an2);
   const Real sL = fabs(vnL * riL) + sqrt(gamma * pL * riL) * an;
   const Real sR = fabs(vnR * riR) + sqrt(gamma * pR * riR) * an;
-  const Real alpha = sL > sR ? sL : sR;
+  // a NaN speed (negative pressure or density at a face point) propagates
+  // into the flux, so the state and then the status word report it
+  const Real alpha = (sL > sR || sL != sL) ? sL : sR;
 #pragma unroll
   for (int v = 0; v < D + 2; ++v) Fh[v] = Real(0.5) * (FL[v] + FR[v] + alpha * (uL[v] - uR[v]));
 }
@@ -922,7 +924,9 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
         double u = __shfl_xor_sync(0xffffffffu, v, o);
         v = u < v ? u : v;
       }
-      if (lane == 0) atomicMin(A.lam_bits, (unsigned long long)__double_as_longlong(v));
+      // a CTA whose cells were all inadmissible contributes nothing, so a
+      // broken state leaves no CFL value and the next dt is 0
+      if (lane == 0 && v < 3.0e38) atomicMin(A.lam_bits, (unsigned long long)__double_as_longlong(v));
     }
     if (bad) atomicExch(A.status, kStatusNonFinite);
   }
@@ -1539,6 +1543,136 @@ __global__ void k_indicator(int nL, int n, const Real* __restrict__ U, unsigned 
   const double g = N > 1 ? 2.0 * sqrt((double)g2) / (double)k0 : 0.0;
   if (g >= 0.0) atomicMax(&gmax[b], (unsigned long long)__double_as_longlong(g));
   else atomicMax(&gmax[b], 0x7FF8000000000000ull);  // NaN or a non-positive mean: flag as huge
+}
+
+// ============================================================ positivity
+// Smallest t in [0, 1] with p(ubar + t du) = eps_p: rho p / (gamma - 1) =
+// E rho - |m|^2 / 2 makes f(t) = (E(t) - eps_p/(gamma-1)) rho(t) - |m(t)|^2/2
+// a quadratic a t^2 + b t + c with f(0) = c > 0 > f(1).
+template <int D, typename Real>
+__device__ __forceinline__ Real pressure_root(const Real (&ub)[D + 2], const Real (&du)[D + 2], Real eps_p,
+                                              Real gm1) {
+  const Real Eb = ub[D + 1] - eps_p / gm1;
+  Real a = du[D + 1] * du[0], b = Eb * du[0] + du[D + 1] * ub[0], c = Eb * ub[0];
+#pragma unroll
+  for (int j = 1; j <= D; ++j) {
+    a -= Real(0.5) * du[j] * du[j];
+    b -= ub[j] * du[j];
+    c -= Real(0.5) * ub[j] * ub[j];
+  }
+  if (fabs(a) < Real(1e-30)) {
+    const Real t = -c / b;
+    return t < Real(0) ? Real(0) : (t > Real(1) ? Real(1) : t);
+  }
+  Real disc = b * b - Real(4) * a * c;
+  disc = disc > Real(0) ? sqrt(disc) : Real(0);
+  const Real r0 = (-b - disc) / (Real(2) * a), r1 = (-b + disc) / (Real(2) * a);
+  Real t = Real(2);
+  if (r0 >= Real(0) && r0 <= Real(1)) t = r0;
+  if (r1 >= Real(0) && r1 <= Real(1) && r1 < t) t = r1;
+  return t > Real(1) ? Real(0) : t;
+}
+
+// Positivity-preserving scaling (reading R17: Zhang & Shu): per cell, the
+// J-weighted mean ubar; theta_1 brings the density to >= eps rho_bar and
+// theta_2 the pressure to >= eps p(ubar) at every volume and face Gauss
+// point; the cell becomes ubar + theta_1 theta_2 (u - ubar) (only written
+// when limited).  A cell whose mean is not admissible sets the status word.
+// One thread per (leaf, cell).
+template <int D, int P, typename Real>
+__global__ void k_limit(int nL, int n, Real* __restrict__ U, const Real* __restrict__ geo,
+                        const unsigned char* __restrict__ affine, Real gamma, Real eps, int* status,
+                        Tab<P + 1, Real> T) {
+  constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
+  constexpr int NG = ((1 << D) - 1) * D;
+  const int nc = D == 3 ? n * n * n : n * n;
+  const size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= (size_t)nL * nc) return;
+  const int b = (int)(w / nc), c = (int)(w % nc);
+  Real* u = U + (size_t)b * NV * Q * nc + c;
+  const Real gm1 = gamma - Real(1);
+  // J-weighted mean
+  Real ub[NV], wsum = Real(0);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) ub[v] = Real(0);
+  const bool aff = affine[b] != 0;
+  for (int q = 0; q < Q; ++q) {
+    Real xi[D], wq = Real(1);
+    for (int a = 0, r = q; a < D; ++a, r /= N) {
+      xi[a] = T.x[r % N];
+      wq *= T.w[r % N];
+    }
+    if (!aff) {
+      Real t[D][D];
+      tangents<D, Real>(geo + (size_t)b * NG * nc + c, nc, xi, t);
+      wq *= jacobian_det<D, Real>(t);
+    }
+    wsum += wq;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) ub[v] += wq * u[((size_t)v * Q + q) * nc];
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) ub[v] /= wsum;
+  Real ke = Real(0);
+#pragma unroll
+  for (int j = 1; j <= D; ++j) ke += ub[j] * ub[j];
+  const Real pb = gm1 * (ub[D + 1] - Real(0.5) * ke / ub[0]);
+  if (!(ub[0] > Real(0) && pb > Real(0))) {
+    atomicExch(status, -4);
+    return;
+  }
+  const Real eps_r = eps * ub[0], eps_p = eps * pb;
+  // check point k: volume point k < Q, else face point (k - Q) of face f
+  auto point = [&](int k, Real (&x)[NV]) {
+    if (k < Q) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) x[v] = u[((size_t)v * Q + k) * nc];
+      return;
+    }
+    const int f = (k - Q) / NFP, fp = (k - Q) % NFP, a = f >> 1, s = f & 1;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      Real acc = Real(0);
+#pragma unroll
+      for (int qn = 0; qn < N; ++qn)
+        acc += (s ? T.lp[qn] : T.lm[qn]) * u[((size_t)v * Q + face_point_index<D, N>(a, fp, qn)) * nc];
+      x[v] = acc;
+    }
+  };
+  constexpr int NCHK = Q + 2 * D * NFP;
+  Real rmin = ub[0];
+  for (int k = 0; k < NCHK; ++k) {
+    Real x[NV];
+    point(k, x);
+    rmin = x[0] < rmin ? x[0] : rmin;
+  }
+  const Real th1 = rmin >= eps_r ? Real(1) : fmin(Real(1), (ub[0] - eps_r) / (ub[0] - rmin));
+  Real th2 = Real(1);
+  for (int k = 0; k < NCHK; ++k) {
+    Real x[NV], du[NV];
+    point(k, x);
+    Real kx = Real(0);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      du[v] = th1 * (x[v] - ub[v]);
+      x[v] = ub[v] + du[v];
+    }
+#pragma unroll
+    for (int j = 1; j <= D; ++j) kx += x[j] * x[j];
+    const Real p = gm1 * (x[D + 1] - Real(0.5) * kx / x[0]);
+    if (p < eps_p) {
+      const Real t = pressure_root<D, Real>(ub, du, eps_p, gm1);
+      th2 = t < th2 ? t : th2;
+    }
+  }
+  const Real theta = th1 * th2;
+  if (!(theta < Real(1))) return;
+  for (int q = 0; q < Q; ++q)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      Real& x = u[((size_t)v * Q + q) * nc];
+      x = ub[v] + theta * (x - ub[v]);
+    }
 }
 
 // State transfer after a regrid (Sec. 3.4): new leaf i copies an old leaf,

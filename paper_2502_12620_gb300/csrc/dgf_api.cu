@@ -136,6 +136,7 @@ struct dgf_forest {
   bool mortar = false;
   Buf fluxmask, mfine, mcoarse, mw, msrc;
   int nmf = 0, nmc = 0;
+  double limiter = 0.0;  // positivity limiter bound (relative); 0 = off
   int slots = 0;
   bool have_state = false;
   bool graph_valid = false;
@@ -750,6 +751,16 @@ cudaError_t do_indicator(dgf_forest* f, const RtMisc& r) {
   if (f->d == 2) return state_f64(f) ? launch_indicator<2, double>(r, f->stream) : launch_indicator<2, float>(r, f->stream);
   return state_f64(f) ? launch_indicator<3, double>(r, f->stream) : launch_indicator<3, float>(r, f->stream);
 }
+// the limiter runs on a compute-precision stage buffer
+cudaError_t do_limit(dgf_forest* f, void* buf) {
+  RtMisc r = misc_args(f, 0);
+  r.Uout = buf;
+  r.geo = f->geo.ptr;
+  r.affine = (const unsigned char*)f->affine.ptr;
+  r.eps = f->limiter;
+  if (f->d == 2) return f->precision == DGF_FP64 ? launch_limit<2, double>(r, f->stream) : launch_limit<2, float>(r, f->stream);
+  return f->precision == DGF_FP64 ? launch_limit<3, double>(r, f->stream) : launch_limit<3, float>(r, f->stream);
+}
 cudaError_t do_transfer(dgf_forest* f, const RtTransfer& r) {
   if (f->d == 2) return state_f64(f) ? launch_transfer<2, double>(r, f->stream) : launch_transfer<2, float>(r, f->stream);
   return state_f64(f) ? launch_transfer<3, double>(r, f->stream) : launch_transfer<3, float>(r, f->stream);
@@ -872,6 +883,7 @@ dgf_status enqueue_step(dgf_forest* f) {
     if ((st = rec(1, [&]() { return do_guard(f, guard_args(f, src[k], f->gtr.ptr, 1)); }))) return st;
     if ((st = rec(2, [&]() { return do_stage(f, stage_args(f, src[k], dst[k], ca[k], cb[k], 0, k == 2)); })))
       return st;
+    if (f->limiter > 0.0 && (st = rec(1, [&]() { return do_limit(f, f->U[dst[k]].ptr); }))) return st;
   }
   return DGF_OK;
 }
@@ -1395,6 +1407,30 @@ dgf_status dgf_tuning(const dgf_forest* f, int32_t* zchunk, int32_t* resident_ct
   if (zchunk) *zchunk = f->zchunk;
   if (resident_ctas) *resident_ctas = f->slots;
   return DGF_OK;
+}
+
+dgf_status dgf_set_limiter(dgf_forest* f, double eps) {
+  if (dgf_status st = require_device(f)) return st;
+  if (f->comp && eps > 0.0) return fail(DGF_EUNSUPPORTED, "the limiter is not available for DGF_FP32_COMP");
+  if (!(eps >= 0.0 && eps < 1.0)) return fail(DGF_EINVAL, "eps must be in [0, 1)");
+  DeviceGuard dg(f->device);
+  cudaStreamSynchronize(f->stream);
+  f->limiter = eps;
+  if (f->graph) cudaGraphExecDestroy(f->graph);
+  if (f->graph_alt) cudaGraphExecDestroy(f->graph_alt);
+  f->graph = f->graph_alt = nullptr;
+  f->graph_valid = false;
+  return DGF_OK;
+}
+
+dgf_status dgf_limit(dgf_forest* f) {
+  if (dgf_status st = require_device(f)) return st;
+  if (!f->have_state) return fail(DGF_ESTATE, "no state set");
+  if (!(f->limiter > 0.0)) return fail(DGF_ESTATE, "no limiter set (dgf_set_limiter)");
+  DeviceGuard dg(f->device);
+  dgf_status st = cuda_check(do_limit(f, f->U[0].ptr), "limit");
+  if (st) return st;
+  return init_lambda(f);
 }
 
 dgf_status dgf_set_timing(dgf_forest* f, int on) {

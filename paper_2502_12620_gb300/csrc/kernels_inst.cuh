@@ -283,6 +283,18 @@ static cudaError_t indicator_p(const RtMisc& r, cudaStream_t s) {
 }
 
 template <int D, int P, typename Real>
+static cudaError_t limit_p(const RtMisc& r, cudaStream_t s) {
+  const int nc = D == 3 ? r.n * r.n * r.n : r.n * r.n;
+  const size_t total = (size_t)r.nL * nc;
+  const int th = 128;
+  if (total == 0) return cudaSuccess;
+  k_limit<D, P, Real><<<(unsigned)((total + th - 1) / th), th, 0, s>>>(
+      r.nL, r.n, (Real*)r.Uout, (const Real*)r.geo, r.affine, (Real)r.gamma, (Real)r.eps, r.status,
+      make_tab<P + 1, Real>(r.T));
+  return cudaGetLastError();
+}
+
+template <int D, int P, typename Real>
 static cudaError_t transfer_p(const RtTransfer& r, cudaStream_t s) {
   const int nc = D == 3 ? r.n * r.n * r.n : r.n * r.n;
   const size_t total = (size_t)r.nL * (D + 2) * nc;
@@ -348,6 +360,12 @@ static cudaError_t convert_p(size_t outer, int inner, void* X, int to_nodal, con
     constexpr int D = DIM;                                                                  \
     using Real = REAL;                                                                      \
     DGF_DISPATCH_P(indicator_p, r, s)                                                       \
+  }                                                                                         \
+  template <>                                                                               \
+  cudaError_t launch_limit<DIM, REAL>(const RtMisc& r, cudaStream_t s) {                    \
+    constexpr int D = DIM;                                                                  \
+    using Real = REAL;                                                                      \
+    DGF_DISPATCH_P(limit_p, r, s)                                                           \
   }                                                                                         \
   template <>                                                                               \
   cudaError_t launch_transfer<DIM, REAL>(const RtTransfer& r, cudaStream_t s) {             \

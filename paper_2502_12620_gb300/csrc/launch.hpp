@@ -94,6 +94,9 @@ struct RtMisc {
   unsigned long long* lam_bits;
   int* status;
   unsigned long long* gmax;  // refinement indicator per leaf (double bits)
+  const void* geo;           // limiter: trilinear coefficients (compute precision)
+  const unsigned char* affine;
+  double eps;                // limiter bound, relative to the cell mean
   RtTables T;
 };
 
@@ -111,6 +114,8 @@ template <int D, typename Real>
 cudaError_t launch_totals(const RtMisc& r, cudaStream_t s);
 template <int D, typename Real>
 cudaError_t launch_indicator(const RtMisc& r, cudaStream_t s);
+template <int D, typename Real>
+cudaError_t launch_limit(const RtMisc& r, cudaStream_t s);
 template <int D, typename Real>
 cudaError_t launch_transfer(const RtTransfer& r, cudaStream_t s);
 // modal <-> nodal in place on [outer][var][mode/point][inner]
