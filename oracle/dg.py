@@ -406,7 +406,7 @@ class Solver:
         return self.cfl * best
 
     def _limit(self, U):
-        if self.limiter is None:
+        if getattr(self, "limiter", None) is None:
             return U
         from .limiter import positivity_limit
         return positivity_limit(self, U, self.limiter)[0]
