@@ -38,6 +38,10 @@ import workloads as W  # noqa: E402
 
 WORKLOAD = "3d-euler-jittered-cube-8roots-71leaves-n8-p2"
 HBM_FALLBACK = 6800.0
+# DRAM bytes (read + write) per k_stage launch of this workload, averaged over
+# the three stages of one time step, from the ncu capture summarised in
+# profiles/k_stage_jitter3d_p2_fp32.md; set to None when the kernel changes.
+STAGE_TRAFFIC_BYTES = 47.93e6
 
 
 def peaks():
@@ -272,7 +276,10 @@ def run_ours(args):
     alg_bytes = state_bytes_avg + geo_bytes
     achieved = alg_bytes / (stage_ms / stage_n / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": "k_stage<3,2,float>",
+            "frac": achieved / pk["hbm_gbs"],
+            "traffic": STAGE_TRAFFIC_BYTES if _SEL[0] == "jitter3d" else None,
+            "traffic_source": "profiles/k_stage_jitter3d_p2_fp32.md (ncu, cold L2, mean of 3 stages)",
+            "kernel": "k_stage<3,2,8,float>",
             "bytes_per_launch": alg_bytes, "avg_launch_us": 1e3 * stage_ms / stage_n,
             "peak_source": pk_kind,
             "other_kernels_us_per_step": {"guard": 1e3 * kt["guard"][0] / args.steps,
