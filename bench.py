@@ -278,7 +278,8 @@ def run_ours(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"],
             "traffic": STAGE_TRAFFIC_BYTES if _SEL[0] == "jitter3d" else None,
-            "traffic_source": "profiles/k_stage_jitter3d_p2_fp32.md (ncu, cold L2, mean of 3 stages)",
+            "traffic_source": ("profiles/k_stage_jitter3d_p2_fp32.md (ncu, cold L2, mean of 3 stages)"
+                               if _SEL[0] == "jitter3d" else None),
             "kernel": "k_stage<3,2,8,float>",
             "bytes_per_launch": alg_bytes, "avg_launch_us": 1e3 * stage_ms / stage_n,
             "peak_source": pk_kind,
@@ -345,7 +346,7 @@ def run_ours(args):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "leaves": nL, "cells": nL * nc, "p": p, "dof": dof,
+        "config": {"workload": WORKLOADS[_SEL[0]][0], "leaves": nL, "cells": nL * nc, "p": p, "dof": dof,
                    "precision": "fp32", "l2_flush": "256 MiB write before every timed step",
                    "parallelism": f"replicas x{ws}"},
         "roofline": roof,
