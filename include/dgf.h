@@ -270,6 +270,8 @@ dgf_status dgf_kernel_times(dgf_forest* f, double* ms, int64_t* launches, int n_
  * u(q) = sum_m K_m phi_m(x_q) (forest element type).
  *   U_nodal  device, input state, read only;
  *   L_nodal  device, output, must not alias U_nodal.
+ * Both must be 16-byte aligned (the kernels move 16-byte vectors);
+ * DGF_EINVAL otherwise.
  * The guard traces go to a 16 MiB array compiled into the library (a
  * file-scope __device__ array; every GPU that loads the library holds it
  * until the process exits).  Forests whose guard traces need more than

@@ -196,6 +196,29 @@ __device__ __forceinline__ void lf_flux(const Real (&uL)[D + 2], const Real (&uR
   for (int v = 0; v < D + 2; ++v) Fh[v] = Real(0.5) * (FL[v] + FR[v] + alpha * (uL[v] - uR[v]));
 }
 
+// 16-byte vector <-> array of VEC elements (float4: 4 floats, double2: 2 doubles)
+template <int VEC, typename V, typename Real>
+__device__ __forceinline__ void vload(const V* p, Real (&a)[VEC]) {
+  const V x = *p;
+  a[0] = x.x;
+  a[1] = x.y;
+  if constexpr (VEC == 4) {
+    a[2] = x.z;
+    a[3] = x.w;
+  }
+}
+template <int VEC, typename V, typename Real>
+__device__ __forceinline__ void vstore(V* p, const Real (&a)[VEC]) {
+  V x;
+  x.x = a[0];
+  x.y = a[1];
+  if constexpr (VEC == 4) {
+    x.z = a[2];
+    x.w = a[3];
+  }
+  *p = x;
+}
+
 // ------------------------------------------------------------ kernel args
 template <int D, int P, typename Real>
 struct StageArgs {
@@ -846,6 +869,7 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
       }
 
       // ------------------------------------------- P6: SSP-RK combination (+ CFL)
+      if constexpr (COMP) {
       for (int w = tid; w < NCL * Q; w += nthr) {
         const int c = w % NCL, q = w / NCL;
         Real o[NV];
@@ -891,6 +915,61 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
             const Real lam = sv + Real(D) * sqrt(gamma * pr * ri);
             const Real hv = A.hcell[(size_t)b * nc + cbase + c] / lam;
             lam_min = hv < lam_min ? hv : lam_min;
+          }
+        }
+      }
+      } else {
+        // VEC consecutive cells per thread: 16-byte shared and global accesses
+        constexpr int VEC = 16 / sizeof(Real);
+        using V = typename std::conditional<sizeof(Real) == 4, float4, double2>::type;
+        constexpr int NCV = NCL / VEC;
+        for (int w = tid; w < NCV * Q; w += nthr) {
+          const int c0 = (w % NCV) * VEC, q = w / NCV;
+          Real o[NV][VEC];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const size_t gi = ((size_t)v * Q + q) * nc + cbase + c0;
+            Real r[VEC], val[VEC];
+            vload<VEC>(reinterpret_cast<const V*>(&RS(v, q, c0)), r);
+            if (A.mode == 1) {
+#pragma unroll
+              for (int e = 0; e < VEC; ++e) val[e] = r[e];
+            } else {
+              Real u[VEC];
+              vload<VEC>(reinterpret_cast<const V*>(&US(v, q, c0)), u);
+#pragma unroll
+              for (int e = 0; e < VEC; ++e) val[e] = A.cb * (u[e] + dt * r[e]);
+              if (A.ca != Real(0)) {
+                Real un[VEC];
+                const V x = __ldcg(reinterpret_cast<const V*>(&Unb[gi]));
+                vload<VEC>(&x, un);
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) val[e] += A.ca * un[e];
+              }
+            }
+            vstore<VEC>(reinterpret_cast<V*>(&Ob[gi]), val);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) o[v][e] = val[e];
+          }
+          if (A.last) {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+              const Real ri = Real(1) / o[0][e];
+              Real ke = Real(0), sv = Real(0);
+#pragma unroll
+              for (int jj = 0; jj < D; ++jj) {
+                ke += o[1 + jj][e] * o[1 + jj][e];
+                sv += fabs(o[1 + jj][e]) * ri;
+              }
+              const Real pr = gm1 * (o[D + 1][e] - Real(0.5) * ke * ri);
+              if (!(o[0][e] > Real(0)) || !(pr > Real(0)) || !(pr < Real(3.0e38))) {
+                bad = true;
+              } else {
+                const Real lam = sv + Real(D) * sqrt(gamma * pr * ri);
+                const Real hv = A.hcell[(size_t)b * nc + cbase + c0 + e] / lam;
+                lam_min = hv < lam_min ? hv : lam_min;
+              }
+            }
           }
         }
       }

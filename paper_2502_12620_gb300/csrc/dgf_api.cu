@@ -1721,6 +1721,8 @@ extern "C" dgf_status dgf_dg_residual_noalloc(dgf_forest* f, const void* U_nodal
   if (dgf_status st = require_device(f)) return st;
   if (!U_nodal || !L_nodal) return fail(DGF_EINVAL, "null state pointer");
   if (U_nodal == L_nodal) return fail(DGF_EINVAL, "input and output must not alias");
+  if (((uintptr_t)U_nodal | (uintptr_t)L_nodal) & 15)
+    return fail(DGF_EINVAL, "state pointers must be 16-byte aligned");
   if (f->comp) return fail(DGF_EUNSUPPORTED, "dgf_dg_residual_noalloc: compensated forests are not supported");
   DeviceGuard dg(f->device);
   const size_t need = (size_t)f->nL * 2 * f->d * f->nv * f->NFP * f->nt * f->esize;
