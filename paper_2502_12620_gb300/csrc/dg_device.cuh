@@ -295,9 +295,9 @@ struct GuardArgs {
 };
 
 // threads per CTA and CTAs per SM of the stage kernel (registers and shared
-// memory decide: FP32 up to p=2 runs 2 x 512 threads per SM)
+// memory decide: FP32 up to p=2 runs 2 x 448 threads per SM, 73 registers)
 #ifndef DGF_STAGE_NT_F32
-#define DGF_STAGE_NT_F32 512
+#define DGF_STAGE_NT_F32 448
 #endif
 template <int P, typename Real>
 struct StageCfg {
