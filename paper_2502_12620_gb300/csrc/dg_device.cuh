@@ -308,14 +308,24 @@ struct StageCfg {
 // shared-memory footprint of the stage kernel (bytes): nodal layer, residual
 // layer, x- and y-face fluxes, carried z-face flux
 template <int D, int P, typename Real>
-__host__ __device__ constexpr size_t stage_smem(int n) {
+__host__ __device__ constexpr size_t stage_smem(int n, int rows) {
   constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
-  const size_t ncl = (size_t)n * n;
+  const size_t ncl = (size_t)n * rows;
   size_t us = NV * Q * ncl;
   size_t rs = us;
-  size_t fx = (size_t)NV * NFP * (n + 1) * n, fy = fx;
+  size_t fx = (size_t)NV * NFP * (n + 1) * rows, fy = (size_t)NV * NFP * (rows + 1) * n;
   size_t fz = D == 3 ? (size_t)NV * NFP * ncl : 0;
   return (us + rs + fx + fy + fz) * sizeof(Real);
+}
+
+// rows of a layer one work item sweeps: the whole layer when its buffers fit
+// the 227 KB of shared memory a CTA may use, else a slab of n/2, n/4, ...
+// rows (FP64 at p = 3 with n = 8)
+template <int D, int P, typename Real>
+__host__ __device__ constexpr int stage_rows(int n) {
+  int r = n;
+  while (r > 1 && stage_smem<D, P, Real>(n, r) + 2048 > 232448) r /= 2;
+  return r;
 }
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -436,16 +446,21 @@ __device__ __forceinline__ int face_point_index(int ax, int fp, int qn) {
 // (each face once); x volume + lift; y volume + lift (and the halo trace of
 // the next layer); z volume + z faces (carried between layers) and 1/J;
 // SSP-RK combination point by point, with the CFL minimum on the last stage.
-template <int D, int P, int NS, typename Real, bool COMP = false, bool MORTAR = false>
+template <int D, int P, int NS, typename Real, bool COMP = false, bool MORTAR = false,
+          int YS = stage_rows<D, P, Real>(NS)>
 __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB)
     k_stage(const StageArgs<D, P, Real> A) {
   constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
   constexpr int NG = ((1 << D) - 1) * D;
   constexpr int n = NS;
-  constexpr int NCL = n * n;
-  constexpr int nc = D == 3 ? NCL * n : NCL;
+  constexpr int YR = YS;                 // rows of the layer one item sweeps (a slab)
+  constexpr int NYS = n / YR;            // slabs per layer
+  constexpr int LAY = n * n;             // cells of a layer (of the block in 2D)
+  constexpr int NCL = n * YR;            // cells of a slab
+  constexpr int nc = D == 3 ? LAY * n : LAY;
   constexpr int nt = D == 3 ? n * n : n;  // guard cells per face
-  constexpr int NF = (n + 1) * n * NFP;   // faces of one direction in a layer
+  constexpr int NFX = (n + 1) * YR * NFP;  // x faces of a slab
+  constexpr int NFY = (YR + 1) * n * NFP;  // y faces of a slab
   const auto& T = A.T;
   const Real gamma = A.gamma;
   const Real gm1 = gamma - Real(1);
@@ -472,27 +487,28 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
   Real* us = reinterpret_cast<Real*>(smem_raw);
   Real* rs = us + NV * Q * NCL;
   Real* fx = rs + RSZ;
-  Real* fy = fx + NV * NFP * (n + 1) * n;
-  Real* fz = fy + NV * NFP * (n + 1) * n;
+  Real* fy = fx + NV * NFP * (n + 1) * YR;
+  Real* fz = fy + NV * NFP * (YR + 1) * n;
   Real* tb = fx;   // halo traces reuse the x-face buffer when it is free
   if (tid < N) sx[tid] = T.x[tid];
 
   Real lam_min = Real(3.0e38);
   bool bad = false;
-  const int items = A.nL * A.nchunks;
+  const int items = A.nL * A.nchunks * NYS;
 
 #define US(v, q, c) us[((v) * Q + (q)) * NCL + (c)]
 #define RS(v, q, c) rs[((v) * Q + (q)) * NCL + (c)]
 // x faces: [v][fp][row j][face fi]; y faces: [v][fp][face fi][column i]
-#define FX(v, fp, j, fi) fx[(((v) * NFP + (fp)) * n + (j)) * (n + 1) + (fi)]
-#define FY(v, fp, fi, i) fy[(((v) * NFP + (fp)) * (n + 1) + (fi)) * n + (i)]
+#define FX(v, fp, j, fi) fx[(((v) * NFP + (fp)) * YR + (j)) * (n + 1) + (fi)]
+#define FY(v, fp, fi, i) fy[(((v) * NFP + (fp)) * (YR + 1) + (fi)) * n + (i)]
 #define TB(v, fp, c) tb[((v) * NFP + (fp)) * NCL + (c)]
 #define FZ(v, fp, c) fz[((v) * NFP + (fp)) * NCL + (c)]
 #define GTR(f, v, fp, t) Tb[(((size_t)(f) * NV + (v)) * NFP + (fp)) * nt + (t)]
 
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    const int b = item / A.nchunks;
-    const int chunk = item - b * A.nchunks;
+    const int b = item / (A.nchunks * NYS);
+    const int chunk = (item / NYS) % A.nchunks;
+    const int j0 = NYS == 1 ? 0 : (item % NYS) * YR;  // first row of the slab
     const int k0 = D == 3 ? chunk * A.zchunk : 0;
     const int k1 = D == 3 ? min(n, k0 + A.zchunk) : 1;
     const Real* __restrict__ Ub = A.U + (size_t)b * NV * Q * nc;
@@ -509,8 +525,8 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
     if (aff && tid < D * D + 1) sam[tid] = A.ameta[(size_t)b * (D * D + 1) + tid];
 
     for (int k = k0; k < k1; ++k) {
-      const int cbase = D == 3 ? k * NCL : 0;
-      const Real* __restrict__ Gk = Gb + cbase;  // geometry of this layer, stride nc
+      const int cbase = (D == 3 ? k * LAY : 0) + j0 * n;  // first cell of the slab
+      const Real* __restrict__ Gk = Gb + cbase;  // geometry of this slab, stride nc
       // ------------------------------------------- L2 prefetch of what comes next
       {
         constexpr int lpr = (NCL * (int)sizeof(Real) + 127) / 128;
@@ -518,11 +534,11 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
           const int r = w / lpr, l = w - r * lpr;
           if constexpr (COMP) {
             if (D == 3 && k + 1 < n) {
-              prefetch_l2(Sb.u64 + (size_t)r * nc + (k + 1) * NCL + l * (128 / sizeof(Real)) / 2);
-              prefetch_l2(Sb.u64 + (size_t)r * nc + (k + 1) * NCL + l * (128 / sizeof(Real)) / 2 + 16);
+              prefetch_l2(Sb.u64 + (size_t)r * nc + cbase + LAY + l * (128 / sizeof(Real)) / 2);
+              prefetch_l2(Sb.u64 + (size_t)r * nc + cbase + LAY + l * (128 / sizeof(Real)) / 2 + 16);
             }
           } else {
-            if (D == 3 && k + 1 < n) prefetch_l2(Ub + (size_t)r * nc + (k + 1) * NCL + l * (128 / sizeof(Real)));
+            if (D == 3 && k + 1 < n) prefetch_l2(Ub + (size_t)r * nc + cbase + LAY + l * (128 / sizeof(Real)));
             if (A.mode == 0 && A.ca != Real(0)) prefetch_l2(Unb + (size_t)r * nc + cbase + l * (128 / sizeof(Real)));
           }
         }
@@ -552,12 +568,12 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
             const int c = w % NCL, fp = (w / NCL) % NFP, v = w / (NCL * NFP);
             Real tr;
             if (k0 == 0) {
-              tr = GTR(4, v, fp, c);
+              tr = GTR(4, v, fp, j0 * n + c);
             } else {
               tr = Real(0);
 #pragma unroll
               for (int qz = 0; qz < N; ++qz)
-                tr += T.lp[qz] * Sb(((size_t)v * Q + fp + NFP * qz) * nc + (k0 - 1) * NCL + c);
+                tr += T.lp[qz] * Sb(((size_t)v * Q + fp + NFP * qz) * nc + cbase - LAY + c);
             }
             TB(v, fp, c) = tr;
           }
@@ -591,7 +607,7 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
               // depend on the chunk length
               const Real xi[3] = {sx[fp % N], sx[fp / N], Real(0)};
               LineGeo<3, 2, Real> lg;
-              lg.init(Gk - NCL + c, nc, xi);
+              lg.init(Gk - LAY + c, nc, xi);
               lg.at(Real(1), Ja);
             }
             lf_flux<3, Real>(uL, uR, Ja, gamma, Fh);
@@ -603,24 +619,25 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
       __syncthreads();
 
       // ------------------------------------------- P2: x and y face fluxes
-      for (int w = tid; w < 2 * NF; w += nthr) {
-        const bool ydir = w >= NF;
-        const int ww = ydir ? w - NF : w;
+      for (int w = tid; w < NFX + NFY; w += nthr) {
+        const bool ydir = w >= NFX;
+        const int ww = ydir ? w - NFX : w;
         Real uL[NV], uR[NV], Ja[D], Fh[NV];
         if (!ydir) {
           const int fi = ww % (n + 1);
-          const int j = (ww / (n + 1)) % n;
-          const int fp = ww / ((n + 1) * n);
+          const int j = (ww / (n + 1)) % YR;
+          const int fp = ww / ((n + 1) * YR);
           const int cl = (fi - 1) + n * j, cr = fi + n * j;
+          const int tg = D == 3 ? j0 + j + n * k : j0 + j;  // guard cell of this row
           if ((fi == 0 && (fmask & 1)) || (fi == n && (fmask & 2))) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) FX(v, fp, j, fi) = GTR(fi == 0 ? 0 : 1, v, fp, D == 3 ? j + n * k : j);
+            for (int v = 0; v < NV; ++v) FX(v, fp, j, fi) = GTR(fi == 0 ? 0 : 1, v, fp, tg);
             continue;
           }
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             if (fi == 0) {
-              uL[v] = GTR(0, v, fp, D == 3 ? j + n * k : j);
+              uL[v] = GTR(0, v, fp, tg);
             } else {
               Real s = Real(0);
 #pragma unroll
@@ -628,7 +645,7 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
               uL[v] = s;
             }
             if (fi == n) {
-              uR[v] = GTR(1, v, fp, D == 3 ? j + n * k : j);
+              uR[v] = GTR(1, v, fp, tg);
             } else {
               Real s = Real(0);
 #pragma unroll
@@ -651,27 +668,43 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
           for (int v = 0; v < NV; ++v) FX(v, fp, j, fi) = Fh[v];
         } else {
           const int i = ww % n;
-          const int fi = (ww / n) % (n + 1);
-          const int fp = ww / ((n + 1) * n);  // qx + N qz
+          const int fi = (ww / n) % (YR + 1);
+          const int fp = ww / ((YR + 1) * n);  // qx + N qz
           const int qx = fp % N, qz = fp / N;
           const int cl = i + n * (fi - 1), cr = i + n * fi;
-          if ((fi == 0 && (fmask & 4)) || (fi == n && (fmask & 8))) {
+          const int tg = D == 3 ? i + n * k : i;
+          // block faces at the first and last row; a slab's other edge rows
+          // take the neighbouring row's trace from the stage input in memory
+          const bool bot = fi == 0 && j0 == 0, top = fi == YR && j0 + YR == n;
+          if ((bot && (fmask & 4)) || (top && (fmask & 8))) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) FY(v, fp, fi, i) = GTR(fi == 0 ? 2 : 3, v, fp, D == 3 ? i + n * k : i);
+            for (int v = 0; v < NV; ++v) FY(v, fp, fi, i) = GTR(bot ? 2 : 3, v, fp, tg);
             continue;
           }
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
-            if (fi == 0) {
-              uL[v] = GTR(2, v, fp, D == 3 ? i + n * k : i);
+            if (bot) {
+              uL[v] = GTR(2, v, fp, tg);
+            } else if (fi == 0) {
+              Real s = Real(0);
+#pragma unroll
+              for (int qy = 0; qy < N; ++qy)
+                s += T.lp[qy] * Sb(((size_t)v * Q + qx + N * qy + N * N * qz) * nc + cbase + cl);
+              uL[v] = s;
             } else {
               Real s = Real(0);
 #pragma unroll
               for (int qy = 0; qy < N; ++qy) s += T.lp[qy] * US(v, qx + N * qy + N * N * qz, cl);
               uL[v] = s;
             }
-            if (fi == n) {
-              uR[v] = GTR(3, v, fp, D == 3 ? i + n * k : i);
+            if (top) {
+              uR[v] = GTR(3, v, fp, tg);
+            } else if (fi == YR) {
+              Real s = Real(0);
+#pragma unroll
+              for (int qy = 0; qy < N; ++qy)
+                s += T.lm[qy] * Sb(((size_t)v * Q + qx + N * qy + N * N * qz) * nc + cbase + cr);
+              uR[v] = s;
             } else {
               Real s = Real(0);
 #pragma unroll
@@ -685,9 +718,9 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
           } else {
             Real xi[D];
             xi[0] = sx[qx];
-            xi[1] = fi == n ? Real(1) : Real(-1);
+            xi[1] = top ? Real(1) : Real(-1);
             if constexpr (D == 3) xi[2] = sx[qz];
-            point_row<D, Real>(Gk + (fi == n ? cl : cr), nc, xi, 1, Ja);
+            point_row<D, Real>(Gk + (top ? cl : cr), nc, xi, 1, Ja);
           }
           lf_flux<D, Real>(uL, uR, Ja, gamma, Fh);
 #pragma unroll
@@ -790,12 +823,12 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
           const int c = ww % NCL, fp = (ww / NCL) % NFP, v = ww / (NCL * NFP);
           Real tr;
           if (k == n - 1) {
-            tr = GTR(5, v, fp, c);
+            tr = GTR(5, v, fp, j0 * n + c);
           } else {
             tr = Real(0);
 #pragma unroll
             for (int qz = 0; qz < N; ++qz)
-              tr += T.lm[qz] * Sb(((size_t)v * Q + fp + NFP * qz) * nc + (k + 1) * NCL + c);
+              tr += T.lm[qz] * Sb(((size_t)v * Q + fp + NFP * qz) * nc + cbase + LAY + c);
           }
           TB(v, fp, c) = tr;
         }

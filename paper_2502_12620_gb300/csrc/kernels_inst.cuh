@@ -75,7 +75,7 @@ bool stage_mortar_prepare(size_t smem);
 
 template <int D, int P, int NS, typename Real>
 static int stage_blocks_per_sm_ns() {
-  const size_t smem = stage_smem<D, P, Real>(NS);
+  const size_t smem = stage_smem<D, P, Real>(NS, stage_rows<D, P, Real>(NS));
   int dev = 0, maxs = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -108,8 +108,8 @@ static int stage_blocks_per_sm(int n) {
 
 template <int D, int P, int NS, typename Real>
 static cudaError_t stage_ns(const StageArgs<D, P, Real>& a, int slots, int comp, cudaStream_t s) {
-  const size_t smem = stage_smem<D, P, Real>(NS);
-  const int items = a.nL * a.nchunks;
+  const size_t smem = stage_smem<D, P, Real>(NS, stage_rows<D, P, Real>(NS));
+  const int items = a.nL * a.nchunks * (NS / stage_rows<D, P, Real>(NS));
   const int grid = items < slots ? items : slots;
   if (a.fluxmask) return stage_mortar_launch<D, P, NS, Real>(a, grid, smem, comp, s);
   if constexpr (std::is_same<Real, float>::value) {
@@ -397,10 +397,10 @@ static cudaError_t convert_p(size_t outer, int inner, void* X, int to_nodal, con
   template <>                                                                               \
   size_t stage_smem_bytes<DIM, REAL>(int p, int n) {                                        \
     switch (p) {                                                                            \
-      case 0: return stage_smem<DIM, 0, REAL>(n);                                           \
-      case 1: return stage_smem<DIM, 1, REAL>(n);                                           \
-      case 2: return stage_smem<DIM, 2, REAL>(n);                                           \
-      case 3: return stage_smem<DIM, 3, REAL>(n);                                           \
+      case 0: return stage_smem<DIM, 0, REAL>(n, stage_rows<DIM, 0, REAL>(n));                                           \
+      case 1: return stage_smem<DIM, 1, REAL>(n, stage_rows<DIM, 1, REAL>(n));                                           \
+      case 2: return stage_smem<DIM, 2, REAL>(n, stage_rows<DIM, 2, REAL>(n));                                           \
+      case 3: return stage_smem<DIM, 3, REAL>(n, stage_rows<DIM, 3, REAL>(n));                                           \
     }                                                                                       \
     return 0;                                                                               \
   }
