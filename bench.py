@@ -12,6 +12,7 @@ on the last stage).  Metric: DG DOF-updates per second per RK stage
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --serve [--serve-requests R] [--serve-active A]
+  python bench.py --amr [--steps K]          (K regrid periods of 10 steps)
 
 Timing: CUDA events on the forest's stream around each step, an L2 flush
 (256 MiB write) before every timed step, warm-up steps first, barrier and
@@ -453,6 +454,87 @@ def run_serve(args):
     return 0
 
 
+# ---------------------------------------------------------------- dynamic AMR
+AMR = dict(B=4, n_seg=8, p=1, refine_above=0.05, coarsen_below=0.01, max_level=4, every=10, limiter=1e-6)
+
+
+def run_amr(args):
+    """Blast on a periodic cube of 4^3 roots with dynamic refinement: the
+    device indicator and adaptation (2:1 closure, state moved on the device)
+    every `every` steps, the positivity limiter after every stage, FP32.
+    The rate counts the DOF updated by each time step (3 stages) over the wall
+    time of the whole run, regrids included."""
+    import torch
+    import paper_2502_12620_gb300 as pkg
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    cfg = AMR
+    w = W.periodic_cube_forest(cfg["B"], n_seg=cfg["n_seg"])
+    width = 1.0 / (cfg["B"] * cfg["n_seg"] * 2 ** (cfg["max_level"] - 1))
+    ic = lambda x: W.blast(x, (0.5, 0.5, 0.5), r0=0.12, width=width)
+    f = pkg.Forest.from_workload(w, p=cfg["p"], precision=pkg.FP32, device=local)
+    stream = torch.cuda.Stream()
+    f.set_stream(stream)
+    f.set_limiter(cfg["limiter"])
+    # initial refinement: adapt to the projected data until it settles
+    for _ in range(cfg["max_level"]):
+        f.project(ic)
+        f.limit()
+        nr, nc = f.adapt(cfg["refine_above"], cfg["coarsen_below"], cfg["max_level"])
+        if nr == 0 and nc == 0:
+            break
+    f.project(ic)
+    f.limit()
+    f.status_word(reset=True)
+    dof_leaf = f.nv * f.M * f.nc
+    for _ in range(args.warmup):
+        f.rk_step()
+    torch.cuda.synchronize()
+    steps = args.steps * cfg["every"]
+    updates = 0
+    leaves = []
+    regrid_s = 0.0
+    changes = 0
+    with Clocks(local) as ck:
+        t0 = time.perf_counter()
+        for i in range(steps):
+            L = f.n_leaves
+            leaves.append(L)
+            f.rk_step()
+            updates += L * dof_leaf * 3
+            if (i + 1) % cfg["every"] == 0:
+                stream.synchronize()  # time the regrid alone
+                r0 = time.perf_counter()
+                nr, nc = f.adapt(cfg["refine_above"], cfg["coarsen_below"], cfg["max_level"])
+                regrid_s += time.perf_counter() - r0
+                changes += (nr > 0 or nc > 0)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    status = f.status_word()
+    value, ms = job_throughput(updates, 1e3 * wall, ws)
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "dynamic AMR: DG DOF-updates/s per RK stage, regrids included", "value": value,
+        "unit": "DOF-updates/s", "n_gpus": ws, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "3d-blast-periodic-cube-4^3-roots-n8-p1-adaptive-to-level-4", **cfg},
+        "amr": {"leaves_min": min(leaves), "leaves_max": max(leaves), "leaves_end": f.n_leaves,
+                "regrids": steps // cfg["every"], "regrids_that_changed_the_forest": changes,
+                "regrid_s": regrid_s, "regrid_ms_each": 1e3 * regrid_s / max(1, steps // cfg["every"]),
+                "wall_s": wall,
+                "status_word": status, "t_end": f.time},
+        "clocks": ck.summary(),
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -463,6 +545,7 @@ def main():
     ap.add_argument("--workload", default="jitter3d", choices=sorted(WORKLOADS))
     ap.add_argument("--quick", action="store_true", help="FP32 timed steps only (profiling runs)")
     ap.add_argument("--serve", action="store_true", help="continuous-batching run instead of the step benchmark")
+    ap.add_argument("--amr", action="store_true", help="dynamic-refinement blast run (steps = regrid periods)")
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--serve-active", type=int, default=8)
     args = ap.parse_args()
@@ -473,6 +556,8 @@ def main():
         return run_reference(args)
     if args.serve:
         return run_serve(args)
+    if args.amr:
+        return run_amr(args)
     return run_ours(args)
 
 

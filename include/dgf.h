@@ -248,8 +248,8 @@ dgf_status dgf_status_word(dgf_forest* f, int32_t* status, int reset);
  * dgf_rk_step of a 3D forest times one residual evaluation for every chunk
  * length n_seg, n_seg/2, ..., 1 and keeps the fastest; later forests of the
  * same device, dimension, degree, n_seg, precision and leaf count in the
- * process reuse that choice (the environment variable DGF_ZCHUNK fixes it
- * instead).  The chunk length changes no bit of any result.  Not a paper
+ * process reuse that choice, and a regrid keeps it (the environment variable
+ * DGF_ZCHUNK fixes it instead).  The chunk length changes no bit of any result.  Not a paper
  * quantity: the paper's per-block loop (Sec. 4.3) has no tiling. */
 dgf_status dgf_tuning(const dgf_forest* f, int32_t* zchunk, int32_t* resident_ctas);
 

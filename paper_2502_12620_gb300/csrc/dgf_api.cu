@@ -137,6 +137,7 @@ struct dgf_forest {
   Buf fluxmask, mfine, mcoarse, mw, msrc;
   int nmf = 0, nmc = 0;
   double limiter = 0.0;  // positivity limiter bound (relative); 0 = off
+  Buf ind;               // refinement indicator per leaf (kept between calls)
   int slots = 0;
   bool have_state = false;
   bool graph_valid = false;
@@ -1024,7 +1025,7 @@ dgf_status dgf_forest_destroy(dgf_forest* f) {
                                &f->gmod, &f->cop, &f->ctr, &f->kind, &f->nbr, &f->orient, &f->qbits, &f->copoff,
                                &f->part, &f->scal, &f->tot, &f->dtout, &f->nodal, &f->fine, &f->affine, &f->ameta,
                                &f->U64[0], &f->U64[1], &f->hcell64, &f->gmod64, &f->fluxmask,
-                               &f->mfine, &f->mcoarse, &f->mw, &f->msrc};
+                               &f->mfine, &f->mcoarse, &f->mw, &f->msrc, &f->ind};
     for (auto* b : bufs) dev_free(f, *b);
     if (f->own_stream && f->stream) cudaStreamDestroy(f->stream);
   }
@@ -1094,7 +1095,7 @@ static dgf_status indicator_host(dgf_forest* f, std::vector<double>& g) {
   if (!f->have_state) return fail(DGF_ESTATE, "no state set");
   DeviceGuard dg(f->device);
   const int64_t L = f->nL;
-  dgf_forest::Buf gb;
+  dgf_forest::Buf& gb = f->ind;
   if (!ensure(f, gb, sizeof(unsigned long long) * std::max<int64_t>(L, 1)))
     return fail(DGF_ENOMEM, "device allocation failed");
   dgf_status st = cuda_check(cudaMemsetAsync(gb.ptr, 0, sizeof(unsigned long long) * L, f->stream), "memset");
@@ -1103,8 +1104,6 @@ static dgf_status indicator_host(dgf_forest* f, std::vector<double>& g) {
   if (!st) st = cuda_check(do_indicator(f, r), "indicator");
   g.assign(L, 0.0);
   if (!st) st = copy_state(f, g.data(), gb.ptr, sizeof(double) * L, cudaMemcpyDeviceToHost);
-  cudaStreamSynchronize(f->stream);
-  dev_free(f, gb);
   return st;
 }
 
@@ -1521,7 +1520,13 @@ static dgf_status regrid(dgf_forest* f, const std::vector<uint64_t>& old_leaves)
   dgf_forest::Buf& live = f->comp ? f->U64[f->cur] : f->U[0];
   old = live;
   live = dgf_forest::Buf();
+  const bool was_tuned = f->tuned;
+  const int tuned_z = f->zchunk;
   dgf_status st = build_device(f);
+  if (was_tuned && f->d == 3 && !getenv("DGF_ZCHUNK")) {
+    f->tuned = true;  // a regrid keeps the chunk length (re-timing every regrid costs more)
+    f->zchunk = tuned_z;
+  }
   if (st) {
     dev_free(f, old);
     f->have_state = false;
