@@ -303,6 +303,47 @@ dgf_status build_device(dgf_forest* f) {
     F.cell_coefficients(F.leaves[i], coef[i]);
     for (int g = 0; g < NG; ++g)
       for (int c = 0; c < nc; ++c) geo64[((size_t)i * NG + g) * nc + c] = coef[i][(size_t)(d + g) * nc + c];
+  });
+
+  // affine blocks: every cell a congruent parallelogram/parallelepiped ->
+  // constant J dxi/dx rows and 1/J per block
+  std::vector<unsigned char> affine(L, 0);
+  std::vector<double> ameta((size_t)L * (d * d + 1), 0.0);
+  parallel_for(L, [&](int64_t i) {
+    const std::vector<double>& C = coef[i];
+    double scale = 0.0;
+    for (int k = d; k < (1 << d) * d; ++k)
+      for (int c = 0; c < nc; ++c) scale = std::max(scale, std::fabs(C[(size_t)k * nc + c]));
+    bool ok = scale > 0.0;
+    for (int cm = 1; cm < (1 << d) && ok; ++cm) {
+      const bool linear = (cm & (cm - 1)) == 0;
+      for (int j = 0; j < d && ok; ++j) {
+        const double* row = &C[((size_t)cm * d + j) * nc];
+        for (int c = 0; c < nc && ok; ++c) {
+          if (!linear && std::fabs(row[c]) > 1e-13 * scale) ok = false;
+          if (linear && std::fabs(row[c] - row[0]) > 1e-13 * scale) ok = false;
+        }
+      }
+    }
+    if (!ok) return;
+    double cc[24], A[9], Ja[9], xi[3] = {0, 0, 0};
+    for (int k = 0; k < (1 << d) * d; ++k) cc[k] = C[(size_t)k * nc];
+    eval_map(d, cc, xi, nullptr, A);
+    const double J = det_and_cofactor(d, A, Ja);
+    if (!(J > 0)) return;
+    affine[i] = 1;
+    for (int k = 0; k < d * d; ++k) ameta[(size_t)i * (d * d + 1) + k] = Ja[k];
+    ameta[(size_t)i * (d * d + 1) + d * d] = 1.0 / J;
+  });
+
+  // cell sizes h = (cell volume)^(1/d), the volume by the Gauss rule (an
+  // affine block's cells: J times the reference volume 2^d)
+  parallel_for(L, [&](int64_t i) {
+    if (affine[i]) {
+      const double h = std::pow((double)(1 << d) / ameta[(size_t)i * (d * d + 1) + d * d], 1.0 / d);
+      for (int c = 0; c < nc; ++c) hcell[(size_t)i * nc + c] = h;
+      return;
+    }
     for (int c = 0; c < nc; ++c) {
       double cc[8 * 3];
       for (int k = 0; k < (1 << d) * d; ++k) cc[k] = coef[i][(size_t)k * nc + c];
@@ -322,37 +363,6 @@ dgf_status build_device(dgf_forest* f) {
       hcell[(size_t)i * nc + c] = std::pow(vol, 1.0 / d);
     }
   });
-
-  // affine blocks: every cell a congruent parallelogram/parallelepiped ->
-  // constant J dxi/dx rows and 1/J per block
-  std::vector<unsigned char> affine(L, 0);
-  std::vector<double> ameta((size_t)L * (d * d + 1), 0.0);
-  for (int64_t i = 0; i < L; ++i) {
-    const std::vector<double>& C = coef[i];
-    double scale = 0.0;
-    for (int k = d; k < (1 << d) * d; ++k)
-      for (int c = 0; c < nc; ++c) scale = std::max(scale, std::fabs(C[(size_t)k * nc + c]));
-    bool ok = scale > 0.0;
-    for (int cm = 1; cm < (1 << d) && ok; ++cm) {
-      const bool linear = (cm & (cm - 1)) == 0;
-      for (int j = 0; j < d && ok; ++j) {
-        const double* row = &C[((size_t)cm * d + j) * nc];
-        for (int c = 0; c < nc && ok; ++c) {
-          if (!linear && std::fabs(row[c]) > 1e-13 * scale) ok = false;
-          if (linear && std::fabs(row[c] - row[0]) > 1e-13 * scale) ok = false;
-        }
-      }
-    }
-    if (!ok) continue;
-    double cc[24], A[9], Ja[9], xi[3] = {0, 0, 0};
-    for (int k = 0; k < (1 << d) * d; ++k) cc[k] = C[(size_t)k * nc];
-    eval_map(d, cc, xi, nullptr, A);
-    const double J = det_and_cofactor(d, A, Ja);
-    if (!(J > 0)) continue;
-    affine[i] = 1;
-    for (int k = 0; k < d * d; ++k) ameta[(size_t)i * (d * d + 1) + k] = Ja[k];
-    ameta[(size_t)i * (d * d + 1) + d * d] = 1.0 / J;
-  }
 
   // combine operators for every finer-neighbour guard cell (Eqs. (13)-(14),
   // J-weighted, integrals by each child's Gauss rule), rotated into my frame
@@ -381,7 +391,22 @@ dgf_status build_device(dgf_forest* f) {
       const int a = fc >> 1, s = fc & 1;
       const int b2 = o.pi[a];
       const int s2 = o.sg[a] > 0 ? 1 - s : s;
+      // fine neighbours that are affine blocks of one Jacobian give every
+      // guard cell of this face the same operator: build it once
+      bool uniform = true;
+      for (int sb = 0; sb < (1 << (d - 1)) && uniform; ++sb) {
+        const int64_t fl = T.nbr[(i * nf + fc) * 4 + sb];
+        const int64_t f0 = T.nbr[(i * nf + fc) * 4];
+        uniform = affine[fl] &&
+                  ameta[(size_t)fl * (d * d + 1) + d * d] == ameta[(size_t)f0 * (d * d + 1) + d * d];
+      }
       for (int t = 0; t < nt; ++t) {
+        if (uniform && t > 0) {
+          const size_t o0 = (size_t)copoff[i * nf + fc];
+          std::memcpy(&cop[(o0 + t) * M * KC], &cop[o0 * M * KC], sizeof(double) * M * KC);
+          std::memcpy(&ctr[(o0 + t) * NFPh * KC], &ctr[o0 * NFPh * KC], sizeof(double) * NFPh * KC);
+          continue;
+        }
         int g[3] = {0, 0, 0}, j = 0;
         for (int ax = 0; ax < d; ++ax) {
           if (ax == a) continue;
