@@ -48,6 +48,9 @@ design notes of the repository):
      maximum over its cells; refine above a threshold (with 2:1 closure),
      then one pass in canonical leaf order coarsening sibling groups below a
      threshold where 2:1 balance allows (``adapt.py``).
+  R11 boundaries: unmatched root faces are outflow (the guard cell mirrors
+     my face cell) unless tagged as a prescribed constant state (inflow /
+     far field).
   R17 positivity: optional scaling limiter of Zhang & Shu (2010) after every
      RK stage, toward the J-weighted cell mean, checked at the volume and
      face Gauss points (``limiter.py``).

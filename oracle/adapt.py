@@ -73,7 +73,8 @@ def adapt(S, U, refine_above, coarsen_below, max_level, g=None):
             n_coarse += 1
         except BalanceError:
             pass
-    S2 = Solver(F, S.p, gamma=S.gamma, cfl=S.cfl, nonconforming=S.nonconforming, limiter=S.limiter)
+    S2 = Solver(F, S.p, gamma=S.gamma, cfl=S.cfl, nonconforming=S.nonconforming, limiter=S.limiter,
+                boundary=S.boundary)
     return S2, None if U is None else S2.regrid_state(S, U), len(flagged), n_coarse
 
 

@@ -138,12 +138,17 @@ def _combine(ops, K_children, corners_children):
 class Solver:
     """One forest + degree p: guard fill, residual, SSP-RK3, CFL, totals."""
 
-    def __init__(self, forest, p, gamma=GAMMA, cfl=0.1, nonconforming="paper", limiter=None):
+    def __init__(self, forest, p, gamma=GAMMA, cfl=0.1, nonconforming="paper", limiter=None,
+                 boundary=None):
         """nonconforming: "paper" (the guard scheme of Sec. 3.5 on both sides
         of a level jump) or "mortar" (reading R15: the coarse side takes the
         fine side's fluxes, integrated against its own test functions).
         limiter: None, or eps of the positivity limiter (reading R17) applied
-        after every Runge-Kutta stage."""
+        after every Runge-Kutta stage.
+        boundary: None (every domain boundary face is outflow), or
+        (tags, state): tags[root][face] = 1 makes that root face's guard
+        cells the constant conserved state `state` (inflow / far field,
+        reading R11), 0 keeps outflow."""
         assert nonconforming in ("paper", "mortar")
         self.F = forest
         self.d, self.n, self.p = forest.d, forest.n, p
@@ -151,6 +156,7 @@ class Solver:
         self.gamma, self.cfl = gamma, cfl
         self.nonconforming = nonconforming
         self.limiter = limiter
+        self.boundary = boundary
         self.nv = self.d + 2
         self._rot_cache = {}
         self.refresh()
@@ -267,6 +273,10 @@ class Solver:
                 g[tt] = (t // n ** j) % n
             gs.append(g)
         nb = F.neighbour_coords(r, lev, pos, f)
+        if nb is None and self.boundary is not None and self.boundary[0][r][f] == 1:
+            # prescribed state: a constant guard cell (mode 0 only, P_0 = 1)
+            out[:, 0, :] = np.asarray(self.boundary[1], float)[:, None]
+            return out
         if nb is None:
             # outflow: mirror image of my own face cell across the face
             sign = np.array([(-1.0) ** k[a] for k in B.mode_indices(d, ops.N)])

@@ -202,3 +202,33 @@ def test_vortex_design_order(p):
         errs.append(S.l2_error(U, lambda x: W.vortex_exact(x, t)))
     order = np.log2(errs[0] / errs[1])
     assert order > p + 0.6, (errs, order)
+
+
+def test_prescribed_state_boundaries():
+    """A free stream stays exact when the tagged boundary faces prescribe that
+    same state (jittered, refined, non-periodic forest); a different
+    prescribed state changes only the cells next to tagged faces, and
+    tagging no face equals the outflow default."""
+    w = W.lattice_forest(2, 2, 1.0, 2, periodic=False, jitter=0.1, seed=4)
+    w["refine"] = [[(0, 1, (0, 0))]]
+    F = FO.build(w)
+    R = len(w["root_corners"])
+    fs = (1.0, 0.3, -0.2, 1.0)
+    state = W.free_stream(np.zeros((1, 2)), state=fs)[0]
+    tags = [[1, 1, 1, 1] for _ in range(R)]
+    S = dg.Solver(F, 2, boundary=(tags, state))
+    L = S.residual(S.project(lambda x: W.free_stream(x, state=fs)))
+    assert np.max(np.abs(L)) < 1e-11
+    U = W.random_modal_state(len(S.leaves), 2, 2, 2, seed=5)
+    S0 = dg.Solver(FO.build(w), 2)
+    Sn = dg.Solver(FO.build(w), 2, boundary=([[0] * 4 for _ in range(R)], state))
+    assert np.array_equal(S0.residual(U), Sn.residual(U))
+    tags1 = [[1, 0, 0, 0] for _ in range(R)]  # x- faces only
+    S1 = dg.Solver(FO.build(w), 2, boundary=(tags1, 2.0 * state))
+    D = np.abs(S1.residual(U) - S0.residual(U)).max(axis=(1, 2))  # per (leaf, cell)
+    T = FO.build(w).leaf_table()
+    cells_x0 = np.array([c % 2 == 0 for c in range(4)])  # the cells next to x-
+    for li in range(len(S1.leaves)):
+        on_xminus = T["kind"][li][0] == 3
+        assert np.all(D[li][~cells_x0] == 0)
+        assert np.any(D[li][cells_x0] > 0) == on_xminus
