@@ -171,6 +171,15 @@ dgf_status dgf_adapt(dgf_forest* f, double refine_above, double coarsen_below, i
 dgf_status dgf_adapt_with(dgf_forest* f, const double* indicator, double refine_above, double coarsen_below,
                           int32_t max_level, int64_t* n_refined, int64_t* n_coarsened);
 
+/* Boundary conditions of the root faces that have no neighbour (Sec. 5-6
+ * use outflow and inflow boundaries): root_face_kind[root * 2d + face] is 0
+ * for outflow (the guard cell mirrors my face cell, the default) or 1 for a
+ * prescribed constant state (inflow / far field: the guard cell is `state`,
+ * nv conserved values, host).  Entries of faces that have a neighbour are
+ * ignored.  Leaf faces inherit their root face's kind.  The device tables are
+ * rebuilt; a state set before the call is kept. */
+dgf_status dgf_set_boundary(dgf_forest* f, const int32_t* root_face_kind, const double* state);
+
 /* Number of leaf blocks. */
 dgf_status dgf_leaf_count(const dgf_forest* f, int64_t* n_leaves);
 /* Integer leaf tables (host arrays sized by dgf_leaf_count = L):

@@ -71,6 +71,7 @@ _SIGS = {
     "dgf_rk_step": [_P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
     "dgf_get_time": [_P, ctypes.POINTER(ctypes.c_double)],
     "dgf_indicator": [_P, ctypes.POINTER(ctypes.c_double)],
+    "dgf_set_boundary": [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)],
     "dgf_set_limiter": [_P, ctypes.c_double],
     "dgf_limit": [_P],
     "dgf_adapt": [_P, ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
@@ -251,6 +252,15 @@ class Forest:
     def coarsen(self, leaf_ids):
         ids = np.ascontiguousarray(leaf_ids, np.int64)
         _check(lib().dgf_block_coarsen(self.h, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(ids)))
+
+    def set_boundary(self, root_face_kind, state):
+        """Root faces without a neighbour: 0 outflow, 1 prescribed state
+        (root_face_kind: [roots][2 dim]); state: nv conserved values."""
+        tags = np.ascontiguousarray(root_face_kind, np.int32)
+        st = np.ascontiguousarray(state, np.float64)
+        assert st.shape == (self.nv,)
+        _check(lib().dgf_set_boundary(self.h, tags.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      st.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
 
     def indicator(self):
         """Refinement indicator per leaf (see dgf_indicator)."""

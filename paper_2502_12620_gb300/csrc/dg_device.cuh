@@ -291,6 +291,7 @@ struct GuardArgs {
   int nmc;
   const Real* __restrict__ mw;        // [nmc][NFP][2^(D-1) NFP] coarse point <- fine sub-face points
   const long long* __restrict__ msrc; // [nmc][nt][2^(D-1)] gtr offset of (fine leaf, face, v 0, point 0, t)
+  const Real* __restrict__ bstate;    // [NV] state of prescribed-state boundary faces (kind 4)
   Tab<P + 1, Real> T;
 };
 
@@ -1125,6 +1126,17 @@ __global__ void __launch_bounds__(128) k_guard(const GuardArgs<D, P, Real> A) {
   Real* out_vol = A.out + (((size_t)b * 2 * D + f) * NV + v) * Q * nt + t;
   Real* out_trace = A.out + (((size_t)b * 2 * D + f) * NV + v) * NFP * nt + t;
 
+  if (kind == 4) {  // prescribed state: a constant guard cell
+    const Real u = A.bstate[v];
+    if (A.mode == 0) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) out_vol[(size_t)q * nt] = u;
+    } else {
+#pragma unroll
+      for (int fp = 0; fp < NFP; ++fp) out_trace[(size_t)fp * nt] = u;
+    }
+    return;
+  }
   if (kind == 3) {  // outflow: the guard is the mirror image of my face cell
     int h[3] = {g[0], g[1], g[2]};
     h[a] = s ? n - 1 : 0;
@@ -1374,6 +1386,11 @@ __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, R
       return c;
     };
     Real* out_trace = A.out + (((size_t)b * 2 * D + f) * NV + v) * NFP * nt + t;
+    if (kind == 4) {  // prescribed state
+#pragma unroll
+      for (int fp = 0; fp < NFP; ++fp) out_trace[(size_t)fp * nt] = A.bstate[v];
+      return;
+    }
     if (kind == 3) {  // outflow: my own face cell's trace
       int h[3] = {g[0], g[1], g[2]};
       h[a] = s ? n - 1 : 0;

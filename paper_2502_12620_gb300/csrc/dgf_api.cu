@@ -138,6 +138,10 @@ struct dgf_forest {
   int nmf = 0, nmc = 0;
   double limiter = 0.0;  // positivity limiter bound (relative); 0 = off
   Buf ind;               // refinement indicator per leaf (kept between calls)
+  // boundary faces: per root face 0 outflow, 1 prescribed state (bstate_h)
+  std::vector<int32_t> bctag;
+  std::vector<double> bstate_h;
+  Buf bstate;
   int slots = 0;
   bool have_state = false;
   bool graph_valid = false;
@@ -284,6 +288,8 @@ dgf_status build_device(dgf_forest* f) {
   std::vector<int> kind(L * nf), nbr(L * nf * 4), orient(L * nf), qbits(L), copoff(L * nf, -1);
   for (int64_t i = 0; i < L * nf; ++i) {
     kind[i] = T.kind[i];
+    if (kind[i] == kBoundary && !f->bctag.empty() && f->bctag[(size_t)T.root[i / nf] * nf + i % nf] == 1)
+      kind[i] = 4;  // prescribed state (device-side code only)
     orient[i] = pack_orient(orient_from_code(T.orient[i], d), d);
     for (int s = 0; s < 4; ++s) nbr[i * 4 + s] = (int)T.nbr[i * 4 + s];
   }
@@ -587,6 +593,12 @@ dgf_status build_device(dgf_forest* f) {
   if (f->device < 0) return DGF_OK;
   DeviceGuard dg(f->device);
   dgf_status st;
+  {
+    std::vector<double> bs(f->nv, 0.0);
+    if (!f->bstate_h.empty()) bs = f->bstate_h;
+    if ((st = f->precision == DGF_FP64 ? upload(f, f->bstate, bs) : upload(f, f->bstate, convert<float>(bs))))
+      return st;
+  }
   if ((st = upload(f, f->kind, kind)) || (st = upload(f, f->nbr, nbr)) || (st = upload(f, f->orient, orient)) ||
       (st = upload(f, f->qbits, qbits)) || (st = upload(f, f->copoff, copoff)) || (st = upload(f, f->geo64, geo64)) ||
       (st = upload(f, f->fine, fine_list)))
@@ -713,6 +725,7 @@ RtGuard guard_args(dgf_forest* f, int src, void* out, int mode) {
   r.nfine = f->nfine;
   r.geo = f->geo.ptr;
   r.gamma = f->gamma;
+  r.bstate = f->bstate.ptr;
   if (f->mortar && mode == 1) {
     r.nfine = 0;  // the coarse side's flux comes from the mortar passes
     r.mfine = (const int*)f->mfine.ptr;
@@ -1050,7 +1063,7 @@ dgf_status dgf_forest_destroy(dgf_forest* f) {
                                &f->gmod, &f->cop, &f->ctr, &f->kind, &f->nbr, &f->orient, &f->qbits, &f->copoff,
                                &f->part, &f->scal, &f->tot, &f->dtout, &f->nodal, &f->fine, &f->affine, &f->ameta,
                                &f->U64[0], &f->U64[1], &f->hcell64, &f->gmod64, &f->fluxmask,
-                               &f->mfine, &f->mcoarse, &f->mw, &f->msrc, &f->ind};
+                               &f->mfine, &f->mcoarse, &f->mw, &f->msrc, &f->ind, &f->bstate};
     for (auto* b : bufs) dev_free(f, *b);
     if (f->own_stream && f->stream) cudaStreamDestroy(f->stream);
   }
@@ -1174,6 +1187,19 @@ dgf_status dgf_adapt(dgf_forest* f, double refine_above, double coarsen_below, i
   dgf_status st = indicator_host(f, g);
   if (st) return st;
   return dgf_adapt_with(f, g.data(), refine_above, coarsen_below, max_level, n_refined, n_coarsened);
+}
+
+dgf_status dgf_set_boundary(dgf_forest* f, const int32_t* root_face_kind, const double* state) {
+  if (!f || !root_face_kind || !state) return fail(DGF_EINVAL, "null argument");
+  const int nf = 2 * f->d;
+  std::vector<int32_t> tags(root_face_kind, root_face_kind + f->host.R * nf);
+  for (int32_t t : tags)
+    if (t != 0 && t != 1) return fail(DGF_EINVAL, "boundary kinds must be 0 (outflow) or 1 (prescribed state)");
+  for (int v = 0; v < f->nv; ++v)
+    if (!std::isfinite(state[v])) return fail(DGF_EINVAL, "non-finite boundary state");
+  f->bctag = tags;
+  f->bstate_h.assign(state, state + f->nv);
+  return build_device(f);
 }
 
 dgf_status dgf_leaf_count(const dgf_forest* f, int64_t* n) {

@@ -191,6 +191,7 @@ static cudaError_t guard_p(const RtGuard& r, cudaStream_t s) {
   a.nmc = r.nmc;
   a.mw = (const Real*)r.mw;
   a.msrc = r.msrc;
+  a.bstate = (const Real*)r.bstate;
   a.T = make_tab<P + 1, Real>(r.T);
   const int nt = D == 3 ? r.n * r.n : r.n;
   if (r.mode == 1) {

@@ -65,6 +65,7 @@ struct RtGuard {
   int nmc;
   const void* mw;
   const long long* msrc;
+  const void* bstate;  // prescribed boundary state (nv values, compute precision)
   RtTables T;
 };
 

@@ -199,3 +199,17 @@ def test_adapt_topology_matches_oracle(dgf, case, seed):
         for k in ("root", "level", "pos", "kind", "nbr", "orient"):
             assert np.array_equal(T[k].astype(np.int64), O[k].astype(np.int64)), (it, k)
     assert done[0] > 0 and done[1] > 0, done  # both rules were exercised
+
+
+def test_boundary_kinds_are_checked(dgf):
+    w = dict(W.lattice_forest(2, 2, 1.0, 2, periodic=False), refine=[])
+    f = _host_forest(dgf, w)
+    state = np.array([1.0, 0.1, 0.0, 2.5])
+    f.set_boundary(np.ones((4, 4), np.int32), state)
+    with pytest.raises(dgf.DgfError) as e:
+        f.set_boundary(np.full((4, 4), 2, np.int32), state)
+    assert e.value.code == -1
+    with pytest.raises(dgf.DgfError):
+        f.set_boundary(np.zeros((4, 4), np.int32), np.array([1.0, np.nan, 0.0, 2.5]))
+    # the leaf table (a paper-level quantity) still reports kind 3 for boundary faces
+    assert (f.leaf_table()["kind"] == 3).sum() == 8

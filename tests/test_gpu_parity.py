@@ -326,3 +326,31 @@ def test_fp64_p3_row_slabs_match_oracle(dgf, mode):
     f.rk_step()
     U1 = S.ssp_rk3_step(U, S.dt(U))
     assert rel(f.get_state(), U1) < TOL["fp64"]
+
+
+# ----------------------------------------------------- prescribed-state boundaries
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_prescribed_state_boundaries_match_oracle(dgf, dim, prec):
+    """Root faces without a neighbour tagged at random as outflow or as a
+    prescribed far-field state: guard cells, residual and RK steps against
+    the oracle on a jittered, refined, non-periodic forest."""
+    w = W.lattice_forest(dim, 2, 1.0, 4 if dim == 2 else 2, periodic=False, jitter=0.1, seed=6,
+                         rotate_roots=True)
+    w["refine"] = [[(0, 1, (0,) * dim)]]
+    R = len(w["root_corners"])
+    tags = np.random.default_rng(dim).integers(0, 2, size=(R, 2 * dim)).astype(np.int32)
+    state = W.free_stream(np.zeros((1, dim)), state=(1.1, 0.4, -0.1, 0.2, 0.9)[: dim + 1] + (0.9,))[0]
+    pr = dgf.FP64 if prec == "fp64" else dgf.FP32
+    f = dgf.Forest.from_workload(w, p=2, precision=pr, cfl=0.2)
+    f.set_boundary(tags, state)
+    S = dg.Solver(FO.build(w), 2, cfl=0.2, boundary=(tags.tolist(), state))
+    U = W.random_modal_state(f.n_leaves, dim, f.n_seg, 2, seed=17).astype(f.dtype).astype(np.float64)
+    f.set_state(U)
+    if prec == "fp64":
+        assert rel(f.fill_guardcells(), S.fill_guardcells(U)) < TOL["fp64"]
+    assert rel(f.dg_residual(), S.residual(U)) < TOL[prec]
+    for _ in range(2):
+        U = S.ssp_rk3_step(U, S.dt(U))
+        f.rk_step()
+    assert rel(f.get_state(), U) < TOL[prec]
