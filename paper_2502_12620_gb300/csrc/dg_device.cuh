@@ -565,18 +565,46 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
       if constexpr (D == 3) {
         if (k == k0) {
           // halo trace below the first layer: guard (z-) or the layer below
-          for (int w = tid; w < NCL * NV * NFP; w += nthr) {
-            const int c = w % NCL, fp = (w / NCL) % NFP, v = w / (NCL * NFP);
-            Real tr;
-            if (k0 == 0) {
-              tr = GTR(4, v, fp, j0 * n + c);
-            } else {
-              tr = Real(0);
+          if constexpr (COMP) {
+            for (int w = tid; w < NCL * NV * NFP; w += nthr) {
+              const int c = w % NCL, fp = (w / NCL) % NFP, v = w / (NCL * NFP);
+              Real tr;
+              if (k0 == 0) {
+                tr = GTR(4, v, fp, j0 * n + c);
+              } else {
+                tr = Real(0);
 #pragma unroll
-              for (int qz = 0; qz < N; ++qz)
-                tr += T.lp[qz] * Sb(((size_t)v * Q + fp + NFP * qz) * nc + cbase - LAY + c);
+                for (int qz = 0; qz < N; ++qz)
+                  tr += T.lp[qz] * Sb(((size_t)v * Q + fp + NFP * qz) * nc + cbase - LAY + c);
+              }
+              TB(v, fp, c) = tr;
             }
-            TB(v, fp, c) = tr;
+          } else {
+            // HV consecutive cells per thread, 16-byte loads and stores
+            constexpr int HV = 16 / (int)sizeof(Real);
+            constexpr int NCV = NCL / HV;
+            using V = typename std::conditional<sizeof(Real) == 4, float4, double2>::type;
+            static_assert(NCL % HV == 0, "a slab holds whole 16-byte groups of cells");
+            for (int w = tid; w < NCV * NV * NFP; w += nthr) {
+              const int c0 = (w % NCV) * HV, fp = (w / NCV) % NFP, v = w / (NCV * NFP);
+              Real tr[HV];
+              if (k0 == 0) {
+                vload<HV>(reinterpret_cast<const V*>(&GTR(4, v, fp, j0 * n + c0)), tr);
+              } else {
+#pragma unroll
+                for (int e = 0; e < HV; ++e) tr[e] = Real(0);
+#pragma unroll
+                for (int qz = 0; qz < N; ++qz) {
+                  Real x[HV];
+                  const V xv = __ldcg(reinterpret_cast<const V*>(Ub + ((size_t)v * Q + fp + NFP * qz) * nc + cbase -
+                                                                  LAY + c0));
+                  vload<HV>(&xv, x);
+#pragma unroll
+                  for (int e = 0; e < HV; ++e) tr[e] += T.lp[qz] * x[e];
+                }
+              }
+              vstore<HV>(reinterpret_cast<V*>(&TB(v, fp, c0)), tr);
+            }
           }
           __syncthreads();
           for (int w = tid; w < NCL * NFP; w += nthr) {
@@ -772,7 +800,11 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
       // ------------------------------------------- P4: y volume + lift (rs +=)
       //                                            and the halo trace above
       constexpr int NY = NCL * NFP;
-      constexpr int ny_total = NY + ((D == 3) ? NCL * NV * NFP : 0);
+      // halo items: one cell each (compensated form) or HV consecutive cells
+      // with 16-byte loads and stores
+      constexpr int HV = COMP ? 1 : 16 / (int)sizeof(Real);
+      constexpr int ny_total = NY + ((D == 3) ? NCL * NV * NFP / HV : 0);
+      static_assert(NCL % HV == 0, "a slab holds whole 16-byte groups of cells");
       for (int w = tid; w < ny_total; w += nthr) {
         if (w < NY) {
           const int c = w % NCL, fp = w / NCL;
@@ -821,17 +853,40 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
           }
         } else if constexpr (D == 3) {
           const int ww = w - NY;
-          const int c = ww % NCL, fp = (ww / NCL) % NFP, v = ww / (NCL * NFP);
-          Real tr;
-          if (k == n - 1) {
-            tr = GTR(5, v, fp, j0 * n + c);
-          } else {
-            tr = Real(0);
+          if constexpr (COMP) {
+            const int c = ww % NCL, fp = (ww / NCL) % NFP, v = ww / (NCL * NFP);
+            Real tr;
+            if (k == n - 1) {
+              tr = GTR(5, v, fp, j0 * n + c);
+            } else {
+              tr = Real(0);
 #pragma unroll
-            for (int qz = 0; qz < N; ++qz)
-              tr += T.lm[qz] * Sb(((size_t)v * Q + fp + NFP * qz) * nc + cbase + LAY + c);
+              for (int qz = 0; qz < N; ++qz)
+                tr += T.lm[qz] * Sb(((size_t)v * Q + fp + NFP * qz) * nc + cbase + LAY + c);
+            }
+            TB(v, fp, c) = tr;
+          } else {
+            using V = typename std::conditional<sizeof(Real) == 4, float4, double2>::type;
+            constexpr int NCV = NCL / HV;
+            const int c0 = (ww % NCV) * HV, fp = (ww / NCV) % NFP, v = ww / (NCV * NFP);
+            Real tr[HV];
+            if (k == n - 1) {
+              vload<HV>(reinterpret_cast<const V*>(&GTR(5, v, fp, j0 * n + c0)), tr);
+            } else {
+#pragma unroll
+              for (int e = 0; e < HV; ++e) tr[e] = Real(0);
+#pragma unroll
+              for (int qz = 0; qz < N; ++qz) {
+                Real x[HV];
+                const V xv = __ldcg(reinterpret_cast<const V*>(Ub + ((size_t)v * Q + fp + NFP * qz) * nc + cbase +
+                                                                LAY + c0));
+                vload<HV>(&xv, x);
+#pragma unroll
+                for (int e = 0; e < HV; ++e) tr[e] += T.lm[qz] * x[e];
+              }
+            }
+            vstore<HV>(reinterpret_cast<V*>(&TB(v, fp, c0)), tr);
           }
-          TB(v, fp, c) = tr;
         }
       }
       __syncthreads();
