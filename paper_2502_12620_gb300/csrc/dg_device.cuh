@@ -282,6 +282,7 @@ struct GuardArgs {
   const Real* __restrict__ ctr;    // [op][2^D M][NFP]: the same operator followed by my face trace
   const int* __restrict__ fine_list;  // [nfine] leaf * 2D + face of every finer-neighbour face
   int nfine;
+  const int* __restrict__ trd;        // [b][f][8] face-trace descriptors (kinds 0, 1, 3), see k_guard_trace
   // mortar mode (reading R15)
   const Real* __restrict__ geo;       // [b][g][cell] trilinear coefficients
   Real gamma;
@@ -1422,96 +1423,68 @@ __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, R
     const int b = (int)(w / ((size_t)nt * NV * 2 * D));
     const int kind = A.kind[b * 2 * D + f];
     if (kind == 2) return;
-    const int a = f >> 1, s = f & 1;
-    int g[3] = {0, 0, 0};
-    {
-      int j = 0;
-      for (int ax = 0; ax < D; ++ax) {
-        if (ax == a) continue;
-        g[ax] = j == 0 ? (t % n) : (t / n);
-        ++j;
-      }
-    }
-    auto cell_of = [&](const int* h) {
-      int c = 0, st = 1;
-      for (int ax = 0; ax < D; ++ax) {
-        c += h[ax] * st;
-        st *= n;
-      }
-      return c;
-    };
     Real* out_trace = A.out + (((size_t)b * 2 * D + f) * NV + v) * NFP * nt + t;
     if (kind == 4) {  // prescribed state
 #pragma unroll
       for (int fp = 0; fp < NFP; ++fp) out_trace[(size_t)fp * nt] = A.bstate[v];
       return;
     }
-    if (kind == 3) {  // outflow: my own face cell's trace
-      int h[3] = {g[0], g[1], g[2]};
-      h[a] = s ? n - 1 : 0;
-      const size_t src0 = ((size_t)b * NV + v) * Q * nc + cell_of(h);
-#pragma unroll
-      for (int fp = 0; fp < NFP; ++fp) {
-        Real acc = Real(0);
-#pragma unroll
-        for (int qn = 0; qn < N; ++qn)
-          acc += (s ? T.lp[qn] : T.lm[qn]) * S(src0 + (size_t)face_point_index<D, N>(a, fp, qn) * nc);
-        out_trace[(size_t)fp * nt] = acc;
-      }
-      return;
-    }
-    const int pk = A.orient[b * 2 * D + f];
-    const int b2 = opi(pk, a);
-    const int s2 = osg(pk, a) > 0 ? 1 - s : s;
-    int h[3] = {0, 0, 0}, e[3] = {0, 0, 0};
-    if (kind == 0) {
-      for (int ax = 0; ax < D; ++ax) {
-        if (ax == a) continue;
-        h[opi(pk, ax)] = osg(pk, ax) > 0 ? g[ax] : n - 1 - g[ax];
-      }
-    } else {
-      const int qb = A.qbits[b];
-      for (int ax = 0; ax < D; ++ax) {
-        if (ax == a) continue;
-        const int G = ((qb >> ax) & 1) * n + g[ax];
-        const int hh = G >> 1, ee = G & 1;
-        h[opi(pk, ax)] = osg(pk, ax) > 0 ? hh : n - 1 - hh;
-        e[opi(pk, ax)] = osg(pk, ax) > 0 ? ee : 1 - ee;
+    // same-level, coarser or outflow (my own face cell): the source cell and
+    // its face points are affine in my guard-cell and face-point digits, the
+    // orientation folded into signed strides (host-built descriptor)
+    const int4 d0 = __ldg(reinterpret_cast<const int4*>(A.trd + (size_t)(b * 2 * D + f) * 8));
+    const int4 d1 = __ldg(reinterpret_cast<const int4*>(A.trd + (size_t)(b * 2 * D + f) * 8 + 4));
+    const int ln = 31 - __clz(n);  // n is a power of two
+    int g0 = t & (n - 1), g1 = t >> ln;
+    int e0 = 0, e1 = 0;
+    if (kind == 1) {
+      // my position on the coarse face: coarse cell G >> 1, child half G & 1
+      const int a = f >> 1, qb = A.qbits[b];
+      const int t0 = a == 0 ? 1 : 0, t1 = a == 2 ? 1 : 2;  // my tangential axes
+      const int G0 = ((qb >> t0) & 1) * n + g0;
+      e0 = G0 & 1;
+      g0 = G0 >> 1;
+      if constexpr (D == 3) {
+        const int G1 = ((qb >> t1) & 1) * n + g1;
+        e1 = G1 & 1;
+        g1 = G1 >> 1;
       }
     }
-    h[b2] = s2 == 0 ? 0 : n - 1;
-    const size_t src0 = ((size_t)A.nbr[(b * 2 * D + f) * 4] * NV + v) * Q * nc + cell_of(h);
+    const size_t src0 = ((size_t)d0.x * NV + v) * Q * nc + (d0.y + g0 * d0.z + g1 * d0.w) + d1.x;
+    const int PN = d1.w >> 1;
+    Real lq[N];
+#pragma unroll
+    for (int qn = 0; qn < N; ++qn) lq[qn] = (d1.w & 1) ? T.lp[qn] : T.lm[qn];
     Real tr[NFP];
 #pragma unroll
-    for (int j = 0; j < NFP; ++j) {
-      Real acc = Real(0);
+    for (int q1 = 0; q1 < (D == 3 ? N : 1); ++q1)
 #pragma unroll
-      for (int qn = 0; qn < N; ++qn)
-        acc += (s2 ? T.lp[qn] : T.lm[qn]) * S(src0 + (size_t)face_point_index<D, N>(b2, j, qn) * nc);
-      tr[j] = acc;
-    }
-    if (kind == 1) {  // split (Eqs. (11)-(12)) of the coarse face trace
+      for (int q0 = 0; q0 < N; ++q0) {
+        Real acc = Real(0);
+#pragma unroll
+        for (int qn = 0; qn < N; ++qn) acc += lq[qn] * S(src0 + (ptrdiff_t)(q0 * d1.y + q1 * d1.z + qn * PN));
+        tr[q0 + N * q1] = acc;
+      }
+    if (kind == 1) {  // split (Eqs. (11)-(12)) of the coarse face trace, in my frame
       Real t2[NFP];
       if constexpr (D == 2) {
-        const int u0 = 1 - b2;
 #pragma unroll
         for (int i = 0; i < N; ++i) {
           Real acc = Real(0);
 #pragma unroll
-          for (int jj = 0; jj < N; ++jj) acc += (e[u0] ? T.Snp[i][jj] : T.Snm[i][jj]) * tr[jj];
+          for (int jj = 0; jj < N; ++jj) acc += (e0 ? T.Snp[i][jj] : T.Snm[i][jj]) * tr[jj];
           t2[i] = acc;
         }
 #pragma unroll
         for (int i = 0; i < N; ++i) tr[i] = t2[i];
       } else {
-        const int u0 = b2 == 0 ? 1 : 0, u1 = b2 == 2 ? 1 : 2;
 #pragma unroll
         for (int i1 = 0; i1 < N; ++i1)
 #pragma unroll
           for (int i0 = 0; i0 < N; ++i0) {
             Real acc = Real(0);
 #pragma unroll
-            for (int jj = 0; jj < N; ++jj) acc += (e[u0] ? T.Snp[i0][jj] : T.Snm[i0][jj]) * tr[jj + N * i1];
+            for (int jj = 0; jj < N; ++jj) acc += (e0 ? T.Snp[i0][jj] : T.Snm[i0][jj]) * tr[jj + N * i1];
             t2[i0 + N * i1] = acc;
           }
 #pragma unroll
@@ -1520,13 +1493,13 @@ __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, R
           for (int i0 = 0; i0 < N; ++i0) {
             Real acc = Real(0);
 #pragma unroll
-            for (int jj = 0; jj < N; ++jj) acc += (e[u1] ? T.Snp[i1][jj] : T.Snm[i1][jj]) * t2[i0 + N * jj];
+            for (int jj = 0; jj < N; ++jj) acc += (e1 ? T.Snp[i1][jj] : T.Snm[i1][jj]) * t2[i0 + N * jj];
             tr[i0 + N * i1] = acc;
           }
       }
     }
 #pragma unroll
-    for (int j = 0; j < NFP; ++j) out_trace[(size_t)map_face_point<D, N>(j, a, b2, pk) * nt] = tr[j];
+    for (int j = 0; j < NFP; ++j) out_trace[(size_t)j * nt] = tr[j];
     return;
   }
   // ---- finer faces: one block per (finer face, guard cell t), all vars;

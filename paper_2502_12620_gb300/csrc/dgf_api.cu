@@ -130,7 +130,7 @@ struct dgf_forest {
   Buf U64[2], hcell64, gmod64;
   cudaGraphExec_t graph_alt = nullptr;  // compensated form: graph of the other u^n buffer
   Buf U[3], geo, geo64, hcell, gtr, gmod, cop, ctr, kind, nbr, orient, qbits, copoff, part, scal, tot,
-      dtout, nodal, fine, affine, ameta;
+      dtout, nodal, fine, affine, ameta, trd;
   int nfine = 0;
   // mortar treatment of level jumps (reading R15)
   bool mortar = false;
@@ -297,6 +297,65 @@ dgf_status build_device(dgf_forest* f) {
     int q = 0;
     for (int a = 0; a < d; ++a) q |= (T.pos[i * d + a] & 1) << a;
     qbits[i] = q;
+  }
+
+  // Face-trace descriptors of the time-step guard kernel.  For a face of kind
+  // same-level, coarser or outflow, the trace seen by my guard cell (g0, g1)
+  // (my tangential axes in increasing order; for a coarser neighbour the
+  // coarse cell index G >> 1 of my position G on its face) at my face point
+  // (q0, q1) is sum_qn l[qn] u(src, cell, point) with
+  //   cell  = cbase + g0 CS0 + g1 CS1,
+  //   point = (pbase + q0 PS0 + q1 PS1 + qn PSN) / nc   (strides times nc),
+  // l the source face's side table (l(+1) or l(-1)): the orientation becomes
+  // signed strides.  Entries: src, cbase, CS0, CS1, pbase, PS0, PS1, PSN * 2
+  // + side.  The outflow trace is my own face cell's (src = me).
+  std::vector<int> trd((size_t)L * nf * 8, 0);
+  {
+    const int Nq = f->p + 1;
+    auto ipw = [](int b, int e) {
+      int r = 1;
+      while (e-- > 0) r *= b;
+      return r;
+    };
+    for (int64_t i = 0; i < L; ++i)
+      for (int fc = 0; fc < nf; ++fc) {
+        const int k = kind[i * nf + fc];
+        if (k != kSame && k != kCoarser && k != kBoundary) continue;
+        const int a = fc >> 1, s = fc & 1;
+        int ta[2] = {0, 0}, m = 0;
+        for (int ax = 0; ax < d; ++ax)
+          if (ax != a) ta[m++] = ax;
+        int src = (int)i, b2 = a, s2 = s, A[2] = {ta[0], ta[1]}, sgn[2] = {1, 1};
+        if (k != kBoundary) {
+          const Orient o = orient_from_code(T.orient[i * nf + fc], d);
+          src = nbr[(i * nf + fc) * 4];
+          b2 = o.pi[a];
+          s2 = o.sg[a] > 0 ? 1 - s : s;
+          for (int j = 0; j < d - 1; ++j) {
+            A[j] = o.pi[ta[j]];
+            sgn[j] = o.sg[ta[j]];
+          }
+        }
+        int cbase = s2 ? (n - 1) * ipw(n, b2) : 0, pbase = 0, CS[2] = {0, 0}, PS[2] = {0, 0};
+        for (int j = 0; j < d - 1; ++j) {
+          const int cs = ipw(n, A[j]), ps = ipw(Nq, A[j]);
+          CS[j] = sgn[j] * cs;
+          PS[j] = sgn[j] * ps;
+          if (sgn[j] < 0) {
+            cbase += (n - 1) * cs;
+            pbase += (Nq - 1) * ps;
+          }
+        }
+        int* e = &trd[((size_t)i * nf + fc) * 8];
+        e[0] = src;
+        e[1] = cbase;
+        e[2] = CS[0];
+        e[3] = CS[1];
+        e[4] = pbase * nc;
+        e[5] = PS[0] * nc;
+        e[6] = PS[1] * nc;
+        e[7] = ipw(Nq, b2) * nc * 2 + s2;
+      }
   }
 
   // geometry: per-cell trilinear coefficients (c >= 1) and sizes h; the
@@ -601,7 +660,7 @@ dgf_status build_device(dgf_forest* f) {
   }
   if ((st = upload(f, f->kind, kind)) || (st = upload(f, f->nbr, nbr)) || (st = upload(f, f->orient, orient)) ||
       (st = upload(f, f->qbits, qbits)) || (st = upload(f, f->copoff, copoff)) || (st = upload(f, f->geo64, geo64)) ||
-      (st = upload(f, f->fine, fine_list)))
+      (st = upload(f, f->fine, fine_list)) || (st = upload(f, f->trd, trd)))
     return st;
   if ((st = upload(f, f->affine, affine)) || (st = upload(f, f->hcell64, hcell))) return st;
   if (f->mortar && ((st = upload(f, f->fluxmask, fluxmask)) || (st = upload(f, f->mfine, mfine)) ||
@@ -723,6 +782,7 @@ RtGuard guard_args(dgf_forest* f, int src, void* out, int mode) {
   r.ctr = f->ctr.ptr;
   r.fine_list = (const int*)f->fine.ptr;
   r.nfine = f->nfine;
+  r.trd = (const int*)f->trd.ptr;
   r.geo = f->geo.ptr;
   r.gamma = f->gamma;
   r.bstate = f->bstate.ptr;
@@ -1063,7 +1123,7 @@ dgf_status dgf_forest_destroy(dgf_forest* f) {
                                &f->gmod, &f->cop, &f->ctr, &f->kind, &f->nbr, &f->orient, &f->qbits, &f->copoff,
                                &f->part, &f->scal, &f->tot, &f->dtout, &f->nodal, &f->fine, &f->affine, &f->ameta,
                                &f->U64[0], &f->U64[1], &f->hcell64, &f->gmod64, &f->fluxmask,
-                               &f->mfine, &f->mcoarse, &f->mw, &f->msrc, &f->ind, &f->bstate};
+                               &f->mfine, &f->mcoarse, &f->mw, &f->msrc, &f->ind, &f->bstate, &f->trd};
     for (auto* b : bufs) dev_free(f, *b);
     if (f->own_stream && f->stream) cudaStreamDestroy(f->stream);
   }

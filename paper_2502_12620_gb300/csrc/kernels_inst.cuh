@@ -183,6 +183,7 @@ static cudaError_t guard_p(const RtGuard& r, cudaStream_t s) {
   a.ctr = (const Real*)r.ctr;
   a.fine_list = r.fine_list;
   a.nfine = r.nfine;
+  a.trd = r.trd;
   a.geo = (const Real*)r.geo;
   a.gamma = (Real)r.gamma;
   a.mfine = r.mfine;

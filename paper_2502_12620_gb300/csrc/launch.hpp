@@ -56,6 +56,7 @@ struct RtGuard {
   const void* ctr;
   const int* fine_list;
   int nfine;
+  const int* trd;  // [leaf][face][8] face-trace descriptors (kinds 0, 1, 3)
   // mortar mode: fine-side and coarse-side faces, coarse-side weights/sources
   const void* geo;
   double gamma;
