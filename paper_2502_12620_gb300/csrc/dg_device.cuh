@@ -264,6 +264,40 @@ struct StateIn {
       return u[i];
     }
   }
+  // VEC = 16 / sizeof(Real) consecutive values from index i (a multiple of
+  // VEC) with 16-byte L2 loads; element for element the same arithmetic as
+  // operator()
+  template <int VEC>
+  __device__ __forceinline__ void vec(size_t i, Real (&a)[VEC]) const {
+    static_assert(VEC * sizeof(Real) == 16, "16-byte groups");
+    if constexpr (COMP) {
+      double x[VEC];
+#pragma unroll
+      for (int e = 0; e < VEC; e += 2) {
+        const double2 q = __ldcg(reinterpret_cast<const double2*>(u64 + i + e));
+        x[e] = q.x;
+        x[e + 1] = q.y;
+      }
+      if (d) {
+        const float4 q = __ldcg(reinterpret_cast<const float4*>(d + i));
+        x[0] += (double)q.x;
+        x[1] += (double)q.y;
+        x[2] += (double)q.z;
+        x[3] += (double)q.w;
+      }
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) a[e] = (Real)x[e];
+    } else {
+      using V = typename std::conditional<sizeof(Real) == 4, float4, double2>::type;
+      const V q = __ldcg(reinterpret_cast<const V*>(u + i));
+      a[0] = q.x;
+      a[1] = q.y;
+      if constexpr (VEC == 4) {
+        a[2] = q.z;
+        a[3] = q.w;
+      }
+    }
+  }
 };
 
 template <int D, int P, typename Real>
@@ -550,38 +584,18 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
         constexpr int VEC = 16 / sizeof(Real);
         using V4 = typename std::conditional<sizeof(Real) == 4, float4, double2>::type;
         constexpr int PER_ROW = NCL / VEC;
-        if constexpr (COMP) {
-          for (int w = tid; w < NV * Q * NCL; w += nthr) {
-            const int r = w / NCL, cc = w - r * NCL;
-            us[r * NCL + cc] = Sb((size_t)r * nc + cbase + cc);
-          }
-        } else {
-          for (int w = tid; w < NV * Q * PER_ROW; w += nthr) {
-            const int r = w / PER_ROW, cv = (w - r * PER_ROW) * VEC;
-            const V4 val = __ldcg(reinterpret_cast<const V4*>(Ub + (size_t)r * nc + cbase + cv));
-            *reinterpret_cast<V4*>(us + r * NCL + cv) = val;
-          }
+        for (int w = tid; w < NV * Q * PER_ROW; w += nthr) {
+          const int r = w / PER_ROW, cv = (w - r * PER_ROW) * VEC;
+          Real x[VEC];
+          Sb.template vec<VEC>((size_t)r * nc + cbase + cv, x);
+          vstore<VEC>(reinterpret_cast<V4*>(us + r * NCL + cv), x);
         }
       }
       if constexpr (D == 3) {
         if (k == k0) {
-          // halo trace below the first layer: guard (z-) or the layer below
-          if constexpr (COMP) {
-            for (int w = tid; w < NCL * NV * NFP; w += nthr) {
-              const int c = w % NCL, fp = (w / NCL) % NFP, v = w / (NCL * NFP);
-              Real tr;
-              if (k0 == 0) {
-                tr = GTR(4, v, fp, j0 * n + c);
-              } else {
-                tr = Real(0);
-#pragma unroll
-                for (int qz = 0; qz < N; ++qz)
-                  tr += T.lp[qz] * Sb(((size_t)v * Q + fp + NFP * qz) * nc + cbase - LAY + c);
-              }
-              TB(v, fp, c) = tr;
-            }
-          } else {
-            // HV consecutive cells per thread, 16-byte loads and stores
+          // halo trace below the first layer: guard (z-) or the layer below,
+          // HV consecutive cells per thread with 16-byte loads and stores
+          {
             constexpr int HV = 16 / (int)sizeof(Real);
             constexpr int NCV = NCL / HV;
             using V = typename std::conditional<sizeof(Real) == 4, float4, double2>::type;
@@ -597,9 +611,7 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
 #pragma unroll
                 for (int qz = 0; qz < N; ++qz) {
                   Real x[HV];
-                  const V xv = __ldcg(reinterpret_cast<const V*>(Ub + ((size_t)v * Q + fp + NFP * qz) * nc + cbase -
-                                                                  LAY + c0));
-                  vload<HV>(&xv, x);
+                  Sb.template vec<HV>(((size_t)v * Q + fp + NFP * qz) * nc + cbase - LAY + c0, x);
 #pragma unroll
                   for (int e = 0; e < HV; ++e) tr[e] += T.lp[qz] * x[e];
                 }
@@ -801,9 +813,8 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
       // ------------------------------------------- P4: y volume + lift (rs +=)
       //                                            and the halo trace above
       constexpr int NY = NCL * NFP;
-      // halo items: one cell each (compensated form) or HV consecutive cells
-      // with 16-byte loads and stores
-      constexpr int HV = COMP ? 1 : 16 / (int)sizeof(Real);
+      // halo items: HV consecutive cells with 16-byte loads and stores
+      constexpr int HV = 16 / (int)sizeof(Real);
       constexpr int ny_total = NY + ((D == 3) ? NCL * NV * NFP / HV : 0);
       static_assert(NCL % HV == 0, "a slab holds whole 16-byte groups of cells");
       for (int w = tid; w < ny_total; w += nthr) {
@@ -854,40 +865,24 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
           }
         } else if constexpr (D == 3) {
           const int ww = w - NY;
-          if constexpr (COMP) {
-            const int c = ww % NCL, fp = (ww / NCL) % NFP, v = ww / (NCL * NFP);
-            Real tr;
-            if (k == n - 1) {
-              tr = GTR(5, v, fp, j0 * n + c);
-            } else {
-              tr = Real(0);
-#pragma unroll
-              for (int qz = 0; qz < N; ++qz)
-                tr += T.lm[qz] * Sb(((size_t)v * Q + fp + NFP * qz) * nc + cbase + LAY + c);
-            }
-            TB(v, fp, c) = tr;
+          using V = typename std::conditional<sizeof(Real) == 4, float4, double2>::type;
+          constexpr int NCV = NCL / HV;
+          const int c0 = (ww % NCV) * HV, fp = (ww / NCV) % NFP, v = ww / (NCV * NFP);
+          Real tr[HV];
+          if (k == n - 1) {
+            vload<HV>(reinterpret_cast<const V*>(&GTR(5, v, fp, j0 * n + c0)), tr);
           } else {
-            using V = typename std::conditional<sizeof(Real) == 4, float4, double2>::type;
-            constexpr int NCV = NCL / HV;
-            const int c0 = (ww % NCV) * HV, fp = (ww / NCV) % NFP, v = ww / (NCV * NFP);
-            Real tr[HV];
-            if (k == n - 1) {
-              vload<HV>(reinterpret_cast<const V*>(&GTR(5, v, fp, j0 * n + c0)), tr);
-            } else {
 #pragma unroll
-              for (int e = 0; e < HV; ++e) tr[e] = Real(0);
+            for (int e = 0; e < HV; ++e) tr[e] = Real(0);
 #pragma unroll
-              for (int qz = 0; qz < N; ++qz) {
-                Real x[HV];
-                const V xv = __ldcg(reinterpret_cast<const V*>(Ub + ((size_t)v * Q + fp + NFP * qz) * nc + cbase +
-                                                                LAY + c0));
-                vload<HV>(&xv, x);
+            for (int qz = 0; qz < N; ++qz) {
+              Real x[HV];
+              Sb.template vec<HV>(((size_t)v * Q + fp + NFP * qz) * nc + cbase + LAY + c0, x);
 #pragma unroll
-                for (int e = 0; e < HV; ++e) tr[e] += T.lm[qz] * x[e];
-              }
+              for (int e = 0; e < HV; ++e) tr[e] += T.lm[qz] * x[e];
             }
-            vstore<HV>(reinterpret_cast<V*>(&TB(v, fp, c0)), tr);
           }
+          vstore<HV>(reinterpret_cast<V*>(&TB(v, fp, c0)), tr);
         }
       }
       __syncthreads();
@@ -959,56 +954,7 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
       }
 
       // ------------------------------------------- P6: SSP-RK combination (+ CFL)
-      if constexpr (COMP) {
-      for (int w = tid; w < NCL * Q; w += nthr) {
-        const int c = w % NCL, q = w / NCL;
-        Real o[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const size_t gi = ((size_t)v * Q + q) * nc + cbase + c;
-          const Real r = RS(v, q, c);
-          Real val;
-          if (A.mode == 1) {
-            val = r;
-            Ob[gi] = val;
-          } else if constexpr (COMP) {
-            // delta^(k+1) = b_k (delta^(k) + dt L); last stage: u^(n+1) = u^n + delta^(3) in FP64
-            const Real din = Sb.d ? Sb.d[gi] : Real(0);
-            const Real dout = A.cb * (din + dt * r);
-            if (A.last) {
-              const double un = Sb.u64[gi] + (double)dout;
-              A.U64out[boff + gi] = un;
-              val = (Real)un;
-            } else {
-              Ob[gi] = dout;
-              val = dout;
-            }
-          } else {
-            val = A.cb * (US(v, q, c) + dt * r);  // the stage input is still in shared memory
-            if (A.ca != Real(0)) val += A.ca * __ldcg(&Unb[gi]);
-            Ob[gi] = val;
-          }
-          o[v] = val;
-        }
-        if (A.last) {
-          const Real ri = Real(1) / o[0];
-          Real ke = Real(0), sv = Real(0);
-#pragma unroll
-          for (int jj = 0; jj < D; ++jj) {
-            ke += o[1 + jj] * o[1 + jj];
-            sv += fabs(o[1 + jj]) * ri;
-          }
-          const Real pr = gm1 * (o[D + 1] - Real(0.5) * ke * ri);
-          if (!(o[0] > Real(0)) || !(pr > Real(0)) || !(pr < Real(3.0e38))) {
-            bad = true;
-          } else {
-            const Real lam = sv + Real(D) * sqrt(gamma * pr * ri);
-            const Real hv = A.hcell[(size_t)b * nc + cbase + c] / lam;
-            lam_min = hv < lam_min ? hv : lam_min;
-          }
-        }
-      }
-      } else {
+      {
         // VEC consecutive cells per thread: 16-byte shared and global accesses
         constexpr int VEC = 16 / sizeof(Real);
         using V = typename std::conditional<sizeof(Real) == 4, float4, double2>::type;
@@ -1024,6 +970,27 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
             if (A.mode == 1) {
 #pragma unroll
               for (int e = 0; e < VEC; ++e) val[e] = r[e];
+            } else if constexpr (COMP) {
+              // delta^(k+1) = b_k (delta^(k) + dt L); last stage: u^(n+1) = u^n + delta^(3) in FP64
+              Real din[VEC];
+#pragma unroll
+              for (int e = 0; e < VEC; ++e) din[e] = Real(0);
+              if (Sb.d) {
+                const float4 x = __ldcg(reinterpret_cast<const float4*>(Sb.d + gi));
+                vload<VEC>(&x, din);
+              }
+#pragma unroll
+              for (int e = 0; e < VEC; ++e) val[e] = A.cb * (din[e] + dt * r[e]);
+              if (A.last) {
+#pragma unroll
+                for (int e = 0; e < VEC; e += 2) {
+                  const double2 un = __ldcg(reinterpret_cast<const double2*>(Sb.u64 + gi + e));
+                  const double2 nw = make_double2(un.x + (double)val[e], un.y + (double)val[e + 1]);
+                  *reinterpret_cast<double2*>(A.U64out + boff + gi + e) = nw;
+                  val[e] = (Real)nw.x;
+                  val[e + 1] = (Real)nw.y;
+                }
+              }
             } else {
               Real u[VEC];
               vload<VEC>(reinterpret_cast<const V*>(&US(v, q, c0)), u);
@@ -1037,7 +1004,8 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
                 for (int e = 0; e < VEC; ++e) val[e] += A.ca * un[e];
               }
             }
-            vstore<VEC>(reinterpret_cast<V*>(&Ob[gi]), val);
+            // the compensated last stage keeps its result in FP64 only
+            if (!(COMP && A.mode != 1 && A.last)) vstore<VEC>(reinterpret_cast<V*>(&Ob[gi]), val);
 #pragma unroll
             for (int e = 0; e < VEC; ++e) o[v][e] = val[e];
           }
