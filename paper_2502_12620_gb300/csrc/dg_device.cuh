@@ -311,7 +311,7 @@ struct GuardArgs {
   const int* __restrict__ nbr;     // [b][f][4]
   const int* __restrict__ orient;  // [b][f] packed decoded orientation
   const int* __restrict__ qbits;   // [b] pos & 1 bits
-  const int* __restrict__ copoff;  // [b][f] first combine operator or -1
+  const int* __restrict__ copoff;  // [b][f] first combine operator << 1 | shared by all guard cells; -1: none
   const Real* __restrict__ cop;    // [op][2^D M][M]: column k' of the operator is contiguous
   const Real* __restrict__ ctr;    // [op][2^D M][NFP]: the same operator followed by my face trace
   const int* __restrict__ fine_list;  // [nfine] leaf * 2D + face of every finer-neighbour face
@@ -1334,7 +1334,8 @@ __global__ void __launch_bounds__(32 << D) k_guard_fine(const GuardArgs<D, P, Re
   }
   for (int q = lane; q < Q; q += 32) srcs[e][q] = S((((size_t)fine * NV + v) * Q + q) * nc + c);
   __syncwarp();
-  const Real* op = A.cop + (size_t)(A.copoff[bf] + t) * KC * Q + (size_t)e * Q * Q;
+  const int co = A.copoff[bf];  // first operator << 1 | one operator shared by every guard cell
+  const Real* op = A.cop + ((size_t)(co >> 1) + ((co & 1) ? 0 : t)) * KC * Q + (size_t)e * Q * Q;
   for (int p = lane; p < Q; p += 32) {
     Real acc0 = Real(0), acc1 = Real(0);
 #pragma unroll 4
@@ -1513,7 +1514,8 @@ __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, R
     sv[e][v][q] = S((((size_t)fine * NV + v) * Q + q) * nc + c);
   }
   __syncwarp();
-  const Real* op = A.ctr + (size_t)(A.copoff[bf] + t) * KC * NFP + (size_t)e * Q * NFP;
+  const int co = A.copoff[bf];  // first operator << 1 | one operator shared by every guard cell
+  const Real* op = A.ctr + ((size_t)(co >> 1) + ((co & 1) ? 0 : t)) * KC * NFP + (size_t)e * Q * NFP;
   for (int pr = lane; pr < NPAIR; pr += 32) {
     const int v = pr / NFP, fp = pr % NFP;
     Real acc0 = Real(0), acc1 = Real(0);

@@ -103,6 +103,30 @@ struct DeviceGuard {
   }
 };
 
+// Host vector whose elements are left uninitialised on resize: the large
+// per-build tables are first touched by the (threaded) loops that fill them.
+template <class T>
+struct NoInit : std::allocator<T> {
+  using value_type = T;
+  template <class U>
+  struct rebind {
+    using other = NoInit<U>;
+  };
+  NoInit() = default;
+  template <class U>
+  NoInit(const NoInit<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept {
+    ::new ((void*)p) U;
+  }
+  template <class U, class... A>
+  void construct(U* p, A&&... a) {
+    ::new ((void*)p) U(std::forward<A>(a)...);
+  }
+};
+template <class T>
+using hvec = std::vector<T, NoInit<T>>;
+
 }  // namespace
 
 struct dgf_forest {
@@ -138,6 +162,10 @@ struct dgf_forest {
   int nmf = 0, nmc = 0;
   double limiter = 0.0;  // positivity limiter bound (relative); 0 = off
   Buf ind;               // refinement indicator per leaf (kept between calls)
+  // host staging of the per-cell geometry, kept between builds so that a
+  // rebuild after a regrid reuses its pages
+  hvec<double> h_geo64, h_hcell;
+  hvec<float> h_geo32, h_hcell32;
   // boundary faces: per root face 0 outflow, 1 prescribed state (bstate_h)
   std::vector<int32_t> bctag;
   std::vector<double> bstate_h;
@@ -202,8 +230,10 @@ int pack_orient(const Orient& o, int d) {
   return v;
 }
 
-template <typename T>
-dgf_status upload(dgf_forest* f, dgf_forest::Buf& b, const std::vector<T>& v) {
+
+template <typename V>
+dgf_status upload(dgf_forest* f, dgf_forest::Buf& b, const V& v) {
+  using T = typename V::value_type;
   if (!ensure(f, b, sizeof(T) * std::max<size_t>(v.size(), 1))) return fail(DGF_ENOMEM, "device allocation failed");
   if (!v.empty())
     return cuda_check(cudaMemcpyAsync(b.ptr, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, f->stream),
@@ -211,9 +241,27 @@ dgf_status upload(dgf_forest* f, dgf_forest::Buf& b, const std::vector<T>& v) {
   return DGF_OK;
 }
 
-template <typename T>
-std::vector<T> convert(const std::vector<double>& v) {
-  return std::vector<T>(v.begin(), v.end());
+template <typename Fn>
+void parallel_for(int64_t n, Fn&& fn);
+
+// element-wise conversion (to the compute precision), in threaded chunks
+template <typename V, typename W>
+void convert_into(const V& v, W& out) {
+  using T = typename W::value_type;
+  out.clear();
+  out.resize(v.size());
+  constexpr int64_t kChunk = 1 << 16;
+  parallel_for(((int64_t)v.size() + kChunk - 1) / kChunk, [&](int64_t c) {
+    const size_t lo = (size_t)c * kChunk, hi = std::min(v.size(), lo + (size_t)kChunk);
+    for (size_t i = lo; i < hi; ++i) out[i] = (T)v[i];
+  });
+}
+
+template <typename T, typename V>
+hvec<T> convert(const V& v) {
+  hvec<T> out;
+  convert_into(v, out);
+  return out;
 }
 
 double phi(const Basis1D& B, int d, int m, const double* xi) {
@@ -361,9 +409,34 @@ dgf_status build_device(dgf_forest* f) {
   // geometry: per-cell trilinear coefficients (c >= 1) and sizes h; the
   // leaves are independent, so host threads take them in any order
   std::vector<std::vector<double>> coef(L);
-  std::vector<double> geo64((size_t)L * NG * nc), hcell((size_t)L * nc);
+  hvec<double>& geo64 = f->h_geo64;
+  hvec<double>& hcell = f->h_hcell;
+  geo64.clear();  // no copy of the old contents when the capacity grows
+  hcell.clear();
+  geo64.resize((size_t)L * NG * nc);
+  hcell.resize((size_t)L * nc);
   const Basis1D& B = f->basis;
-  for (int64_t i = 0; i < L; ++i) F.block_nodes(F.leaves[i]);  // fills the node cache; reads only below
+  {
+    // block nodes of every leaf and of its uncached ancestors, one level at a
+    // time: the blocks of a level in parallel from their parents' nodes
+    const std::vector<uint64_t> miss = F.uncached_nodes(F.leaves);
+    auto level_of = [](uint64_t k) {
+      int64_t r;
+      int lev, pos[3];
+      Forest::unkey(k, &r, &lev, pos);
+      return lev;
+    };
+    size_t lo = 0;
+    while (lo < miss.size()) {
+      const int lev = level_of(miss[lo]);
+      size_t hi = lo;
+      while (hi < miss.size() && level_of(miss[hi]) == lev) ++hi;
+      std::vector<std::vector<double>> X(hi - lo);
+      parallel_for((int64_t)(hi - lo), [&](int64_t j) { F.compute_nodes(miss[lo + j], X[j]); });
+      for (size_t j = lo; j < hi; ++j) F.put_nodes(miss[j], std::move(X[j - lo]));
+      lo = hi;
+    }
+  }
   parallel_for(L, [&](int64_t i) {
     F.cell_coefficients(F.leaves[i], coef[i]);
     for (int g = 0; g < NG; ++g)
@@ -432,21 +505,33 @@ dgf_status build_device(dgf_forest* f) {
   // combine operators for every finer-neighbour guard cell (Eqs. (13)-(14),
   // J-weighted, integrals by each child's Gauss rule), rotated into my frame
   const int nt = f->nt;
-  std::vector<double> cop;
   int64_t nops = 0;
   const int KC = (1 << d) * M;
   std::vector<int> fine_list;
   for (int64_t i = 0; i < L; ++i)
     for (int fc = 0; fc < nf; ++fc)
-      if (kind[i * nf + fc] == kFiner) {
-        copoff[i * nf + fc] = (int)nops;
-        nops += nt;
-        fine_list.push_back((int)(i * nf + fc));
-      }
+      if (kind[i * nf + fc] == kFiner) fine_list.push_back((int)(i * nf + fc));
+  // fine neighbours that are affine blocks of one Jacobian give every guard
+  // cell of a face the same operator: such a face stores one, flagged by bit
+  // 0 of its entry (copoff = first operator << 1 | shared)
+  std::vector<unsigned char> shared_op(fine_list.size(), 0);
+  for (size_t fi = 0; fi < fine_list.size(); ++fi) {
+    const int64_t i = fine_list[fi] / nf;
+    const int fc = fine_list[fi] % nf;
+    bool uniform = true;
+    for (int sb = 0; sb < (1 << (d - 1)) && uniform; ++sb) {
+      const int64_t fl = T.nbr[(i * nf + fc) * 4 + sb];
+      const int64_t f0 = T.nbr[(i * nf + fc) * 4];
+      uniform = affine[fl] &&
+                ameta[(size_t)fl * (d * d + 1) + d * d] == ameta[(size_t)f0 * (d * d + 1) + d * d];
+    }
+    shared_op[fi] = uniform;
+    copoff[i * nf + fc] = (int)(nops << 1) | (uniform ? 1 : 0);
+    nops += uniform ? 1 : nt;
+  }
   f->nfine = (int)fine_list.size();
-  cop.assign((size_t)nops * M * KC, 0.0);
   const int NFPh = f->NFP;
-  std::vector<double> ctr((size_t)nops * NFPh * KC, 0.0);
+  hvec<double> cop((size_t)nops * M * KC), ctr((size_t)nops * NFPh * KC);
   std::atomic<bool> singular{false};
   parallel_for((int64_t)fine_list.size(), [&](int64_t fi) {
     {
@@ -456,22 +541,9 @@ dgf_status build_device(dgf_forest* f) {
       const int a = fc >> 1, s = fc & 1;
       const int b2 = o.pi[a];
       const int s2 = o.sg[a] > 0 ? 1 - s : s;
-      // fine neighbours that are affine blocks of one Jacobian give every
-      // guard cell of this face the same operator: build it once
-      bool uniform = true;
-      for (int sb = 0; sb < (1 << (d - 1)) && uniform; ++sb) {
-        const int64_t fl = T.nbr[(i * nf + fc) * 4 + sb];
-        const int64_t f0 = T.nbr[(i * nf + fc) * 4];
-        uniform = affine[fl] &&
-                  ameta[(size_t)fl * (d * d + 1) + d * d] == ameta[(size_t)f0 * (d * d + 1) + d * d];
-      }
-      for (int t = 0; t < nt; ++t) {
-        if (uniform && t > 0) {
-          const size_t o0 = (size_t)copoff[i * nf + fc];
-          std::memcpy(&cop[(o0 + t) * M * KC], &cop[o0 * M * KC], sizeof(double) * M * KC);
-          std::memcpy(&ctr[(o0 + t) * NFPh * KC], &ctr[o0 * NFPh * KC], sizeof(double) * NFPh * KC);
-          continue;
-        }
+      const size_t o0 = (size_t)(copoff[i * nf + fc] >> 1);
+      const int tn = shared_op[fi] ? 1 : nt;
+      for (int t = 0; t < tn; ++t) {
         int g[3] = {0, 0, 0}, j = 0;
         for (int ax = 0; ax < d; ++ax) {
           if (ax == a) continue;
@@ -530,7 +602,7 @@ dgf_status build_device(dgf_forest* f) {
         }
         // evaluate the parent polynomial (neighbour frame) at my Gauss points:
         // my point p sits at neighbour coordinates xi_{pi[a]} = sigma_a x_{p_a}
-        double* dst = &cop[((size_t)copoff[i * nf + fc] + t) * M * KC];
+        double* dst = &cop[(o0 + t) * M * KC];
         for (int pt = 0; pt < M; ++pt) {
           double xs[3] = {0, 0, 0};
           int rem = pt;
@@ -549,7 +621,8 @@ dgf_status build_device(dgf_forest* f) {
         // trace operator: the guard cell's values on its face touching me
         // (xi_a = -1 on my + face, +1 on my - face) at my face points
         const std::vector<double>& ext = s ? B.lm : B.lp;
-        double* tdst = &ctr[((size_t)copoff[i * nf + fc] + t) * NFPh * KC];
+        double* tdst = &ctr[(o0 + t) * NFPh * KC];
+        std::fill(tdst, tdst + (size_t)NFPh * KC, 0.0);
         for (int fpp = 0; fpp < NFPh; ++fpp) {
           int dig[3] = {0, 0, 0}, rem = fpp;
           for (int ax = 0; ax < d; ++ax) {
@@ -674,7 +747,9 @@ dgf_status build_device(dgf_forest* f) {
     if (f->mortar && (st = upload(f, f->mw, mw))) return st;
   } else {
     if (f->mortar && (st = upload(f, f->mw, convert<float>(mw)))) return st;
-    if ((st = upload(f, f->geo, convert<float>(geo64))) || (st = upload(f, f->hcell, convert<float>(hcell))) ||
+    convert_into(geo64, f->h_geo32);
+    convert_into(hcell, f->h_hcell32);
+    if ((st = upload(f, f->geo, f->h_geo32)) || (st = upload(f, f->hcell, f->h_hcell32)) ||
         (st = upload(f, f->cop, convert<float>(cop))) || (st = upload(f, f->ctr, convert<float>(ctr))) ||
         (st = upload(f, f->ameta, convert<float>(ameta))))
       return st;

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <string>
 #include <unordered_map>
+#include <unordered_set>
 
 namespace dgf {
 
@@ -684,18 +685,12 @@ Forest::Tables Forest::tables() const {
 }
 
 // --------------------------------------------------------------- geometry
-const std::vector<double>& Forest::block_nodes(uint64_t k) {
-  auto it = node_cache_.find(k);
-  if (it != node_cache_.end()) return it->second;
-  int64_t r;
-  int lev, pos[3];
-  unkey(k, &r, &lev, pos);
-  if (lev == 1) return node_cache_[k] = root_nodes[r];
-  int pp[3] = {pos[0] >> 1, pos[1] >> 1, pos[2] >> 1};
-  const std::vector<double> PX = block_nodes(key(r, lev - 1, pp));  // copy: the cache may rehash
+// nodes of a child block from its parent's nodes: each child node is the
+// parent's (bi/tri)linear interpolant at the child node's position
+static void child_nodes(int d, int n, const int* pos, const std::vector<double>& PX, std::vector<double>& out) {
   const int nn1 = n + 1;
   const int nn = (int)std::pow(nn1, d);
-  std::vector<double> out(nn * d, 0.0);
+  out.assign((size_t)nn * d, 0.0);
   for (int li = 0; li < nn; ++li) {
     int I[3] = {0, 0, 0}, t = li;
     for (int a = 0; a < d; ++a) {
@@ -722,7 +717,57 @@ const std::vector<double>& Forest::block_nodes(uint64_t k) {
       for (int j = 0; j < d; ++j) out[li * d + j] += wgt * PX[J * d + j];
     }
   }
-  return node_cache_[k] = out;
+}
+
+const std::vector<double>& Forest::block_nodes(uint64_t k) {
+  auto it = node_cache_.find(k);
+  if (it != node_cache_.end()) return it->second;
+  int64_t r;
+  int lev, pos[3];
+  unkey(k, &r, &lev, pos);
+  if (lev == 1) return node_cache_[k] = root_nodes[r];
+  int pp[3] = {pos[0] >> 1, pos[1] >> 1, pos[2] >> 1};
+  const std::vector<double> PX = block_nodes(key(r, lev - 1, pp));  // copy: the cache may rehash
+  std::vector<double> out;
+  child_nodes(d, n, pos, PX, out);
+  return node_cache_[k] = std::move(out);
+}
+
+std::vector<uint64_t> Forest::uncached_nodes(const std::vector<uint64_t>& keys) const {
+  std::vector<uint64_t> out;
+  std::unordered_set<uint64_t> seen;
+  for (uint64_t k : keys) {
+    // walk up until a cached block (or a root)
+    while (!node_cache_.count(k) && seen.insert(k).second) {
+      out.push_back(k);
+      int64_t r;
+      int lev, pos[3];
+      unkey(k, &r, &lev, pos);
+      if (lev == 1) break;
+      int pp[3] = {pos[0] >> 1, pos[1] >> 1, pos[2] >> 1};
+      k = key(r, lev - 1, pp);
+    }
+  }
+  auto level_of = [](uint64_t k) {
+    int64_t r;
+    int lev, pos[3];
+    unkey(k, &r, &lev, pos);
+    return lev;
+  };
+  std::stable_sort(out.begin(), out.end(), [&](uint64_t a, uint64_t b) { return level_of(a) < level_of(b); });
+  return out;
+}
+
+void Forest::compute_nodes(uint64_t k, std::vector<double>& out) const {
+  int64_t r;
+  int lev, pos[3];
+  unkey(k, &r, &lev, pos);
+  if (lev == 1) {
+    out = root_nodes[r];
+    return;
+  }
+  int pp[3] = {pos[0] >> 1, pos[1] >> 1, pos[2] >> 1};
+  child_nodes(d, n, pos, node_cache_.at(key(r, lev - 1, pp)), out);
 }
 
 void Forest::cell_coefficients(uint64_t k, std::vector<double>& out) {

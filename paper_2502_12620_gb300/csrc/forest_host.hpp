@@ -102,6 +102,14 @@ class Forest {
 
   // geometry
   const std::vector<double>& block_nodes(uint64_t k);
+  // Filling the node cache for many blocks from several threads: the blocks
+  // (and their ancestors) whose nodes are not cached, in increasing level
+  // order; the nodes of one of them from its parent's cached nodes (reads
+  // the cache only, so blocks of one level may run concurrently); and the
+  // insertion of the result (one thread).
+  std::vector<uint64_t> uncached_nodes(const std::vector<uint64_t>& keys) const;
+  void compute_nodes(uint64_t k, std::vector<double>& out) const;
+  void put_nodes(uint64_t k, std::vector<double>&& X) { node_cache_[k] = std::move(X); }
   // trilinear coefficients X_c (c = 0..2^d-1, c = variable mask) of every
   // cell of a leaf: out[(c*d + j)*nc + cell]
   void cell_coefficients(uint64_t k, std::vector<double>& out);
