@@ -49,6 +49,8 @@ CASES = {
     "jitter3d_s3": lambda: W.jitter3d_forest(seed=3, n_seg=2),
     "cube_rot": lambda: W.periodic_cube_forest(3, n_seg=2, rotate_roots=True, seed=7),
     "outflow2d": lambda: dict(W.lattice_forest(2, 2, 1.0, 2, periodic=False), refine=[[(1, 1, (0, 0))]]),
+    "single_root2d": lambda: W.single_root_2d(n_seg=2),
+    "strip3_2d": lambda: W.three_root_strip_2d(n_seg=2),
 }
 
 

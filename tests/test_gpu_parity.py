@@ -41,6 +41,8 @@ SMALL = {
     "cube_rot_3d": lambda: W.periodic_cube_forest(2, n_seg=2, rotate_roots=True, seed=5),
     "outflow_2d": lambda: dict(W.lattice_forest(2, 2, 1.0, 4, periodic=False, jitter=0.1, seed=2),
                                refine=[[(0, 1, (0, 0))]]),
+    "single_root_2d": lambda: W.single_root_2d(n_seg=4),
+    "strip3_2d": lambda: W.three_root_strip_2d(n_seg=4),
 }
 
 
@@ -89,7 +91,7 @@ def test_free_stream_preserved(dgf, prec):
     assert np.max(np.abs(L)) < (1e-11 if prec == "fp64" else 2e-4) * scale
 
 
-@pytest.mark.parametrize("case", ["pair_2d", "jitter_3d_n2", "outflow_2d"])
+@pytest.mark.parametrize("case", ["pair_2d", "jitter_3d_n2", "outflow_2d", "strip3_2d"])
 def test_rk_steps_match_oracle(dgf, case):
     w = _small(case)
     f, S = _pair(dgf, w, 2, dgf.FP64, cfl=0.2)

@@ -55,12 +55,17 @@ def _inverse(code, d):
     return FO.orient_code(ipi, isg)
 
 
-@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("seed", [0, 1, 2, "strip3", "single"])
 def test_same_level_relations_are_mutual(seed):
-    w = W.jitter3d_forest(seed=seed, n_seg=2)
+    if seed == "strip3":
+        w = W.three_root_strip_2d(n_seg=2)
+    elif seed == "single":
+        w = W.single_root_2d(n_seg=2)
+    else:
+        w = W.jitter3d_forest(seed=seed, n_seg=2)
     F = FO.build(w)
     T = F.leaf_table()
-    d = 3
+    d = w["dim"]
     for i in range(len(F.leaves())):
         for f in range(2 * d):
             if T["kind"][i, f] != FO.SAME:

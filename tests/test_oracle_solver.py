@@ -129,6 +129,17 @@ def test_free_stream_preserved_on_jittered_rotated_multilevel(p, seed):
     assert np.max(np.abs(L)) < 1e-10
 
 
+@pytest.mark.parametrize("case", ["single_root", "strip3"])
+@pytest.mark.parametrize("p", [1, 3])
+def test_free_stream_preserved_on_paper_2d_root_sets(case, p):
+    """The self-glued single root and the three rotated rectangular roots of
+    the 2D convection test (Sec. 5), each with a level jump."""
+    w = W.single_root_2d(n_seg=4) if case == "single_root" else W.three_root_strip_2d(n_seg=4)
+    S = dg.Solver(FO.build(w), p)
+    L = S.residual(S.project(W.free_stream))
+    assert np.max(np.abs(L)) < 1e-10
+
+
 def test_free_stream_preserved_with_outflow_boundaries():
     w = W.lattice_forest(2, 2, 1.0, 2, periodic=False, jitter=0.1, seed=4)
     w["refine"] = [[(0, 1, (0, 0))]]

@@ -63,6 +63,8 @@ def lattice_forest(d, roots_per_axis, extent, n_seg, *, jitter=0.0,
                    rotate_roots=False, seed=0, origin=None, periodic=True):
     """Roots on a regular lattice of ``roots_per_axis^d`` blocks.
 
+    roots_per_axis: an int, or one count per axis (anisotropic roots, e.g.
+        (1, 3): a strip of three roots, each glued to itself across x).
     extent: physical edge length of the whole domain (cube/square).
     jitter: cell nodes strictly interior to the domain are moved by a seeded
         uniform offset in [-jitter*h, +jitter*h] per coordinate (h = cell size);
@@ -74,40 +76,54 @@ def lattice_forest(d, roots_per_axis, extent, n_seg, *, jitter=0.0,
     root_frame ((perm, signs) per root).
     """
     rng = np.random.default_rng(seed)
-    B = int(roots_per_axis)
+    if np.ndim(roots_per_axis) == 0:
+        Bs = (int(roots_per_axis),) * d
+    else:
+        Bs = tuple(int(b) for b in roots_per_axis)
+        assert len(Bs) == d
     n = int(n_seg)
-    G = B * n + 1  # global lattice nodes per axis
-    h = extent / (B * n)
+    G = tuple(B * n + 1 for B in Bs)  # global lattice nodes per axis
+    hs = [extent / (B * n) for B in Bs]
     org = np.zeros(d) if origin is None else np.asarray(origin, float)
 
     # global cell-node lattice, index order x fastest: lat[k][j][i] in 3D
-    axes = [org[a] + h * np.arange(G) for a in range(d)]
+    axes = [org[a] + hs[a] * np.arange(G[a]) for a in range(d)]
     grids = np.meshgrid(*axes, indexing="ij")  # grids[a][i0,i1,...]
-    lat = np.stack(grids, axis=-1)  # shape (G,)*d + (d,), index [i0,i1,..]
+    lat = np.stack(grids, axis=-1)  # shape G + (d,), index [i0,i1,..]
     if jitter > 0.0:
-        interior = np.ones((G,) * d, bool)
+        interior = np.ones(G, bool)
         for a in range(d):
             sl = [slice(None)] * d
             sl[a] = 0
             interior[tuple(sl)] = False
-            sl[a] = G - 1
+            sl[a] = G[a] - 1
             interior[tuple(sl)] = False
-        noise = rng.uniform(-jitter * h, jitter * h, size=lat.shape)
+        if len(set(Bs)) == 1:
+            noise = rng.uniform(-jitter * hs[0], jitter * hs[0], size=lat.shape)
+        else:
+            noise = rng.uniform(-jitter, jitter, size=lat.shape) * np.asarray(hs)
         lat = lat + noise * interior[..., None]
 
     # block-corner nodes: lattice points at multiples of n
-    C = B + 1
-    nodes = np.zeros((C ** d, d))
+    Cs = [B + 1 for B in Bs]
+    ncorner = int(np.prod(Cs))
+    nodes = np.zeros((ncorner, d))
     ids = {}
-    for flat in range(C ** d):
-        c = [(flat // C ** a) % C for a in range(d)]
+    for flat in range(ncorner):
+        c, r = [], flat
+        for a in range(d):
+            c.append(r % Cs[a])
+            r //= Cs[a]
         ids[tuple(c)] = flat
         nodes[flat] = lat[tuple(ci * n for ci in c)]
 
     rots = proper_rotations(d)
     root_corners, root_cell_nodes, root_block, root_frame = [], [], [], []
-    for flat in range(B ** d):
-        b = [(flat // B ** a) % B for a in range(d)]
+    for flat in range(int(np.prod(Bs))):
+        b, r = [], flat
+        for a in range(d):
+            b.append(r % Bs[a])
+            r //= Bs[a]
         if rotate_roots:
             perm, signs = rots[int(rng.integers(len(rots)))]
         else:
@@ -138,6 +154,28 @@ def lattice_forest(d, roots_per_axis, extent, n_seg, *, jitter=0.0,
                 root_cell_nodes=np.asarray(root_cell_nodes),
                 periodic=per, root_block=root_block, root_frame=root_frame,
                 extent=float(extent), origin=org)
+
+
+def single_root_2d(n_seg=4, refine=True):
+    """One square root covering the periodic unit square, glued to itself
+    across both axes (the first root set of the 2D convection test, Sec. 5);
+    with ``refine`` its corner child is refined again, so the 2:1 closure and
+    the level jumps wrap around the periodic faces."""
+    w = lattice_forest(2, 1, 1.0, n_seg)
+    if refine:
+        w["refine"] = [[(0, 1, (0, 0))], [(0, 2, (0, 0))]]
+    return w
+
+
+def three_root_strip_2d(n_seg=4, seed=1, refine=True):
+    """Three rectangular roots stacked along y over the periodic unit square,
+    each in a seeded rotated local frame (the third root set of the 2D
+    convection test, Sec. 5: roots in relative rotation); every root is glued
+    to itself across x and to its neighbours across y."""
+    w = lattice_forest(2, (1, 3), 1.0, n_seg, rotate_roots=True, seed=seed)
+    if refine:
+        w["refine"] = [[(1, 1, (0, 0))]]
+    return w
 
 
 def local_child_toward(frame, global_dir_bits):
