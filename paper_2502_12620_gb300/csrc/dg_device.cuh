@@ -270,6 +270,7 @@ struct StateIn {
   template <int VEC>
   __device__ __forceinline__ void vec(size_t i, Real (&a)[VEC]) const {
     static_assert(VEC * sizeof(Real) == 16, "16-byte groups");
+    static_assert(!COMP || sizeof(Real) == 4, "the compensated form computes in FP32");
     if constexpr (COMP) {
       double x[VEC];
 #pragma unroll
