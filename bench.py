@@ -11,6 +11,7 @@ on the last stage).  Metric: DG DOF-updates per second per RK stage
 (= DOF x 3 x steps / time).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                 [--workload jitter3d|cube8|cube8p1] [--nonconforming paper|mortar]
   python bench.py --serve [--serve-requests R] [--serve-active A]
   python bench.py --amr [--steps K]          (K regrid periods of 10 steps)
 
@@ -60,6 +61,7 @@ WORKLOADS = {
     "cube8p1": ("3d-euler-periodic-cube-8^3-roots-n8-p1", lambda: W.periodic_cube_forest(8), 1),
 }
 _SEL = ["jitter3d"]
+_NC = ["paper"]  # level-jump treatment: the paper's guard scheme or the mortar repair
 
 
 def the_workload():
@@ -237,7 +239,7 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def make(prec):
-        f = pkg.Forest.from_workload(w, p=p, precision=prec, device=local, cfl=0.1)
+        f = pkg.Forest.from_workload(w, p=p, precision=prec, device=local, cfl=0.1, nonconforming=_NC[0])
         f.set_stream(stream)
         f.project(vortex)
         return f
@@ -257,7 +259,7 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"workload": WORKLOADS[_SEL[0]][0], "value": value, "unit": "DOF-updates/s",
                               "ms_per_step": ms / args.steps, "dof": dof, "status_word": status,
-                              "clocks": ck.summary()}))
+                              "nonconforming": _NC[0], "clocks": ck.summary()}))
         return 0
 
     # instrumented replay of the same steps: per-kernel durations
@@ -349,7 +351,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[_SEL[0]][0], "leaves": nL, "cells": nL * nc, "p": p, "dof": dof,
                    "precision": "fp32", "l2_flush": "256 MiB write before every timed step",
-                   "parallelism": f"replicas x{ws}"},
+                   "nonconforming": _NC[0], "parallelism": f"replicas x{ws}"},
         "roofline": roof,
         "fp64": {"value": value64, "unit": "DOF-updates/s", "ms_per_step": ms64 / k64, "steps": k64},
         "fp32_comp": {"value": valuec, "unit": "DOF-updates/s", "ms_per_step": msc / kc, "steps": kc},
@@ -546,10 +548,13 @@ def main():
     ap.add_argument("--quick", action="store_true", help="FP32 timed steps only (profiling runs)")
     ap.add_argument("--serve", action="store_true", help="continuous-batching run instead of the step benchmark")
     ap.add_argument("--amr", action="store_true", help="dynamic-refinement blast run (steps = regrid periods)")
+    ap.add_argument("--nonconforming", default="paper", choices=["paper", "mortar"],
+                    help="level jumps: the paper's guard-cell scheme (default) or the conservative mortar repair")
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--serve-active", type=int, default=8)
     args = ap.parse_args()
     _SEL[0] = args.workload
+    _NC[0] = args.nonconforming
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

@@ -1383,14 +1383,19 @@ __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, R
   const int nt = D == 3 ? n * n : n;
   const int nc = D == 3 ? n * n * n : n * n;
   const auto& T = A.T;
+  // n and nt are powers of two: guard-cell digits by shifts and masks (the
+  // launch keeps the thread count below 2^32)
+  const int ln = 31 - __clz(n), lnt = (D - 1) * ln;
   if ((int)blockIdx.x >= n_fine_blocks) {
     const size_t total = (size_t)A.nL * 2 * D * nt * NV;
-    const size_t w = (size_t)(blockIdx.x - n_fine_blocks) * NTH + threadIdx.x;
-    if (w >= total) return;
-    const int t = (int)(w % nt);
-    const int v = (int)((w / nt) % NV);
-    const int f = (int)((w / ((size_t)nt * NV)) % (2 * D));
-    const int b = (int)(w / ((size_t)nt * NV * 2 * D));
+    const size_t wl = (size_t)(blockIdx.x - n_fine_blocks) * NTH + threadIdx.x;
+    if (wl >= total) return;
+    const unsigned w = (unsigned)wl;
+    const int t = (int)(w & (unsigned)(nt - 1));
+    const unsigned r = w >> lnt;
+    const int v = (int)(r % NV);
+    const int f = (int)((r / NV) % (2 * D));
+    const int b = (int)(r / (NV * 2 * D));
     const int kind = A.kind[b * 2 * D + f];
     if (kind == 2) return;
     Real* out_trace = A.out + (((size_t)b * 2 * D + f) * NV + v) * NFP * nt + t;
@@ -1404,7 +1409,6 @@ __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, R
     // orientation folded into signed strides (host-built descriptor)
     const int4 d0 = __ldg(reinterpret_cast<const int4*>(A.trd + (size_t)(b * 2 * D + f) * 8));
     const int4 d1 = __ldg(reinterpret_cast<const int4*>(A.trd + (size_t)(b * 2 * D + f) * 8 + 4));
-    const int ln = 31 - __clz(n);  // n is a power of two
     int g0 = t & (n - 1), g1 = t >> ln;
     int e0 = 0, e1 = 0;
     if (kind == 1) {
@@ -1477,10 +1481,10 @@ __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, R
   constexpr int NPAIR = NV * NFP;
   __shared__ Real sv[NW][NV][Q];
   __shared__ Real pv[NW][NPAIR];
-  const size_t item = blockIdx.x;
+  const unsigned item = blockIdx.x;
   const int lane = threadIdx.x & 31, e = threadIdx.x >> 5;
-  const int t = (int)(item % nt);
-  const int bf = A.fine_list[item / nt];
+  const int t = (int)(item & (unsigned)(nt - 1));
+  const int bf = A.fine_list[item >> lnt];
   const int b = bf / (2 * D), f = bf % (2 * D);
   const int a = f >> 1, s = f & 1;
   const int pk = A.orient[bf];

@@ -200,6 +200,7 @@ static cudaError_t guard_p(const RtGuard& r, cudaStream_t s) {
     // by the combine blocks unless the mortar passes replace them)
     constexpr int NTH = 32 << D;
     const size_t items = (size_t)r.nL * 2 * D * (D + 2) * nt;
+    if (items >= ((size_t)1 << 32)) return cudaErrorInvalidConfiguration;  // the kernel indexes in 32 bits
     const size_t ntb = (items + NTH - 1) / NTH;
     const int nfb = r.nfine * nt;
     const bool comp = std::is_same<Real, float>::value && r.comp;
