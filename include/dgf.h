@@ -264,8 +264,9 @@ dgf_status dgf_tuning(const dgf_forest* f, int32_t* zchunk, int32_t* resident_ct
 
 /* Kernel timing: when on, rk_step launches stage by stage (no graph) with
  * CUDA events around every kernel; dgf_kernel_times synchronises and returns
- * summed milliseconds and launch counts for the kernel classes
- * 0 = dt, 1 = guard, 2 = stage, then resets the sums. */
+ * summed milliseconds and kernel launch counts for the classes 0 = dt,
+ * 1 = guard (with the mortar passes and the limiter), 2 = stage, then resets
+ * the sums. */
 dgf_status dgf_set_timing(dgf_forest* f, int on);
 dgf_status dgf_kernel_times(dgf_forest* f, double* ms, int64_t* launches, int n_classes);
 

@@ -1028,7 +1028,9 @@ dgf_status autotune(dgf_forest* f) {
 // enqueue one time increment; timing mode records events around kernels
 dgf_status enqueue_step(dgf_forest* f) {
   DevScalars* s = (DevScalars*)f->scal.ptr;
-  auto rec = [&](int cls, auto&& launch) -> dgf_status {
+  // kernels one call launches: the guard call adds the mortar passes
+  const int guard_kernels = 1 + (f->mortar && f->nmf > 0) + (f->mortar && f->nmc > 0);
+  auto rec = [&](int cls, auto&& launch, int kernels = 1) -> dgf_status {
     cudaEvent_t a = nullptr, b = nullptr;
     if (f->timing) {
       cudaEventCreate(&a);
@@ -1039,7 +1041,7 @@ dgf_status enqueue_step(dgf_forest* f) {
     if (f->timing) {
       cudaEventRecord(b, f->stream);
       f->ev.push_back({a, b, cls});
-      f->launches[cls] += 1;
+      f->launches[cls] += kernels;
     }
     return cuda_check(e, cls == 0 ? "dt" : (cls == 1 ? "guard" : "stage"));
   };
@@ -1054,7 +1056,8 @@ dgf_status enqueue_step(dgf_forest* f) {
   const int src[3] = {0, 1, 2}, dst[3] = {1, 2, 0};
   const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
   for (int k = 0; k < 3; ++k) {
-    if ((st = rec(1, [&]() { return do_guard(f, guard_args(f, src[k], f->gtr.ptr, 1)); }))) return st;
+    if ((st = rec(1, [&]() { return do_guard(f, guard_args(f, src[k], f->gtr.ptr, 1)); }, guard_kernels)))
+      return st;
     if ((st = rec(2, [&]() { return do_stage(f, stage_args(f, src[k], dst[k], ca[k], cb[k], 0, k == 2)); })))
       return st;
     if (f->limiter > 0.0 && (st = rec(1, [&]() { return do_limit(f, f->U[dst[k]].ptr); }))) return st;
