@@ -137,6 +137,33 @@ def test_quad_points_match_oracle_geometry(dgf):
     assert np.allclose(f.quad_points(), S.quad_points(), rtol=0, atol=1e-14)
 
 
+def test_geometry_after_refine_and_coarsen_matches_a_fresh_build(dgf):
+    """Rebuilds after refinement and coarsening (node cache filled level by
+    level from several threads, geometry staging reused between builds) give
+    the same Gauss points as the oracle's forest with the same leaves, for
+    two levels below rotated jittered roots and back."""
+    from oracle import dg
+    w = W.jitter3d_forest(seed=5, n_seg=2)
+    w["refine"] = []
+    f = _host_forest(dgf, w)
+    O = FO.build(w)
+    for lev in (1, 2):
+        keys = [k for k in O.leaves() if k[1] == lev and k[0] % 2 == 0][:3]
+        f.refine([O.leaves().index(k) for k in keys])
+        O.refine(keys)
+        assert np.allclose(f.quad_points(), dg.Solver(O, 2).quad_points(), rtol=0, atol=1e-14)
+    parents = sorted({(k[0], k[1] - 1, tuple(x >> 1 for x in k[2])) for k in O.leaves() if k[1] == 3})
+    T = f.leaf_table()
+    first_child = []
+    for par in parents:
+        kid = (par[0], par[1] + 1, tuple(2 * x for x in par[2]))
+        first_child.append(O.leaves().index(kid))
+    f.coarsen(first_child)
+    O.coarsen(parents)
+    assert f.n_leaves == len(O.leaves())
+    assert np.allclose(f.quad_points(), dg.Solver(O, 2).quad_points(), rtol=0, atol=1e-14)
+
+
 def test_bad_descriptions_are_rejected(dgf):
     w = W.rotated_pair_2d()
     with pytest.raises(dgf.DgfError) as e:
