@@ -1368,10 +1368,12 @@ __global__ void __launch_bounds__(32 << D) k_guard_fine(const GuardArgs<D, P, Re
 }
 
 // Guard traces for the time step (mode 1), one launch: the first
-// n_fine_blocks blocks run the finer-face combine (one block per finer face,
-// guard cell and var, one warp per fine child), the remaining blocks compute
-// the traces of same-level, coarser and outflow faces, one thread per
-// (leaf, face, guard cell, var) as in k_guard.
+// n_fine_blocks blocks run the finer-face combine (one block per finer face
+// and guard cell, all vars, one warp per fine child), the remaining blocks
+// compute the traces of same-level, coarser, outflow and prescribed-state
+// faces, one thread per (leaf, face, guard cell, var), from the host-built
+// face-trace descriptors (source cell and face points as affine functions
+// of my guard-cell and face-point digits).
 template <int D, int P, typename Real, bool COMP = false>
 __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, Real> A, int n_fine_blocks) {
   const StateIn<Real, COMP> S{A.U, A.U64, A.Din};
