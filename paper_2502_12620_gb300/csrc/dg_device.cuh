@@ -240,26 +240,33 @@ struct StageArgs {
   int* status;
   Real ca, cb, gamma;
   int mode, last;
-  const double* __restrict__ U64;  // compensated form: u^n in FP64 (stage input base)
+  const double* __restrict__ U64;  // compensated form: u^n in FP64 (the last stage's update)
+  const float* __restrict__ Uhi;   // compensated form: u^n = hi + lo in FP32 (every stage input)
+  const float* __restrict__ Ulo;
   const float* __restrict__ Din;   // compensated form: delta^(k), null at stage 1
   double* __restrict__ U64out;     // compensated form, last stage: u^(n+1) in FP64
   const unsigned char* __restrict__ fluxmask;  // [b] bit f: gtr holds face f's flux (mortar), or null
   Tab<P + 1, Real> T;
 };
 
-// Stage input u^(k) at a flat index: one array (plain), or u^n in FP64 plus
-// the FP32 increment delta^(k) (compensated SSP-RK3: the state accumulates
-// in FP64, each stage changes it by an O(dt) increment kept in FP32).
+// Stage input u^(k) at a flat index: one array (plain), or u^n plus the FP32
+// increment delta^(k) (compensated SSP-RK3: the state accumulates in FP64,
+// each stage changes it by an O(dt) increment kept in FP32).  The stages read
+// u^n as the FP32 pair hi + lo (hi = fl(u^n), lo = fl(u^n - hi), split once per
+// time step), so the input hi + (lo + delta) costs FP32 adds only; it is
+// within one FP32 rounding of fl(u^n + delta).
 template <typename Real, bool COMP>
 struct StateIn {
   const Real* u;
-  const double* u64;
+  const double* u64;  // u^n in FP64 (the last stage's update reads it)
+  const float* hi;
+  const float* lo;
   const float* d;
   __device__ __forceinline__ Real operator()(size_t i) const {
     if constexpr (COMP) {
-      double x = __ldcg(&u64[i]);
-      if (d) x += (double)__ldcg(&d[i]);
-      return (Real)x;
+      float x = __ldcg(&lo[i]);
+      if (d) x += __ldcg(&d[i]);
+      return (Real)(__ldcg(&hi[i]) + x);
     } else {
       return u[i];
     }
@@ -272,22 +279,19 @@ struct StateIn {
     static_assert(VEC * sizeof(Real) == 16, "16-byte groups");
     static_assert(!COMP || sizeof(Real) == 4, "the compensated form computes in FP32");
     if constexpr (COMP) {
-      double x[VEC];
-#pragma unroll
-      for (int e = 0; e < VEC; e += 2) {
-        const double2 q = __ldcg(reinterpret_cast<const double2*>(u64 + i + e));
-        x[e] = q.x;
-        x[e + 1] = q.y;
-      }
+      const float4 h = __ldcg(reinterpret_cast<const float4*>(hi + i));
+      float4 x = __ldcg(reinterpret_cast<const float4*>(lo + i));
       if (d) {
         const float4 q = __ldcg(reinterpret_cast<const float4*>(d + i));
-        x[0] += (double)q.x;
-        x[1] += (double)q.y;
-        x[2] += (double)q.z;
-        x[3] += (double)q.w;
+        x.x += q.x;
+        x.y += q.y;
+        x.z += q.z;
+        x.w += q.w;
       }
-#pragma unroll
-      for (int e = 0; e < VEC; ++e) a[e] = (Real)x[e];
+      a[0] = h.x + x.x;
+      a[1] = h.y + x.y;
+      a[2] = h.z + x.z;
+      a[3] = h.w + x.w;
     } else {
       using V = typename std::conditional<sizeof(Real) == 4, float4, double2>::type;
       const V q = __ldcg(reinterpret_cast<const V*>(u + i));
@@ -306,6 +310,8 @@ struct GuardArgs {
   int nL, n, mode;  // mode 0: modal guard cells; 1: traces
   const Real* __restrict__ U;
   const double* __restrict__ U64;  // compensated form: u^n in FP64
+  const float* __restrict__ Uhi;   // compensated form: u^n = hi + lo in FP32
+  const float* __restrict__ Ulo;
   const float* __restrict__ Din;   // compensated form: delta^(k), null at stage 1
   Real* __restrict__ out;
   const int* __restrict__ kind;    // [b][f]
@@ -551,8 +557,8 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
     const Real* __restrict__ Ub = A.U + (size_t)b * NV * Q * nc;
     const Real* __restrict__ Unb = A.Un + (size_t)b * NV * Q * nc;
     const size_t boff = (size_t)b * NV * Q * nc;
-    const StateIn<Real, COMP> Sb{A.U + boff, COMP ? A.U64 + boff : nullptr,
-                                 (COMP && A.Din) ? A.Din + boff : nullptr};
+    const StateIn<Real, COMP> Sb{A.U + boff, COMP ? A.U64 + boff : nullptr, COMP ? A.Uhi + boff : nullptr,
+                                 COMP ? A.Ulo + boff : nullptr, (COMP && A.Din) ? A.Din + boff : nullptr};
     Real* __restrict__ Ob = A.Uout + (size_t)b * NV * Q * nc;
     const Real* __restrict__ Gb = A.geo + (size_t)b * NG * nc;
     const Real* __restrict__ Tb = A.gtr + (size_t)b * 2 * D * NV * NFP * nt;
@@ -571,8 +577,10 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
           const int r = w / lpr, l = w - r * lpr;
           if constexpr (COMP) {
             if (D == 3 && k + 1 < n) {
-              prefetch_l2(Sb.u64 + (size_t)r * nc + cbase + LAY + l * (128 / sizeof(Real)) / 2);
-              prefetch_l2(Sb.u64 + (size_t)r * nc + cbase + LAY + l * (128 / sizeof(Real)) / 2 + 16);
+              const size_t o = (size_t)r * nc + cbase + LAY + l * (128 / sizeof(Real));
+              prefetch_l2(Sb.hi + o);
+              prefetch_l2(Sb.lo + o);
+              if (Sb.d) prefetch_l2(Sb.d + o);
             }
           } else {
             if (D == 3 && k + 1 < n) prefetch_l2(Ub + (size_t)r * nc + cbase + LAY + l * (128 / sizeof(Real)));
@@ -1114,7 +1122,7 @@ __device__ __forceinline__ int map_point(const int* js, int pk) {
 // one thread per (leaf, face, guard cell t, var); finer faces are skipped
 template <int D, int P, typename Real, bool COMP = false>
 __global__ void __launch_bounds__(128) k_guard(const GuardArgs<D, P, Real> A) {
-  const StateIn<Real, COMP> S{A.U, A.U64, A.Din};
+  const StateIn<Real, COMP> S{A.U, A.U64, A.Uhi, A.Ulo, A.Din};
   constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
   const int n = A.n;
   const int nt = D == 3 ? n * n : n;
@@ -1289,7 +1297,7 @@ __global__ void __launch_bounds__(128) k_guard(const GuardArgs<D, P, Real> A) {
 // added in fixed child order, and (mode 1) the trace at my face is formed.
 template <int D, int P, typename Real, bool COMP = false>
 __global__ void __launch_bounds__(32 << D) k_guard_fine(const GuardArgs<D, P, Real> A) {
-  const StateIn<Real, COMP> S{A.U, A.U64, A.Din};
+  const StateIn<Real, COMP> S{A.U, A.U64, A.Uhi, A.Ulo, A.Din};
   constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
   constexpr int NW = 1 << D;
   constexpr int KC = NW * Q;
@@ -1376,7 +1384,7 @@ __global__ void __launch_bounds__(32 << D) k_guard_fine(const GuardArgs<D, P, Re
 // of my guard-cell and face-point digits).
 template <int D, int P, typename Real, bool COMP = false>
 __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, Real> A, int n_fine_blocks) {
-  const StateIn<Real, COMP> S{A.U, A.U64, A.Din};
+  const StateIn<Real, COMP> S{A.U, A.U64, A.Uhi, A.Ulo, A.Din};
   constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
   constexpr int NW = 1 << D;
   constexpr int KC = NW * Q;
@@ -1552,7 +1560,7 @@ __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, R
 // takes it as the face flux.  One thread per (face, guard cell, face point).
 template <int D, int P, typename Real, bool COMP = false>
 __global__ void __launch_bounds__(128) k_mortar_fine(const GuardArgs<D, P, Real> A) {
-  const StateIn<Real, COMP> S{A.U, A.U64, A.Din};
+  const StateIn<Real, COMP> S{A.U, A.U64, A.Uhi, A.Ulo, A.Din};
   constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
   constexpr int NG = ((1 << D) - 1) * D;
   const int n = A.n;

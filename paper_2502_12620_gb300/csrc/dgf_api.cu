@@ -64,6 +64,17 @@ __global__ void k_dt(DevScalars* s, double cfl) {
 
 __global__ void k_reset_lam(DevScalars* s) { s->lam_bits = kInfBits; }
 
+// compensated form: u^n as the FP32 pair hi = fl(u^n), lo = fl(u^n - hi)
+// (u^n - hi is exact in FP64), so hi + lo carries u^n to about 48 bits
+__global__ void k_split(const double* __restrict__ u, float* __restrict__ hi, float* __restrict__ lo, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double x = u[i];
+  const float h = (float)x;
+  hi[i] = h;
+  lo[i] = (float)(x - (double)h);
+}
+
 __global__ void k_widen(const float* __restrict__ in, double* __restrict__ out, size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = (double)in[i];
@@ -152,6 +163,7 @@ struct dgf_forest {
     size_t bytes = 0;
   };
   Buf U64[2], hcell64, gmod64;
+  Buf Uhi, Ulo;  // compensated form: u^n as the FP32 pair hi + lo, split once per step
   cudaGraphExec_t graph_alt = nullptr;  // compensated form: graph of the other u^n buffer
   Buf U[3], geo, geo64, hcell, gtr, gmod, cop, ctr, kind, nbr, orient, qbits, copoff, part, scal, tot,
       dtout, nodal, fine, affine, ameta, trd;
@@ -757,10 +769,14 @@ dgf_status build_device(dgf_forest* f) {
   const size_t sbytes = (size_t)L * f->nv * M * nc * f->esize;
   for (int k = 0; k < 3; ++k)
     if (!ensure(f, f->U[k], sbytes)) return fail(DGF_ENOMEM, "state allocation failed");
-  if (f->comp)
+  if (f->comp) {
     for (int k = 0; k < 2; ++k)
       if (!ensure(f, f->U64[k], (size_t)L * f->nv * M * nc * sizeof(double)))
         return fail(DGF_ENOMEM, "state allocation failed");
+    if (!ensure(f, f->Uhi, (size_t)L * f->nv * M * nc * sizeof(float)) ||
+        !ensure(f, f->Ulo, (size_t)L * f->nv * M * nc * sizeof(float)))
+      return fail(DGF_ENOMEM, "state allocation failed");
+  }
   if (!ensure(f, f->gtr, (size_t)L * nf * f->nv * f->NFP * nt * f->esize) ||
       !ensure(f, f->part, (size_t)L * nc * f->nv * sizeof(double)))
     return fail(DGF_ENOMEM, "scratch allocation failed");
@@ -832,6 +848,8 @@ RtStage stage_args(dgf_forest* f, int src, int dst, double ca, double cb, int mo
   if (f->comp) {
     r.comp = 1;
     r.U64 = (const double*)f->U64[f->cur].ptr;
+    r.Uhi = (const float*)f->Uhi.ptr;
+    r.Ulo = (const float*)f->Ulo.ptr;
     r.Din = src == 0 ? nullptr : (const float*)f->U[src].ptr;
     r.U64out = (double*)f->U64[1 - f->cur].ptr;
   }
@@ -873,6 +891,8 @@ RtGuard guard_args(dgf_forest* f, int src, void* out, int mode) {
   if (f->comp) {
     r.comp = 1;
     r.U64 = (const double*)f->U64[f->cur].ptr;
+    r.Uhi = (const float*)f->Uhi.ptr;
+    r.Ulo = (const float*)f->Ulo.ptr;
     r.Din = src == 0 ? nullptr : (const float*)f->U[src].ptr;
   }
   r.T = f->tab;
@@ -905,6 +925,16 @@ cudaError_t do_stage(dgf_forest* f, const RtStage& r) {
   if (f->d == 2) return f->precision == DGF_FP64 ? launch_stage<2, double>(r, f->stream) : launch_stage<2, float>(r, f->stream);
   return f->precision == DGF_FP64 ? launch_stage<3, double>(r, f->stream) : launch_stage<3, float>(r, f->stream);
 }
+// compensated form: split u^n into the FP32 pair the stage inputs read
+// (nothing to do in the other precisions)
+cudaError_t split_state(dgf_forest* f) {
+  if (!f->comp) return cudaSuccess;
+  const size_t n = (size_t)f->nL * f->nv * f->M * f->nc;
+  k_split<<<(unsigned)((n + 255) / 256), 256, 0, f->stream>>>((const double*)f->U64[f->cur].ptr, (float*)f->Uhi.ptr,
+                                                                (float*)f->Ulo.ptr, n);
+  return cudaGetLastError();
+}
+
 cudaError_t do_guard(dgf_forest* f, const RtGuard& r) {
   if (f->d == 2) return f->precision == DGF_FP64 ? launch_guard<2, double>(r, f->stream) : launch_guard<2, float>(r, f->stream);
   return f->precision == DGF_FP64 ? launch_guard<3, double>(r, f->stream) : launch_guard<3, float>(r, f->stream);
@@ -989,7 +1019,8 @@ dgf_status autotune(dgf_forest* f) {
       return DGF_OK;
     }
   }
-  dgf_status st = cuda_check(do_guard(f, guard_args(f, 0, f->gtr.ptr, 1)), "guard");
+  dgf_status st = cuda_check(split_state(f), "split");
+  if (!st) st = cuda_check(do_guard(f, guard_args(f, 0, f->gtr.ptr, 1)), "guard");
   if (st) return st;
   cudaEvent_t a, b;
   cudaEventCreate(&a);
@@ -1050,6 +1081,7 @@ dgf_status enqueue_step(dgf_forest* f) {
     return cudaGetLastError();
   });
   if (st) return st;
+  if (f->comp && (st = rec(0, [&]() { return split_state(f); }))) return st;
   // Shu-Osher SSP-RK3: (src, dst, a, b): dst = a U^n + b (src + dt L(src)).
   // Compensated form: U[1], U[2] hold the FP32 increments delta^(1), delta^(2)
   // (delta^(k+1) = b (delta^(k) + dt L)), the last stage writes u^(n+1) in FP64.
@@ -1200,7 +1232,7 @@ dgf_status dgf_forest_destroy(dgf_forest* f) {
     dgf_forest::Buf* bufs[] = {&f->U[0], &f->U[1], &f->U[2], &f->geo, &f->geo64, &f->hcell, &f->gtr,
                                &f->gmod, &f->cop, &f->ctr, &f->kind, &f->nbr, &f->orient, &f->qbits, &f->copoff,
                                &f->part, &f->scal, &f->tot, &f->dtout, &f->nodal, &f->fine, &f->affine, &f->ameta,
-                               &f->U64[0], &f->U64[1], &f->hcell64, &f->gmod64, &f->fluxmask,
+                               &f->U64[0], &f->U64[1], &f->hcell64, &f->gmod64, &f->Uhi, &f->Ulo, &f->fluxmask,
                                &f->mfine, &f->mcoarse, &f->mw, &f->msrc, &f->ind, &f->bstate, &f->trd};
     for (auto* b : bufs) dev_free(f, *b);
     if (f->own_stream && f->stream) cudaStreamDestroy(f->stream);
@@ -1447,7 +1479,8 @@ dgf_status dgf_fill_guardcells(dgf_forest* f, void* guard, int is_device) {
   DeviceGuard dg(f->device);
   const size_t count = (size_t)f->nL * 2 * f->d * f->nv * f->M * f->nt;
   if (!ensure(f, f->gmod, count * f->esize)) return fail(DGF_ENOMEM, "guard allocation failed");
-  dgf_status st = cuda_check(do_guard(f, guard_args(f, 0, f->gmod.ptr, 0)), "guard");
+  dgf_status st = cuda_check(split_state(f), "split");
+  if (!st) st = cuda_check(do_guard(f, guard_args(f, 0, f->gmod.ptr, 0)), "guard");
   if (st) return st;
   const bool dbl = f->precision == DGF_FP64;
   if ((st = cuda_check(do_convert(f, f->gmod.ptr, (size_t)f->nL * 2 * f->d, f->nt, 0, dbl), "to modal"))) return st;
@@ -1465,7 +1498,8 @@ dgf_status dgf_dg_residual(dgf_forest* f, void* dst, int is_device) {
   if (!dst) return fail(DGF_EINVAL, "null destination");
   if (!f->have_state) return fail(DGF_ESTATE, "no state set");
   DeviceGuard dg(f->device);
-  dgf_status st = cuda_check(do_guard(f, guard_args(f, 0, f->gtr.ptr, 1)), "guard");
+  dgf_status st = cuda_check(split_state(f), "split");
+  if (!st) st = cuda_check(do_guard(f, guard_args(f, 0, f->gtr.ptr, 1)), "guard");
   if (st) return st;
   if ((st = cuda_check(do_stage(f, stage_args(f, 0, 1, 0.0, 1.0, 1, 0)), "stage"))) return st;
   const bool dbl = f->precision == DGF_FP64;

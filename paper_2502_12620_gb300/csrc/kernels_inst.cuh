@@ -151,6 +151,8 @@ static cudaError_t stage_p(const RtStage& r, cudaStream_t s) {
   a.mode = r.mode;
   a.last = r.last;
   a.U64 = r.U64;
+  a.Uhi = r.Uhi;
+  a.Ulo = r.Ulo;
   a.Din = r.Din;
   a.U64out = r.U64out;
   a.fluxmask = r.fluxmask;
@@ -172,6 +174,8 @@ static cudaError_t guard_p(const RtGuard& r, cudaStream_t s) {
   a.mode = r.mode;
   a.U = (const Real*)r.U;
   a.U64 = r.U64;
+  a.Uhi = r.Uhi;
+  a.Ulo = r.Ulo;
   a.Din = r.Din;
   a.out = (Real*)r.out;
   a.kind = r.kind;

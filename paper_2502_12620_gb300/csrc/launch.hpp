@@ -34,6 +34,8 @@ struct RtStage {
   int mode, last;
   int comp;             // compensated form (FP32 kernels only)
   const double* U64;    // compensated: u^n
+  const float* Uhi;     // compensated: u^n = hi + lo in FP32, read by every stage
+  const float* Ulo;
   const float* Din;     // compensated: delta^(k) or null
   double* U64out;       // compensated, last stage: u^(n+1)
   const unsigned char* fluxmask;  // mortar mode: per block, faces whose flux is in gtr
@@ -44,6 +46,8 @@ struct RtGuard {
   int p, nL, n, mode;
   int comp;
   const double* U64;
+  const float* Uhi;
+  const float* Ulo;
   const float* Din;
   const void* U;
   void* out;

@@ -66,7 +66,8 @@ def leaf_count(workload):
 
 def footprint_bytes(workload, p, precision=FP32):
     """Device bytes a solve holds while resident, estimated before it is
-    built: three stage buffers (two more in FP64 for the compensated form),
+    built: three stage buffers (for the compensated form two more in FP64
+    and u^n split into two FP32 arrays),
     the cell map coefficients and cell sizes in the compute precision and in
     FP64, the guard traces and modal guard cells, the per-leaf tables and
     1 MiB for the finer-face operators and scalars."""
@@ -76,7 +77,7 @@ def footprint_bytes(workload, p, precision=FP32):
     M = N ** d
     es = 8 if precision == FP64 else 4
     dof = L * nc * M * (d + 2)
-    state = 3 * dof * es + (2 * dof * 8 if precision == FP32_COMP else 0)
+    state = 3 * dof * es + (2 * dof * 8 + 2 * dof * 4 if precision == FP32_COMP else 0)
     geo = L * nc * (((1 << d) - 1) * d + 1) * (es + 8)
     faces = L * 2 * d * (d + 2) * n ** (d - 1)
     guard = faces * N ** (d - 1) * es + faces * M * (es + 8)
