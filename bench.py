@@ -43,7 +43,7 @@ HBM_FALLBACK = 6800.0
 # DRAM bytes (read + write) per k_stage launch of this workload, averaged over
 # the three stages of one time step, from the ncu capture summarised in
 # profiles/k_stage_jitter3d_p2_fp32.md; set to None when the kernel changes.
-STAGE_TRAFFIC_BYTES = 42.71e6
+STAGE_TRAFFIC_BYTES = 42.67e6
 
 
 def peaks():
