@@ -740,8 +740,8 @@ dgf_status build_device(dgf_forest* f) {
   {
     std::vector<double> bs(f->nv, 0.0);
     if (!f->bstate_h.empty()) bs = f->bstate_h;
-    if ((st = f->precision == DGF_FP64 ? upload(f, f->bstate, bs) : upload(f, f->bstate, convert<float>(bs))))
-      return st;
+    st = f->precision == DGF_FP64 ? upload(f, f->bstate, bs) : upload(f, f->bstate, convert<float>(bs));
+    if (st) return st;
   }
   if ((st = upload(f, f->kind, kind)) || (st = upload(f, f->nbr, nbr)) || (st = upload(f, f->orient, orient)) ||
       (st = upload(f, f->qbits, qbits)) || (st = upload(f, f->copoff, copoff)) || (st = upload(f, f->geo64, geo64)) ||
