@@ -11,7 +11,8 @@ on the last stage).  Metric: DG DOF-updates per second per RK stage
 (= DOF x 3 x steps / time).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                 [--workload jitter3d|cube8|cube8p1] [--nonconforming paper|mortar]
+                 [--workload jitter3d|jitter3dp1|jitter3dp3|cube8|cube8p1|cube8p3]
+                 [--nonconforming paper|mortar]
   python bench.py --serve [--serve-requests R] [--serve-active A]
   python bench.py --amr [--steps K]          (K regrid periods of 10 steps)
 
@@ -59,6 +60,9 @@ WORKLOADS = {
     # larger affine case for profiling (state 141 MB FP32, above L2)
     "cube8": ("3d-euler-periodic-cube-8^3-roots-n8-p2", lambda: W.periodic_cube_forest(8), 2),
     "cube8p1": ("3d-euler-periodic-cube-8^3-roots-n8-p1", lambda: W.periodic_cube_forest(8), 1),
+    "cube8p3": ("3d-euler-periodic-cube-8^3-roots-n8-p3", lambda: W.periodic_cube_forest(8), 3),
+    "jitter3dp1": ("3d-euler-jittered-cube-8roots-71leaves-n8-p1", lambda: W.jitter3d_forest(seed=0), 1),
+    "jitter3dp3": ("3d-euler-jittered-cube-8roots-71leaves-n8-p3", lambda: W.jitter3d_forest(seed=0), 3),
 }
 _SEL = ["jitter3d"]
 _NC = ["paper"]  # level-jump treatment: the paper's guard scheme or the mortar repair
