@@ -342,10 +342,18 @@ struct GuardArgs {
 #ifndef DGF_STAGE_NT_F32
 #define DGF_STAGE_NT_F32 448
 #endif
+// FP32 at p <= 1 (build-time tuning knobs, the same as p = 2 by default)
+#ifndef DGF_STAGE_NT_F32_P1
+#define DGF_STAGE_NT_F32_P1 DGF_STAGE_NT_F32
+#endif
+#ifndef DGF_STAGE_MINB_F32_P1
+#define DGF_STAGE_MINB_F32_P1 2
+#endif
 template <int P, typename Real>
 struct StageCfg {
-  static constexpr int NT = sizeof(Real) == 4 ? (P <= 2 ? DGF_STAGE_NT_F32 : 512) : (P <= 1 ? 512 : 256);
-  static constexpr int MINB = (sizeof(Real) == 4 && P <= 2) ? 2 : 1;
+  static constexpr int NT = sizeof(Real) == 4 ? (P <= 1 ? DGF_STAGE_NT_F32_P1 : P <= 2 ? DGF_STAGE_NT_F32 : 512)
+                                              : (P <= 1 ? 512 : 256);
+  static constexpr int MINB = sizeof(Real) == 4 ? (P <= 1 ? DGF_STAGE_MINB_F32_P1 : P <= 2 ? 2 : 1) : 1;
 };
 
 // shared-memory footprint of the stage kernel (bytes): nodal layer, residual
