@@ -70,7 +70,9 @@ typedef int32_t dgf_status;
  * u^n is kept in FP64, each stage keeps its increment delta^(k) = u^(k) - u^n
  * in FP32 (delta^(k+1) = b_k (delta^(k) + dt L(u^n + delta^(k))), b = 1, 1/4,
  * 2/3) and u^(n+1) = u^n + delta^(3) is formed in FP64; the residual runs in
- * FP32.  The state, residual and guard cells at this ABI are double. */
+ * FP32, reading u^n as the FP32 pair hi + lo (hi = fl(u^n), lo = fl(u^n - hi),
+ * split once per step) so that a stage input costs FP32 adds only.  The
+ * state, residual and guard cells at this ABI are double. */
 #define DGF_FP32_COMP 2
 
 /* Fluxes across a level jump.  DGF_NC_PAPER: each side evaluates the
