@@ -338,16 +338,18 @@ struct GuardArgs {
 };
 
 // threads per CTA and CTAs per SM of the stage kernel (registers and shared
-// memory decide: FP32 up to p=2 runs 2 x 448 threads per SM, 73 registers)
+// memory decide: FP32 at p = 2 runs 2 x 448 threads per SM, 72 registers)
 #ifndef DGF_STAGE_NT_F32
 #define DGF_STAGE_NT_F32 448
 #endif
-// FP32 at p <= 1 (build-time tuning knobs, the same as p = 2 by default)
+// FP32 at p <= 1: smaller CTAs, four per SM (a layer's line work is a third
+// of p = 2's; measured faster on forests of a thousand leaves and more,
+// slower on the 71-leaf cube)
 #ifndef DGF_STAGE_NT_F32_P1
-#define DGF_STAGE_NT_F32_P1 DGF_STAGE_NT_F32
+#define DGF_STAGE_NT_F32_P1 256
 #endif
 #ifndef DGF_STAGE_MINB_F32_P1
-#define DGF_STAGE_MINB_F32_P1 2
+#define DGF_STAGE_MINB_F32_P1 4
 #endif
 template <int P, typename Real>
 struct StageCfg {
