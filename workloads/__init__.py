@@ -133,11 +133,13 @@ def lattice_forest(d, roots_per_axis, extent, n_seg, *, jitter=0.0,
             kap = [(k >> a) & 1 for a in range(d)]
             off = _local_to_global_index(kap, 1, perm, signs)
             corners.append(ids[tuple(b[a] + off[a] for a in range(d))])
-        cn = np.zeros(((n + 1) ** d, d))
-        for li in range((n + 1) ** d):
-            I = [(li // (n + 1) ** a) % (n + 1) for a in range(d)]
-            g = _local_to_global_index(I, n, perm, signs)
-            cn[li] = lat[tuple(b[a] * n + g[a] for a in range(d))]
+        # local node li (x fastest) -> global lattice index, all at once
+        li = np.arange((n + 1) ** d)
+        gidx = [None] * d
+        for a in range(d):
+            Ia = (li // (n + 1) ** a) % (n + 1)
+            gidx[perm[a]] = b[perm[a]] * n + (Ia if signs[a] > 0 else n - Ia)
+        cn = lat[tuple(gidx)]
         root_corners.append(corners)
         root_cell_nodes.append(cn)
         root_block.append(tuple(b))
