@@ -223,6 +223,13 @@ class Forest:
         except Exception:
             pass
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
     @property
     def device_bytes(self):
         """Device bytes the library holds for this forest (0 when it allocates

@@ -164,6 +164,13 @@ def test_geometry_after_refine_and_coarsen_matches_a_fresh_build(dgf):
     assert np.allclose(f.quad_points(), dg.Solver(O, 2).quad_points(), rtol=0, atol=1e-14)
 
 
+def test_forest_closes_as_a_context_manager(dgf):
+    with _host_forest(dgf, W.rotated_pair_2d()) as f:
+        assert f.n_leaves > 0 and f.h
+    assert f.h is None
+    f.close()  # closing twice is harmless
+
+
 def test_bad_descriptions_are_rejected(dgf):
     w = W.rotated_pair_2d()
     with pytest.raises(dgf.DgfError) as e:
