@@ -41,10 +41,12 @@ import workloads as W  # noqa: E402
 
 WORKLOAD = "3d-euler-jittered-cube-8roots-71leaves-n8-p2"
 HBM_FALLBACK = 6800.0
-# DRAM bytes (read + write) per k_stage launch of this workload, averaged over
-# the three stages of one time step, from the ncu capture summarised in
-# profiles/k_stage_jitter3d_p2_fp32.md; set to None when the kernel changes.
-STAGE_TRAFFIC_BYTES = 42.67e6
+# DRAM bytes (read + write) per stage-kernel launch, averaged over the three
+# stages of one time step (ncu dram__bytes_read.sum + dram__bytes_write.sum,
+# cold L2), by workload, for the stage kernel as it is now; a workload
+# without a capture of the current kernel reports null.
+STAGE_TRAFFIC_BYTES = {}
+TRAFFIC_HOW = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, cold L2, mean of the 3 stages of a step"
 
 
 def peaks():
@@ -150,63 +152,93 @@ def job_throughput(units_per_rank, ms_local, ws):
 
 
 # ---------------------------------------------------------------- CPU legs
-ORACLE_SAMPLE = r'''
-import sys, time, json, os
-sys.path.insert(0, {root!r})
-import numpy as np
-import workloads as W
-from oracle import dg, forest as FO
-w = W.jitter3d_forest(seed=0)
-S = dg.Solver(FO.build(w), 2, cfl=0.1)
-U = S.project(lambda x: W.isentropic_vortex(x, scale=10.0))
-leaves = list(range(0, len(S.leaves), max(1, len(S.leaves) // {nleaves})))[:{nleaves}]
-times = []
-for it in range({reps}):
-    t0 = time.perf_counter()
-    L = S.residual(U, leaves=leaves)
-    V = U + 1e-4 * L
-    times.append(time.perf_counter() - t0)
-dof = len(leaves) * S.nv * S.ops.M * S.n ** S.d
-print(json.dumps(dict(times=times, dof=dof, nleaves=len(leaves))))
-'''
+def _oracle_worker(rank, nworkers, nleaves, reps, barrier, queue):
+    """One process of the oracle timing: builds the FP64 oracle on the bench
+    workload, then (after every process has built it) times `reps` SSP-RK3
+    stages (guard fill + residual + mass solve + update) on its share of the
+    first `nleaves` leaves.  Runs in a spawned process."""
+    from oracle import dg, forest as FO
+    S = dg.Solver(FO.build(W.jitter3d_forest(seed=0)), 2, cfl=0.1)
+    U = S.project(vortex)
+    mine = list(range(rank, nleaves, nworkers))
+    spans = []
+    for _ in range(reps):
+        barrier.wait()
+        t0 = time.time()
+        if mine:
+            L = S.residual(U, leaves=mine)
+            V = U[mine] + 1e-4 * L[mine]  # noqa: F841  (the stage update of those leaves)
+        spans.append((t0, time.time()))
+    dof = len(mine) * S.nv * S.ops.M * S.n ** S.d
+    queue.put((rank, spans, dof))
 
 
-def run_oracle_sample(nleaves, reps):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ORACLE_SAMPLE.format(root=ROOT, nleaves=nleaves, reps=reps)
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
-    if out.returncode != 0:
-        raise RuntimeError(out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+def oracle_timing(nworkers, nleaves, reps):
+    """Time the oracle with `nworkers` spawned processes (one thread each,
+    leaves dealt round robin).  Returns per-repetition wall times (max end -
+    min start over the processes) and the DOF updated per repetition."""
+    import multiprocessing as mp
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    ctx = mp.get_context("spawn")
+    barrier, queue = ctx.Barrier(nworkers), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(r, nworkers, nleaves, reps, barrier, queue))
+             for r in range(nworkers)]
+    for pr in procs:
+        pr.start()
+    res = [queue.get(timeout=1800) for _ in procs]
+    for pr in procs:
+        pr.join()
+    walls = [max(r[1][i][1] for r in res) - min(r[1][i][0] for r in res) for i in range(reps)]
+    return walls, sum(r[2] for r in res)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 def cpu_baseline():
-    r = run_oracle_sample(71, 1)
-    t = sum(r["times"])
-    return {"value": r["dof"] * len(r["times"]) / t, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
-            "sample": (f"one SSP-RK3 stage (guard fill + residual + mass solve + update) of the full "
-                       f"{r['nleaves']}-leaf workload in FP64 on 1 host thread, {t:.1f} s")}
+    """The oracle as it stands on the host cores: one thread, and one process
+    per core parallel over leaves (the core count is stated)."""
+    cores = host_cores()
+    w1, dof = oracle_timing(1, 71, 1)
+    wa, dofa = oracle_timing(cores, 71, 2)
+    v1 = dof / w1[0]
+    va = dofa * len(wa) / sum(wa)
+    return {"value": va, "unit": "DOF-updates/s", "cores": cores, "nproc": os.cpu_count(), "kind": "oracle",
+            "value_1_thread": v1,
+            "sample": (f"one SSP-RK3 stage (guard fill + residual + mass solve + update) of the full 71-leaf "
+                       f"workload in FP64: {w1[0]:.1f} s on 1 thread; {len(wa)} stages on {cores} processes "
+                       f"(one thread each, leaves dealt round robin), {sum(wa):.1f} s")}
 
 
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    # each step: one SSP-RK3 stage on a leaf subset sized so the run stays short
-    per_leaf = 0.1
+    # each step: one SSP-RK3 stage on all host cores; the leaf sample is the
+    # whole workload unless that would take more than a few minutes
+    cores = host_cores()
+    per_leaf = 0.25 / cores
     budget = 150.0
-    nleaves = int(max(1, min(71, budget / max(1, args.steps + args.warmup) / per_leaf)))
-    r = run_oracle_sample(nleaves, args.steps + args.warmup)
-    times = r["times"][args.warmup:]
+    nleaves = int(max(cores, min(71, budget / max(1, args.steps + args.warmup) / per_leaf)))
+    nleaves = min(nleaves, 71)
+    walls, dof = oracle_timing(cores, nleaves, args.steps + args.warmup)
+    times = walls[args.warmup:]
     t = sum(times)
-    value = r["dof"] * len(times) / t
+    value = dof * len(times) / t
     line = {"impl": "reference", "metric": "DG DOF-updates/s per RK stage", "value": value,
             "unit": "DOF-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_leaves": r["nleaves"]},
-            "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
-                             "sample": f"one SSP-RK3 stage per step on {r['nleaves']} of the 71 leaves, FP64, 1 thread"},
+            "config": {"workload": WORKLOAD, "sample_leaves": nleaves},
+            "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": cores, "nproc": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": (f"one SSP-RK3 stage per step on {nleaves} of the 71 leaves, FP64, "
+                                        f"{cores} processes of one thread, leaves dealt round robin")},
             "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -284,9 +316,8 @@ def run_ours(args):
     achieved = alg_bytes / (stage_ms / stage_n / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"],
-            "traffic": STAGE_TRAFFIC_BYTES if _SEL[0] == "jitter3d" else None,
-            "traffic_source": ("profiles/k_stage_jitter3d_p2_fp32.md (ncu, cold L2, mean of 3 stages)"
-                               if _SEL[0] == "jitter3d" else None),
+            "traffic": STAGE_TRAFFIC_BYTES.get(_SEL[0]),
+            "traffic_how": TRAFFIC_HOW,
             "kernel": "k_stage<3,2,8,float>",
             "bytes_per_launch": alg_bytes, "avg_launch_us": 1e3 * stage_ms / stage_n,
             "peak_source": pk_kind,
@@ -367,17 +398,94 @@ def run_ours(args):
         "tuning": f32.tuning(),
         "status_word": status,
     }
+    if not args.quick_line:
+        # affine periodic cubes far above L2 (each state copy 0.34 / 1.13 GB)
+        line["over_l2"] = {k: over_l2_case(k, args, stream, flush, pk, pk_kind, torch, pkg) for k in OVER_L2}
+        line["serve"] = run_serve(args, sub=True)
+        line["amr"] = run_amr(args, sub=True)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
     return 0
 
 
+# affine periodic cubes of B^3 roots of 8^3 cells whose state is far above the
+# 129 MB L2: the roofline of the stage kernel where HBM is the bound
+OVER_L2 = {
+    "cube16p1": ("3d-euler-periodic-cube-16^3-roots-n8-p1", 16, 1),
+    "cube16p2": ("3d-euler-periodic-cube-16^3-roots-n8-p2", 16, 2),
+}
+
+
+def over_l2_case(key, args, stream, flush, pk, pk_kind, torch, pkg):
+    """FP32 DOF-update rate, stage-kernel roofline (state bytes of the
+    affine FP32 form: 8 B per DOF on the first stage, 12 B on the others,
+    plus the cell sizes on the last) and the FP32-vs-FP64 difference after a
+    few steps from the same nodal values, on one affine periodic cube."""
+    name, B, p = OVER_L2[key]
+    w = W.periodic_cube_forest(B)
+    f32 = pkg.Forest.from_workload(w, p=p, precision=pkg.FP32, cfl=0.1)
+    f32.set_stream(stream)
+    vals = vortex(f32.quad_points())
+    f32.set_state_nodal(vals)
+    dof = f32.n_leaves * f32.nv * f32.M * f32.nc
+    for _ in range(args.warmup):
+        f32.rk_step()
+    ms = timed_steps(f32, args.steps, stream, flush, torch)
+    value = dof * 3 * args.steps / (ms / 1e3)
+    f32.set_timing(True)
+    f32.kernel_times()
+    timed_steps(f32, args.steps, stream, flush, torch)
+    kt = f32.kernel_times()
+    f32.set_timing(False)
+    stage_ms, stage_n = kt["stage"]
+    cells = f32.n_leaves * f32.nc
+    alg = dof * 4 * (2 + 3 + 3) / 3.0 + cells * 4 / 3.0
+    achieved = alg / (stage_ms / stage_n / 1e3) / 1e9
+    # FP32 against FP64 after the same steps from the same nodal values
+    nacc = 5
+    f32.set_state_nodal(vals)
+    f32.set_time(0.0)
+    f64 = pkg.Forest.from_workload(w, p=p, precision=pkg.FP64, cfl=0.1)
+    f64.set_stream(stream)
+    f64.set_state_nodal(vals)
+    del vals
+    torch.cuda.synchronize()
+    t64 = time.perf_counter()
+    for _ in range(nacc):
+        f64.rk_step()
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t64
+    for _ in range(nacc):
+        f32.rk_step()
+    a = f32.get_state().astype(np.float64)
+    b = f64.get_state()
+    l2 = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    linf = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+    out = {"workload": name, "leaves": f32.n_leaves, "cells": cells, "p": p, "dof": dof,
+           "state_bytes_fp32": dof * 4, "value": value, "unit": "DOF-updates/s", "ms_per_step": ms / args.steps,
+           "steps": args.steps,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                        "frac": achieved / pk["hbm_gbs"], "traffic": STAGE_TRAFFIC_BYTES.get(key),
+                        "traffic_how": TRAFFIC_HOW, "kernel": f"k_stage<3,{p},8,float>",
+                        "bytes_per_launch": alg, "avg_launch_us": 1e3 * stage_ms / stage_n,
+                        "peak_source": pk_kind,
+                        "other_kernels_us_per_step": {"guard": 1e3 * kt["guard"][0] / args.steps,
+                                                      "dt": 1e3 * kt["dt"][0] / args.steps}},
+           "fp64_value": dof * 3 * nacc / t64,
+           "accuracy": {"steps": nacc, "l2_rel_fp32_vs_fp64": l2, "linf_rel_fp32_vs_fp64": linf},
+           "tuning": f32.tuning(), "status_word": f32.status_word()}
+    f32.close()
+    f64.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- serving
 SERVE_MIX = dict(rate=20.0, seed=0, blocks=(64, 512), degrees=(1, 2, 3), t_end=(0.05, 0.5), t_scale=0.1)
 
 
-def run_serve(args):
+def run_serve(args, sub=False):
     """Continuous batching: Poisson arrivals of independent solves (blast or
     vortex, periodic cubes of 64-512 blocks, p in 1..3, FP32), each admitted
     by its device footprint, built on a worker thread (forest, upload of its
@@ -388,11 +496,11 @@ def run_serve(args):
     from paper_2502_12620_gb300 import serve
 
     ws, rank, local = dist_env()
-    if ws > 1:
+    if ws > 1 and not sub:
         import torch.distributed as dist
         dist.init_process_group("gloo")
     torch.cuda.set_device(local)
-    mix = W.serving_mix(args.serve_requests, **SERVE_MIX)
+    mix = W.serving_mix(args.serve_sub_requests if sub else args.serve_requests, **SERVE_MIX)
     # request payloads, made before the run: each solve's initial values at its
     # quadrature points (the vortex payload is shared by requests of one shape)
     t_prep = time.perf_counter()
@@ -437,6 +545,13 @@ def run_serve(args):
         wall = time.perf_counter() - t0
     sm = serve.summarize(res, wall)
     updates = sum(r.dof * 3 * r.steps for r in res)
+    if sub:
+        return {"workload": "serving-mix-periodic-cubes-64-512-blocks-n8-p1-3-blast-or-vortex",
+                "requests": len(res), "value": updates / wall, "unit": "DOF-updates/s",
+                "p50_s": sm["p50_s"], "p99_s": sm["p99_s"], "wall_s": wall, "max_active": args.serve_active,
+                "failed": sum(1 for r in res if r.status != 0), "peak_active": srv.peak_active,
+                "mean_queue_s": float(np.mean([r.admitted - r.arrival for r in res])),
+                "payload_prep_s": t_prep, **{k: list(v) if isinstance(v, tuple) else v for k, v in SERVE_MIX.items()}}
     value, ms = job_throughput(updates, 1e3 * wall, ws)
     if rank != 0:
         return 0
@@ -464,7 +579,7 @@ def run_serve(args):
 AMR = dict(B=4, n_seg=8, p=1, refine_above=0.05, coarsen_below=0.01, max_level=4, every=10, limiter=1e-6)
 
 
-def run_amr(args):
+def run_amr(args, sub=False):
     """Blast on a periodic cube of 4^3 roots with dynamic refinement: the
     device indicator and adaptation (2:1 closure, state moved on the device)
     every `every` steps, the positivity limiter after every stage, FP32.
@@ -474,7 +589,7 @@ def run_amr(args):
     import paper_2502_12620_gb300 as pkg
 
     ws, rank, local = dist_env()
-    if ws > 1:
+    if ws > 1 and not sub:
         import torch.distributed as dist
         dist.init_process_group("gloo")
     torch.cuda.set_device(local)
@@ -500,7 +615,7 @@ def run_amr(args):
     for _ in range(args.warmup):
         f.rk_step()
     torch.cuda.synchronize()
-    steps = args.steps * cfg["every"]
+    steps = (args.amr_sub_periods if sub else args.steps) * cfg["every"]
     updates = 0
     leaves = []
     regrid_s = 0.0
@@ -521,6 +636,14 @@ def run_amr(args):
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     status = f.status_word()
+    amr = {"leaves_min": min(leaves), "leaves_max": max(leaves), "leaves_end": f.n_leaves,
+           "regrids": steps // cfg["every"], "regrids_that_changed_the_forest": changes,
+           "regrid_s": regrid_s, "regrid_ms_each": 1e3 * regrid_s / max(1, steps // cfg["every"]),
+           "wall_s": wall, "status_word": status, "t_end": f.time}
+    if sub:
+        f.close()
+        return {"workload": "3d-blast-periodic-cube-4^3-roots-n8-p1-adaptive-to-level-4", "value": updates / wall,
+                "unit": "DOF-updates/s", "steps": steps, **amr, **cfg}
     value, ms = job_throughput(updates, 1e3 * wall, ws)
     if rank != 0:
         return 0
@@ -530,11 +653,7 @@ def run_amr(args):
         "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "3d-blast-periodic-cube-4^3-roots-n8-p1-adaptive-to-level-4", **cfg},
-        "amr": {"leaves_min": min(leaves), "leaves_max": max(leaves), "leaves_end": f.n_leaves,
-                "regrids": steps // cfg["every"], "regrids_that_changed_the_forest": changes,
-                "regrid_s": regrid_s, "regrid_ms_each": 1e3 * regrid_s / max(1, steps // cfg["every"]),
-                "wall_s": wall,
-                "status_word": status, "t_end": f.time},
+        "amr": amr,
         "clocks": ck.summary(),
     }
     print(json.dumps(line))
@@ -554,6 +673,10 @@ def main():
     ap.add_argument("--amr", action="store_true", help="dynamic-refinement blast run (steps = regrid periods)")
     ap.add_argument("--nonconforming", default="paper", choices=["paper", "mortar"],
                     help="level jumps: the paper's guard-cell scheme (default) or the conservative mortar repair")
+    ap.add_argument("--quick-line", action="store_true",
+                    help="the step line without the over-L2, serving and AMR sub-objects")
+    ap.add_argument("--serve-sub-requests", type=int, default=16)
+    ap.add_argument("--amr-sub-periods", type=int, default=6)
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--serve-active", type=int, default=8)
     args = ap.parse_args()

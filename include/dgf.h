@@ -282,14 +282,18 @@ dgf_status dgf_kernel_times(dgf_forest* f, double* ms, int64_t* launches, int n_
  * u(q) = sum_m K_m phi_m(x_q) (forest element type).
  *   U_nodal  device, input state, read only;
  *   L_nodal  device, output, must not alias U_nodal.
- * Both must be 16-byte aligned (the kernels move 16-byte vectors);
- * DGF_EINVAL otherwise.
+ * Both must be 16-byte aligned (the kernels move 16-byte vectors) and be
+ * device (or managed) memory of the forest's device; DGF_EINVAL otherwise,
+ * before anything is launched.
  * The guard traces go to a 16 MiB array compiled into the library (a
  * file-scope __device__ array; every GPU that loads the library holds it
  * until the process exits).  Forests whose guard traces need more than
  * 16 MiB get DGF_EUNSUPPORTED.  The first call on a device looks up that
  * array's device address (cudaGetSymbolAddress), so make the first call on
- * each device outside any stream capture.  No cudaMalloc, cudaFree or
+ * each device outside any stream capture.  The address is kept per device
+ * for the life of the process; after a cudaDeviceReset the next call finds
+ * it stale and looks it up again (so that call, too, belongs outside a
+ * capture).  No cudaMalloc, cudaFree or
  * allocator callback is made.  All calls share the one array and every call
  * overwrites what it reads, so nothing needs clearing, but calls whose GPU
  * work overlaps (several streams, several host threads, several forests on

@@ -1933,6 +1933,15 @@ void* g_noalloc_ptr[kMaxDevices] = {};
 dgf_status noalloc_scratch(int device, void** out) {
   if (device < 0 || device >= kMaxDevices) return fail(DGF_EINVAL, "device ordinal out of range");
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (g_noalloc_ptr[device]) {
+    // a device reset since the last call invalidates the cached address:
+    // look it up again when the driver no longer knows it as device memory
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, g_noalloc_ptr[device]) != cudaSuccess || a.type != cudaMemoryTypeDevice) {
+      cudaGetLastError();
+      g_noalloc_ptr[device] = nullptr;
+    }
+  }
   if (!g_noalloc_ptr[device]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -1941,6 +1950,17 @@ dgf_status noalloc_scratch(int device, void** out) {
   }
   *out = g_noalloc_ptr[device];
   return DGF_OK;
+}
+
+// device memory of the forest's device (plain or managed)?  Host pointers
+// would reach the kernels and fault there, so they are refused up front.
+bool on_device(const void* p, int device) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == device;
 }
 
 }  // namespace
@@ -1953,6 +1973,8 @@ extern "C" dgf_status dgf_dg_residual_noalloc(dgf_forest* f, const void* U_nodal
     return fail(DGF_EINVAL, "state pointers must be 16-byte aligned");
   if (f->comp) return fail(DGF_EUNSUPPORTED, "dgf_dg_residual_noalloc: compensated forests are not supported");
   DeviceGuard dg(f->device);
+  if (!on_device(U_nodal, f->device) || !on_device(L_nodal, f->device))
+    return fail(DGF_EINVAL, "dgf_dg_residual_noalloc: state pointers must be device memory of the forest's device");
   const size_t need = (size_t)f->nL * 2 * f->d * f->nv * f->NFP * f->nt * f->esize;
   if (need > kNoAllocScratchBytes)
     return fail(DGF_EUNSUPPORTED, "dgf_dg_residual_noalloc: the guard traces of this forest need " +

@@ -27,6 +27,17 @@ def rel(a, b):
     return float(np.linalg.norm((np.asarray(a, float) - b).ravel()) / max(np.linalg.norm(np.ravel(b)), 1e-300))
 
 
+def assert_matches(L, Lo, prec, S, U):
+    """Relative L2 over the whole array and, element by element, the largest
+    deviation against the size of the terms summed into L (so one wrong face
+    point in one leaf cannot hide in the global norm)."""
+    tol = TOL["fp64" if prec == "fp64" else "fp32"]
+    e = rel(L, Lo)
+    assert e < tol, e
+    emax = float(np.max(np.abs(np.asarray(L, float) - Lo)))
+    assert emax < tol * term_scale(S, U), (emax, term_scale(S, U))
+
+
 def _pair(dgf, w, p, prec, cfl=0.1):
     f = dgf.Forest.from_workload(w, p=p, precision=prec, cfl=cfl)
     S = dg.Solver(FO.build(w), p, cfl=cfl)
@@ -76,9 +87,10 @@ def test_residual_matches_oracle(dgf, case, p, prec):
     f, S = _pair(dgf, w, p, dgf.FP64 if prec == "fp64" else dgf.FP32)
     U = W.random_modal_state(f.n_leaves, f.dim, f.n_seg, p, seed=p + 11)
     f.set_state(U)
+    Uin = U.astype(f.dtype).astype(np.float64)
     L = f.dg_residual()
-    Lo = S.residual(U.astype(f.dtype).astype(np.float64))
-    assert rel(L, Lo) < TOL[prec], rel(L, Lo)
+    Lo = S.residual(Uin)
+    assert_matches(L, Lo, prec, S, Uin)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -215,7 +227,7 @@ def test_compensated_residual_and_steps_match_oracle(dgf, case):
     U = W.random_modal_state(f.n_leaves, f.dim, f.n_seg, 2, seed=9)
     f.set_state(U)
     assert rel(f.get_state(), U) < 1e-15  # the state itself is FP64
-    assert rel(f.dg_residual(), S.residual(U)) < TOL["fp32"]
+    assert_matches(f.dg_residual(), S.residual(U), "fp32", S, U)
     for _ in range(3):
         U = S.ssp_rk3_step(U, S.dt(U))
         f.rk_step()
@@ -274,9 +286,10 @@ def test_mortar_residual_matches_oracle(dgf, case, p, prec):
     S = dg.Solver(FO.build(w), p, nonconforming="mortar")
     U = W.random_modal_state(f.n_leaves, f.dim, f.n_seg, p, seed=p + 21)
     f.set_state(U)
+    Uin = U.astype(f.dtype).astype(np.float64)
     L = f.dg_residual()
-    Lo = S.residual(U.astype(f.dtype).astype(np.float64))
-    assert rel(L, Lo) < TOL["fp32" if prec != "fp64" else "fp64"], rel(L, Lo)
+    Lo = S.residual(Uin)
+    assert_matches(L, Lo, prec, S, Uin)
 
 
 @pytest.mark.parametrize("case", ["pair_2d", "jitter_3d_n4"])
@@ -351,7 +364,7 @@ def test_prescribed_state_boundaries_match_oracle(dgf, dim, prec):
     f.set_state(U)
     if prec == "fp64":
         assert rel(f.fill_guardcells(), S.fill_guardcells(U)) < TOL["fp64"]
-    assert rel(f.dg_residual(), S.residual(U)) < TOL[prec]
+    assert_matches(f.dg_residual(), S.residual(U), prec, S, U)
     for _ in range(2):
         U = S.ssp_rk3_step(U, S.dt(U))
         f.rk_step()

@@ -3,11 +3,14 @@ fixes: an independent textbook 1D DG, free-stream preservation, conservation,
 the SSP-RK3 stability polynomial, design order on the isentropic vortex, and
 restriction(prolongation(u)) = u through a regrid."""
 import copy
+import itertools
+import math
 
 import numpy as np
 import pytest
 
 import workloads as W
+from oracle import basis as B
 from oracle import dg
 from oracle import euler as E
 from oracle import forest as FO
@@ -243,3 +246,172 @@ def test_prescribed_state_boundaries():
         on_xminus = T["kind"][li][0] == 3
         assert np.all(D[li][~cells_x0] == 0)
         assert np.any(D[li][cells_x0] > 0) == on_xminus
+
+
+# ------------------------------------------------------- time increment (reading R5)
+def _one_cell_3d(moved_corner_offset, n_seg=1, corner=7):
+    """One root on the unit cube (outflow faces) whose corner `corner` (bit a
+    of the index = side along axis a) is moved by the given offset; its
+    n_seg^3 cells are trilinear in the root's corners."""
+    nodes = np.array([[(k >> a) & 1 for a in range(3)] for k in range(8)], float)
+    nodes[corner] += np.asarray(moved_corner_offset, float)
+    return dict(dim=3, n_seg=n_seg, nodes=nodes, root_corners=np.arange(8, dtype=np.int64)[None],
+                root_cell_nodes=None, periodic=[], refine=[])
+
+
+def _lam(prim):
+    """sum_i (|u_i| + c) of one primitive state (rho, u, v, w, p)."""
+    rho, u, pr = prim[0], np.asarray(prim[1:4]), prim[4]
+    return float(np.sum(np.abs(u)) + 3.0 * math.sqrt(1.4 * pr / rho))
+
+
+@pytest.mark.parametrize("p", [0, 1, 2])
+def test_dt_closed_form_uniform_state_affine_cube(p):
+    """Affine periodic cube of 2^3 roots with 2^3 cells each (edge h = 1/4):
+    dt = CFL h / sum_i(|u_i| + c) for a uniform state."""
+    prim = (1.3, 0.4, -0.7, 0.2, 0.8)
+    S = dg.Solver(FO.build(W.periodic_cube_forest(2, n_seg=2)), p, cfl=0.3)
+    U = S.project(lambda x: W.free_stream(x, state=prim))
+    assert abs(S.dt(U) - 0.3 * 0.25 / _lam(prim)) < 1e-14
+
+
+@pytest.mark.parametrize("delta", [(0.1, -0.05, 0.08), (-0.2, -0.1, -0.15)])
+def test_dt_closed_form_jittered_single_cell(delta):
+    """One trilinear cell, the unit cube with corner (1,1,1) moved by delta:
+    J = 1 + delta . grad(s0 s1 s2), so the volume is 1 + (d0 + d1 + d2)/4
+    and h = volume^(1/3)."""
+    prim = (0.9, -0.3, 0.5, 0.1, 1.2)
+    S = dg.Solver(FO.build(_one_cell_3d(delta)), 1, cfl=0.25)
+    U = S.project(lambda x: W.free_stream(x, state=prim))
+    h = (1.0 + sum(delta) / 4.0) ** (1.0 / 3.0)
+    assert abs(S.dt(U) - 0.25 * h / _lam(prim)) < 1e-14
+
+
+def test_dt_is_the_minimum_over_cells():
+    """Root of 2^3 cells of edge 1/2 whose centre node is moved by delta:
+    the cell with that node as its corner k has volume
+    h^3 (1 + sum_a s_a delta_a / (4 h)), s_a = +1 if the node is on the
+    cell's upper side along axis a; the smallest volume sets dt."""
+    delta = np.array([0.06, -0.04, 0.05])
+    w = _one_cell_3d((0, 0, 0), n_seg=2)
+    cn = np.array([[i, j, k] for k in range(3) for j in range(3) for i in range(3)], float) / 2.0
+    cn[13] += delta  # the centre node (1, 1, 1) of the 3^3 cell-node lattice
+    w["root_cell_nodes"] = cn[None]
+    prim = (1.0, 0.2, 0.3, -0.4, 1.0)
+    S = dg.Solver(FO.build(w), 1, cfl=0.2)
+    U = S.project(lambda x: W.free_stream(x, state=prim))
+    vols = []
+    for bits in itertools.product((0, 1), repeat=3):  # cell at the lower (0) or upper (1) half
+        s = np.array([1.0 if b == 0 else -1.0 for b in bits])  # the centre is the cell's upper corner when b = 0
+        vols.append(0.125 * (1.0 + float(s @ delta) / (4 * 0.5)))
+    assert abs(S.dt(U) - 0.2 * min(vols) ** (1 / 3) / _lam(prim)) < 1e-14
+
+
+def test_dt_is_the_minimum_over_gauss_points():
+    """Unit cube cell, p = 1, rho u = a + b P_1(xi_x) with the other
+    conserved variables constant: velocity and sound speed differ at the two
+    Gauss points xi_x = -+1/sqrt(3); dt takes the larger sum_i(|u_i| + c)."""
+    S = dg.Solver(FO.build(_one_cell_3d((0, 0, 0))), 1, cfl=0.4)
+    U = np.zeros(S.shape())
+    rho, a, b, E = 1.1, 0.3, 0.5, 2.5
+    U[0, 0, 0, 0] = rho
+    U[0, 1, 0, 0] = a
+    U[0, 1, 1, 0] = b  # mode k = (1, 0, 0)
+    U[0, 4, 0, 0] = E
+    lam = []
+    for xi in (-1 / math.sqrt(3), 1 / math.sqrt(3)):
+        u = (a + b * xi) / rho
+        pr = 0.4 * (E - 0.5 * rho * u * u)
+        lam.append(abs(u) + 3.0 * math.sqrt(1.4 * pr / rho))
+    assert abs(S.dt(U) - 0.4 * 1.0 / max(lam)) < 1e-14
+
+
+def test_run_clips_the_last_increment_to_t_end():
+    """The last increment is shortened so the march ends at t_end exactly."""
+    S = dg.Solver(FO.build(W.periodic_cube_forest(1, n_seg=2)), 1, cfl=0.3)
+    U = S.project(lambda x: W.free_stream(x, state=(1.0, 0.5, 0.0, 0.0, 1.0)))
+    dt = S.dt(U)
+    t_end = 2.5 * dt
+    _, t = S.run(U, 100, t_end=t_end)
+    assert t == pytest.approx(t_end, rel=0, abs=1e-15)
+    _, t2 = S.run(U, 2, t_end=t_end)
+    assert t2 == pytest.approx(2 * dt, rel=1e-15)
+
+
+# ------------------------------------------------------- design order, p = 1..3
+def _entropy_wave(x, t=0.0, d=2):
+    """rho = 1 + 0.2 sin(2 pi (sum_a x_a - d t)), unit velocity along every
+    axis, unit pressure: an exact Euler solution (the density is carried by
+    the flow), periodic on the unit square/cube."""
+    x = np.asarray(x, float)
+    s = 2 * math.pi * (np.sum(x, axis=-1) - x.shape[-1] * t)
+    vel = np.ones(x.shape[:-1] + (x.shape[-1],))
+    return W.prim_to_cons(1.0 + 0.2 * np.sin(s), vel, np.ones(x.shape[:-1]))
+
+
+def _l2_error_overintegrated(S, U, fun, extra=3):
+    """Relative L2 error against fun with a Gauss rule of p + 1 + extra points
+    per axis (the error between the Gauss points counts too)."""
+    xq, wq = B.tensor_points(S.d, S.ops.N + extra)
+    Phi = B.eval_basis(xq, S.ops.N)
+    num = den = 0.0
+    for li, C in enumerate(S.corners):
+        ex = fun(dg.map_points(C, xq))
+        uq = np.einsum("qm,vmc->cqv", Phi, U[li])
+        _, J, _ = dg.jacobian(C, xq)
+        num += float(np.einsum("q,cq,cqv->", wq, J, (uq - ex) ** 2))
+        den += float(np.einsum("q,cq,cqv->", wq, J, ex ** 2))
+    return math.sqrt(num / den)
+
+
+def _wave_error(w, p, t_end, dt):
+    S = dg.Solver(FO.build(w), p, cfl=1.0)
+    U = S.project(_entropy_wave)
+    t = 0.0
+    while t < t_end - 1e-14:
+        h = min(dt, t_end - t)
+        U = S.ssp_rk3_step(U, h)
+        t += h
+    return _l2_error_overintegrated(S, U, lambda x: _entropy_wave(x, t))
+
+
+# (p, n_seg pair, t_end, dt): even p needs finer cells before the observed
+# order settles at p + 1 (2.53 at n = 4 -> 8, 2.91 at 8 -> 16 in 2D)
+WAVE_2D = {1: ((2, 4), 0.05, 2e-3), 2: ((8, 16), 0.03, 5e-4), 3: ((2, 4), 0.05, 1e-3)}
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_entropy_wave_design_order_2d_two_levels(p):
+    """Design order p + 1 (Sec. 5.1, the conclusion's optimal-order claim) on
+    a 2-level forest: 2x2 roots of the periodic unit square with one root
+    refined, cells halved by doubling n_seg; a fixed small time step keeps
+    the SSP-RK3 error below the spatial one."""
+    ns, t_end, dt = WAVE_2D[p]
+    errs = []
+    for n in ns:
+        w = W.lattice_forest(2, 2, 1.0, n)
+        w["refine"] = [[(0, 1, (0, 0))]]
+        errs.append(_wave_error(w, p, t_end, dt))
+    order = math.log2(errs[0] / errs[1])
+    assert order > p + 0.8, (errs, order)
+
+
+def test_entropy_wave_design_order_3d_two_levels_p1():
+    """Design order p + 1 in 3D on a 2-level forest: 2^3 periodic roots, one
+    refined, n_seg 2 -> 4."""
+    errs = []
+    for n in (2, 4):
+        w = W.periodic_cube_forest(2, n_seg=n)
+        w["refine"] = [[(0, 1, (0, 0, 0))]]
+        errs.append(_wave_error(w, 1, 0.02, 2e-3))
+    order = math.log2(errs[0] / errs[1])
+    assert order > 1.8, (errs, order)
+
+
+def test_entropy_wave_design_order_3d_p3():
+    """Design order p + 1 in 3D at p = 3: one periodic root, n_seg 2 -> 4."""
+    errs = []
+    for n in (2, 4):
+        errs.append(_wave_error(W.periodic_cube_forest(1, n_seg=n), 3, 0.03, 1e-3))
+    order = math.log2(errs[0] / errs[1])
+    assert order > 3.8, (errs, order)

@@ -68,6 +68,6 @@ def test_reference_arm_prints_on_rank_zero_only(monkeypatch):
     monkeypatch.setenv("RANK", "1")
     monkeypatch.setenv("WORLD_SIZE", "2")
     called = []
-    monkeypatch.setattr(bench, "run_oracle_sample", lambda *a: called.append(a))
+    monkeypatch.setattr(bench, "oracle_timing", lambda *a: called.append(a))
     assert bench.run_reference(Args()) == 0
     assert called == []
