@@ -63,6 +63,8 @@ WORKLOADS = {
     "cube8": ("3d-euler-periodic-cube-8^3-roots-n8-p2", lambda: W.periodic_cube_forest(8), 2),
     "cube8p1": ("3d-euler-periodic-cube-8^3-roots-n8-p1", lambda: W.periodic_cube_forest(8), 1),
     "cube8p3": ("3d-euler-periodic-cube-8^3-roots-n8-p3", lambda: W.periodic_cube_forest(8), 3),
+    "cube16p1": ("3d-euler-periodic-cube-16^3-roots-n8-p1", lambda: W.periodic_cube_forest(16), 1),
+    "cube16p2": ("3d-euler-periodic-cube-16^3-roots-n8-p2", lambda: W.periodic_cube_forest(16), 2),
     "jitter3dp1": ("3d-euler-jittered-cube-8roots-71leaves-n8-p1", lambda: W.jitter3d_forest(seed=0), 1),
     "jitter3dp3": ("3d-euler-jittered-cube-8roots-71leaves-n8-p3", lambda: W.jitter3d_forest(seed=0), 3),
 }

@@ -152,6 +152,7 @@ struct dgf_forest {
   size_t esize = 8;   // element size of the device compute buffers
   size_t sesize = 8;  // element size of the state at the C ABI
   bool comp = false;  // compensated form: u^n in FP64, stage increments in FP32
+  bool all_affine = false;  // every leaf an affine block (the stage kernel needs no per-cell geometry)
   int cur = 0;        // compensated form: which U64 buffer holds u^n
   int d = 0, n = 0, p = 0, N = 0, nv = 0, M = 0, nc = 0, NG = 0, nt = 0, NFP = 0;
   int64_t nL = 0;
@@ -748,6 +749,7 @@ dgf_status build_device(dgf_forest* f) {
       (st = upload(f, f->fine, fine_list)) || (st = upload(f, f->trd, trd)))
     return st;
   if ((st = upload(f, f->affine, affine)) || (st = upload(f, f->hcell64, hcell))) return st;
+  f->all_affine = std::all_of(affine.begin(), affine.end(), [](unsigned char a) { return a != 0; });
   if (f->mortar && ((st = upload(f, f->fluxmask, fluxmask)) || (st = upload(f, f->mfine, mfine)) ||
                     (st = upload(f, f->mcoarse, mcoarse)) || (st = upload(f, f->msrc, msrc))))
     return st;
@@ -786,8 +788,11 @@ dgf_status build_device(dgf_forest* f) {
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device);
     int occ = 0;
-    if (d == 2) occ = f->precision == DGF_FP64 ? stage_occupancy<2, double>(f->p, n) : stage_occupancy<2, float>(f->p, n);
-    else occ = f->precision == DGF_FP64 ? stage_occupancy<3, double>(f->p, n) : stage_occupancy<3, float>(f->p, n);
+    const int cp = f->comp ? 1 : 0;
+    if (d == 2)
+      occ = f->precision == DGF_FP64 ? stage_occupancy<2, double>(f->p, n, cp) : stage_occupancy<2, float>(f->p, n, cp);
+    else
+      occ = f->precision == DGF_FP64 ? stage_occupancy<3, double>(f->p, n, cp) : stage_occupancy<3, float>(f->p, n, cp);
     f->slots = occ * sms;
     f->zchunk = 1;
     if (d == 3 && f->slots > 0) {
@@ -826,6 +831,7 @@ RtStage stage_args(dgf_forest* f, int src, int dst, double ca, double cb, int mo
   r.zchunk = f->zchunk;
   r.slots = f->slots;
   r.affine = (const unsigned char*)f->affine.ptr;
+  r.all_affine = f->all_affine ? 1 : 0;
   r.ameta = f->ameta.ptr;
   r.kind = (const int*)f->kind.ptr;
   r.nbr = (const int*)f->nbr.ptr;

@@ -22,6 +22,7 @@ struct RtStage {
   const void* gtr;
   const void* hcell;
   const unsigned char* affine;
+  int all_affine;  // every leaf affine
   const void* ameta;
   const int* kind;
   const int* nbr;
@@ -132,6 +133,6 @@ template <int D, typename Real>
 size_t stage_smem_bytes(int p, int n);
 // resident stage CTAs per SM (0: does not fit)
 template <int D, typename Real>
-int stage_occupancy(int p, int n);
+int stage_occupancy(int p, int n, int comp);
 
 }  // namespace dgf
