@@ -49,6 +49,13 @@ STAGE_TRAFFIC_BYTES = {}
 TRAFFIC_HOW = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, cold L2, mean of the 3 stages of a step"
 
 
+def stage_kernel_name(f, p):
+    """The stage kernel the forest's time step launches (after tuning)."""
+    if f.tuning()["stage_kernel"] == "pair":
+        return f"k_stage_pair<{p}>"
+    return f"k_stage<3,{p},8,float>"
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
@@ -320,7 +327,7 @@ def run_ours(args):
             "frac": achieved / pk["hbm_gbs"],
             "traffic": STAGE_TRAFFIC_BYTES.get(_SEL[0]),
             "traffic_how": TRAFFIC_HOW,
-            "kernel": "k_stage<3,2,8,float>",
+            "kernel": stage_kernel_name(f32, p),
             "bytes_per_launch": alg_bytes, "avg_launch_us": 1e3 * stage_ms / stage_n,
             "peak_source": pk_kind,
             "other_kernels_us_per_step": {"guard": 1e3 * kt["guard"][0] / args.steps,
@@ -469,7 +476,7 @@ def over_l2_case(key, args, stream, flush, pk, pk_kind, torch, pkg):
            "steps": args.steps,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                         "frac": achieved / pk["hbm_gbs"], "traffic": STAGE_TRAFFIC_BYTES.get(key),
-                        "traffic_how": TRAFFIC_HOW, "kernel": f"k_stage<3,{p},8,float>",
+                        "traffic_how": TRAFFIC_HOW, "kernel": stage_kernel_name(f32, p),
                         "bytes_per_launch": alg, "avg_launch_us": 1e3 * stage_ms / stage_n,
                         "peak_source": pk_kind,
                         "other_kernels_us_per_step": {"guard": 1e3 * kt["guard"][0] / args.steps,

@@ -264,6 +264,18 @@ dgf_status dgf_status_word(dgf_forest* f, int32_t* status, int reset);
  * quantity: the paper's per-block loop (Sec. 4.3) has no tiling. */
 dgf_status dgf_tuning(const dgf_forest* f, int32_t* zchunk, int32_t* resident_ctas);
 
+/* Which stage kernel the forest's time step launches (host value, no sync):
+ * 0 = the cell-pair FP32 kernel (3D forests of 8^3-cell blocks at p = 1, 2
+ * in plain FP32: f32x2 arithmetic on cell pairs, TMA-staged layers), 1 =
+ * the general layer-sweep kernel.  The first dgf_rk_step of a 3D forest
+ * times both where both apply and keeps the faster (the z-chunk length is
+ * tuned with it); DGF_STAGE_KERNEL=pair|classic in the environment pins the
+ * choice.  The two kernels round differently, so results agree within the
+ * FP32 tolerance, not bit for bit; a given kernel is bitwise reproducible
+ * and independent of the z-chunk length.  The paper has no counterpart (a
+ * tuning report). */
+dgf_status dgf_stage_kernel(const dgf_forest* f, int32_t* kernel);
+
 /* Kernel timing: when on, rk_step launches stage by stage (no graph) with
  * CUDA events around every kernel; dgf_kernel_times synchronises and returns
  * summed milliseconds and kernel launch counts for the classes 0 = dt,

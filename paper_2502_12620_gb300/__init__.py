@@ -85,6 +85,7 @@ _SIGS = {
     "dgf_status_word": [_P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int],
     "dgf_set_timing": [_P, ctypes.c_int],
     "dgf_tuning": [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
+    "dgf_stage_kernel": [_P, ctypes.POINTER(ctypes.c_int32)],
     "dgf_kernel_times": [_P, _P, _P, ctypes.c_int],
     "dgf_dg_residual_noalloc": [_P, _P, _P],
 }
@@ -397,7 +398,9 @@ class Forest:
         z = ctypes.c_int32()
         c = ctypes.c_int32()
         _check(lib().dgf_tuning(self.h, ctypes.byref(z), ctypes.byref(c)))
-        return {"zchunk": z.value, "resident_ctas": c.value}
+        k = ctypes.c_int32()
+        _check(lib().dgf_stage_kernel(self.h, ctypes.byref(k)))
+        return {"zchunk": z.value, "resident_ctas": c.value, "stage_kernel": ("pair", "classic")[k.value]}
 
     def set_timing(self, on):
         _check(lib().dgf_set_timing(self.h, int(on)))

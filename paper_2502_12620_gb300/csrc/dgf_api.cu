@@ -183,7 +183,9 @@ struct dgf_forest {
   std::vector<int32_t> bctag;
   std::vector<double> bstate_h;
   Buf bstate;
-  int slots = 0;
+  int slots = 0;            // resident CTAs of the chosen stage kernel
+  int slots_k[2] = {0, 0};  // resident CTAs: [0] the cell-pair kernel where it applies, [1] k_stage
+  int kernel = 0;           // stage kernel: 0 the cell-pair kernel where it applies, 1 k_stage
   bool have_state = false;
   bool graph_valid = false;
   cudaGraphExec_t graph = nullptr;
@@ -312,6 +314,12 @@ bool chol_solve(int M, std::vector<double>& A, std::vector<double>& B, int nrhs)
     }
   }
   return true;
+}
+
+// the cell-pair FP32 stage kernel covers 3D forests of 8^3-cell blocks at
+// p = 1, 2 in plain FP32
+bool pair_applies(const dgf_forest* f) {
+  return f->d == 3 && f->n == 8 && (f->p == 1 || f->p == 2) && f->precision == DGF_FP32 && !f->comp;
 }
 
 // Build every leaf-dependent device array: integer tables, FP64 geometry,
@@ -787,13 +795,23 @@ dgf_status build_device(dgf_forest* f) {
   {
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device);
-    int occ = 0;
     const int cp = f->comp ? 1 : 0;
-    if (d == 2)
-      occ = f->precision == DGF_FP64 ? stage_occupancy<2, double>(f->p, n, cp) : stage_occupancy<2, float>(f->p, n, cp);
-    else
-      occ = f->precision == DGF_FP64 ? stage_occupancy<3, double>(f->p, n, cp) : stage_occupancy<3, float>(f->p, n, cp);
-    f->slots = occ * sms;
+    for (int kk = 0; kk < 2; ++kk) {
+      int occ = 0;
+      if (d == 2)
+        occ = f->precision == DGF_FP64 ? stage_occupancy<2, double>(f->p, n, cp, kk)
+                                       : stage_occupancy<2, float>(f->p, n, cp, kk);
+      else
+        occ = f->precision == DGF_FP64 ? stage_occupancy<3, double>(f->p, n, cp, kk)
+                                       : stage_occupancy<3, float>(f->p, n, cp, kk);
+      f->slots_k[kk] = occ * sms;
+    }
+    // the cell-pair kernel unless it does not apply (its slots equal k_stage's
+    // then) or DGF_STAGE_KERNEL=classic; the autotuner may still pick k_stage
+    f->kernel = pair_applies(f) ? 0 : 1;
+    if (const char* ks = getenv("DGF_STAGE_KERNEL"))
+      if (strcmp(ks, "classic") == 0) f->kernel = 1;
+    f->slots = f->slots_k[f->kernel];
     f->zchunk = 1;
     if (d == 3 && f->slots > 0) {
       double best = 1e300;
@@ -810,7 +828,7 @@ dgf_status build_device(dgf_forest* f) {
       if (const char* zc = getenv("DGF_ZCHUNK")) f->zchunk = std::max(1, std::min(n, atoi(zc)));
     }
   }
-  f->tuned = d != 3 || getenv("DGF_ZCHUNK") != nullptr;
+  f->tuned = d != 3 || (getenv("DGF_ZCHUNK") != nullptr && getenv("DGF_STAGE_KERNEL") != nullptr);
   if (f->graph) {
     cudaGraphExecDestroy(f->graph);
     f->graph = nullptr;
@@ -830,6 +848,7 @@ RtStage stage_args(dgf_forest* f, int src, int dst, double ca, double cb, int mo
   r.n = f->n;
   r.zchunk = f->zchunk;
   r.slots = f->slots;
+  r.kernel = f->kernel;
   r.affine = (const unsigned char*)f->affine.ptr;
   r.all_affine = f->all_affine ? 1 : 0;
   r.ameta = f->ameta.ptr;
@@ -1005,60 +1024,84 @@ dgf_status init_lambda(dgf_forest* f) {
   return cuda_check(do_cfl(f, misc_args(f, 0)), "cfl");
 }
 
-// Autotuner for the stage kernel's tile: time one residual evaluation (mode 1,
+// Autotuner for the stage kernel: time one residual evaluation (mode 1,
 // written to a scratch stage buffer, the state is untouched) for every
-// z-chunk length n, n/2, ..., 1 and keep the fastest (median of 3 launches).
-// chunk lengths chosen so far, by (device, dim, p, n, precision, leaves): a
-// forest of a shape already timed in this process takes the earlier choice
+// stage kernel that applies to the forest (the cell-pair kernel and
+// k_stage, each with its own persistent grid) and every z-chunk length n,
+// n/2, ..., 1, and keep the fastest pair (median of 3 launches).  Choices
+// so far, by (device, dim, p, n, precision, leaves, all affine): a forest of
+// a shape already timed in this process takes the earlier choice.
+// DGF_ZCHUNK fixes the chunk length, DGF_STAGE_KERNEL=classic|pair the kernel.
 std::mutex g_tune_mutex;
-std::map<std::vector<long long>, int> g_tune_cache;
+std::map<std::vector<long long>, std::pair<int, int>> g_tune_cache;
 
 dgf_status autotune(dgf_forest* f) {
   f->tuned = true;
   if (f->d != 3 || f->slots <= 0) return DGF_OK;
-  const std::vector<long long> key = {f->device, f->d, f->p, f->n, f->precision, (long long)f->nL};
+  const std::vector<long long> key = {f->device, f->d, f->p, f->n, f->precision, (long long)f->nL, f->all_affine};
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      f->zchunk = it->second;
+      if (!getenv("DGF_ZCHUNK")) f->zchunk = it->second.first;
+      if (!getenv("DGF_STAGE_KERNEL")) f->kernel = it->second.second;
+      f->slots = f->slots_k[f->kernel];
       return DGF_OK;
     }
   }
   dgf_status st = cuda_check(split_state(f), "split");
   if (!st) st = cuda_check(do_guard(f, guard_args(f, 0, f->gtr.ptr, 1)), "guard");
   if (st) return st;
+  std::vector<int> kernels;
+  const char* ks = getenv("DGF_STAGE_KERNEL");
+  // the cell-pair kernel is a candidate only where it applies (distinct slots)
+  if (!(ks && strcmp(ks, "classic") == 0) && pair_applies(f) && f->slots_k[0] > 0) kernels.push_back(0);
+  if (!(ks && strcmp(ks, "pair") == 0) || kernels.empty()) kernels.push_back(1);
+  std::vector<int> zs;
+  if (getenv("DGF_ZCHUNK")) zs.push_back(f->zchunk);
+  else
+    for (int z = f->n; z >= 1; z /= 2) zs.push_back(z);
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  int best_z = f->zchunk;
+  int best_z = f->zchunk, best_k = f->kernel;
   float best = 1e30f;
-  for (int z = f->n; z >= 1; z /= 2) {
-    f->zchunk = z;
-    float t[3];
-    for (int r = 0; r < 4; ++r) {
-      cudaEventRecord(a, f->stream);
-      cudaError_t e = do_stage(f, stage_args(f, 0, 1, 0.0, 1.0, 1, 0));
-      cudaEventRecord(b, f->stream);
-      if (e != cudaSuccess) {
-        cudaEventDestroy(a);
-        cudaEventDestroy(b);
-        return cuda_check(e, "autotune");
+  for (int kk : kernels) {
+    f->kernel = kk;
+    f->slots = f->slots_k[kk];
+    for (int z : zs) {
+      f->zchunk = z;
+      float t[3];
+      for (int r = 0; r < 4; ++r) {
+        cudaEventRecord(a, f->stream);
+        cudaError_t e = do_stage(f, stage_args(f, 0, 1, 0.0, 1.0, 1, 0));
+        cudaEventRecord(b, f->stream);
+        if (e != cudaSuccess) {
+          cudaEventDestroy(a);
+          cudaEventDestroy(b);
+          return cuda_check(e, "autotune");
+        }
+        cudaEventSynchronize(b);
+        if (r > 0) cudaEventElapsedTime(&t[r - 1], a, b);  // first launch warms up
       }
-      cudaEventSynchronize(b);
-      if (r > 0) cudaEventElapsedTime(&t[r - 1], a, b);  // first launch warms up
-    }
-    std::sort(t, t + 3);
-    if (t[1] < best) {
-      best = t[1];
-      best_z = z;
+      std::sort(t, t + 3);
+      // k_stage must beat the cell-pair kernel by 2 % to be chosen, so that
+      // timing noise does not flip the choice (the kernels round differently)
+      const float tt = kk == 1 && !kernels.empty() && kernels[0] == 0 ? t[1] * 1.02f : t[1];
+      if (tt < best) {
+        best = tt;
+        best_z = z;
+        best_k = kk;
+      }
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   f->zchunk = best_z;
+  f->kernel = best_k;
+  f->slots = f->slots_k[best_k];
   std::lock_guard<std::mutex> lock(g_tune_mutex);
-  g_tune_cache[key] = best_z;
+  g_tune_cache[key] = {best_z, best_k};
   return DGF_OK;
 }
 
@@ -1637,6 +1680,12 @@ dgf_status dgf_tuning(const dgf_forest* f, int32_t* zchunk, int32_t* resident_ct
   return DGF_OK;
 }
 
+dgf_status dgf_stage_kernel(const dgf_forest* f, int32_t* kernel) {
+  if (!f || !kernel) return fail(DGF_EINVAL, "null argument");
+  *kernel = f->kernel;
+  return DGF_OK;
+}
+
 dgf_status dgf_set_limiter(dgf_forest* f, double eps) {
   if (dgf_status st = require_device(f)) return st;
   if (f->comp && eps > 0.0) return fail(DGF_EUNSUPPORTED, "the limiter is not available for DGF_FP32_COMP");
@@ -1750,11 +1799,17 @@ static dgf_status regrid(dgf_forest* f, const std::vector<uint64_t>& old_leaves)
   old = live;
   live = dgf_forest::Buf();
   const bool was_tuned = f->tuned;
-  const int tuned_z = f->zchunk;
+  const int tuned_z = f->zchunk, tuned_k = f->kernel;
   dgf_status st = build_device(f);
-  if (was_tuned && f->d == 3 && !getenv("DGF_ZCHUNK")) {
-    f->tuned = true;  // a regrid keeps the chunk length (re-timing every regrid costs more)
-    f->zchunk = tuned_z;
+  if (was_tuned && f->d == 3) {
+    // a regrid keeps the tuned stage kernel and chunk length (re-timing every
+    // regrid costs more than it gains)
+    f->tuned = true;
+    if (!getenv("DGF_ZCHUNK")) f->zchunk = tuned_z;
+    if (!getenv("DGF_STAGE_KERNEL")) {
+      f->kernel = tuned_k;
+      f->slots = f->slots_k[tuned_k];
+    }
   }
   if (st) {
     dev_free(f, old);

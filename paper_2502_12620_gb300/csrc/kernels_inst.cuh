@@ -78,15 +78,7 @@ bool stage_mortar_prepare(size_t smem);
   DGF_INSTANTIATE_MORTAR_P(DIM, 3, REAL)
 
 // The cell-pair FP32 stage kernel (stage_pair.cuh) serves 3D forests of 8^3-cell
-// blocks at p = 1, 2 in plain FP32; DGF_STAGE_KERNEL=classic selects k_stage
-// for them too (for comparisons).
-inline bool pair_enabled() {
-  static const bool on = [] {
-    const char* e = std::getenv("DGF_STAGE_KERNEL");
-    return !(e && std::strcmp(e, "classic") == 0);
-  }();
-  return on;
-}
+// blocks at p = 1, 2 in plain FP32 (RtStage::kernel 0); k_stage serves the rest.
 template <int D, int P, int NS, typename Real>
 constexpr bool pair_shape() {
   return D == 3 && NS == 8 && (P == 1 || P == 2) && std::is_same<Real, float>::value;
@@ -102,9 +94,9 @@ template <int D, int P, int NS, typename Real>
 static int stage_blocks_per_sm_classic();
 
 template <int D, int P, int NS, typename Real>
-static int stage_blocks_per_sm_ns(int comp) {
+static int stage_blocks_per_sm_ns(int comp, int kernel) {
   if constexpr (pair_shape<D, P, NS, Real>()) {
-    if (!comp && pair_enabled()) {
+    if (!comp && kernel == 0) {
       const int nb = stage_pair_blocks_per_sm<P>();
       if (nb > 0) return nb;
     }
@@ -136,22 +128,23 @@ static int stage_blocks_per_sm_classic() {
 }
 
 template <int D, int P, typename Real>
-static int stage_blocks_per_sm(int n, int comp) {
+static int stage_blocks_per_sm(int n, int comp, int kernel) {
   switch (n) {
-    case 2: return stage_blocks_per_sm_ns<D, P, 2, Real>(comp);
-    case 4: return stage_blocks_per_sm_ns<D, P, 4, Real>(comp);
-    case 8: return stage_blocks_per_sm_ns<D, P, 8, Real>(comp);
+    case 2: return stage_blocks_per_sm_ns<D, P, 2, Real>(comp, kernel);
+    case 4: return stage_blocks_per_sm_ns<D, P, 4, Real>(comp, kernel);
+    case 8: return stage_blocks_per_sm_ns<D, P, 8, Real>(comp, kernel);
   }
   return 0;  // n_seg other than 2, 4, 8 is not instantiated
 }
 
 template <int D, int P, int NS, typename Real>
-static cudaError_t stage_ns(const StageArgs<D, P, Real>& a, int slots, int comp, int all_affine, cudaStream_t s) {
+static cudaError_t stage_ns(const StageArgs<D, P, Real>& a, int slots, int comp, int all_affine, int kernel,
+                            cudaStream_t s) {
   const size_t smem = stage_smem<D, P, Real>(NS, stage_rows<D, P, Real>(NS));
   const int items = a.nL * a.nchunks * (NS / stage_rows<D, P, Real>(NS));
   const int grid = items < slots ? items : slots;
   if constexpr (pair_shape<D, P, NS, Real>()) {
-    if (!comp && pair_enabled()) {
+    if (!comp && kernel == 0) {
       const int g = a.nL * a.nchunks < slots ? a.nL * a.nchunks : slots;
       if constexpr (P == 1 || P == 2) return stage_pair_launch<P>(a, g, a.fluxmask != nullptr, all_affine != 0, s);
     }
@@ -204,9 +197,9 @@ static cudaError_t stage_p(const RtStage& r, cudaStream_t s) {
   a.T = make_tab<P + 1, Real>(r.T);
   if (r.slots <= 0) return cudaErrorInvalidConfiguration;
   switch (r.n) {
-    case 2: return stage_ns<D, P, 2, Real>(a, r.slots, r.comp, r.all_affine, s);
-    case 4: return stage_ns<D, P, 4, Real>(a, r.slots, r.comp, r.all_affine, s);
-    case 8: return stage_ns<D, P, 8, Real>(a, r.slots, r.comp, r.all_affine, s);
+    case 2: return stage_ns<D, P, 2, Real>(a, r.slots, r.comp, r.all_affine, r.kernel, s);
+    case 4: return stage_ns<D, P, 4, Real>(a, r.slots, r.comp, r.all_affine, r.kernel, s);
+    case 8: return stage_ns<D, P, 8, Real>(a, r.slots, r.comp, r.all_affine, r.kernel, s);
   }
   return cudaErrorInvalidConfiguration;
 }
@@ -437,12 +430,12 @@ static cudaError_t convert_p(size_t outer, int inner, void* X, int to_nodal, con
     return cudaErrorInvalidValue;                                                           \
   }                                                                                         \
   template <>                                                                               \
-  int stage_occupancy<DIM, REAL>(int p, int n, int comp) {                                  \
+  int stage_occupancy<DIM, REAL>(int p, int n, int comp, int kernel) {                      \
     switch (p) {                                                                            \
-      case 0: return stage_blocks_per_sm<DIM, 0, REAL>(n, comp);                            \
-      case 1: return stage_blocks_per_sm<DIM, 1, REAL>(n, comp);                            \
-      case 2: return stage_blocks_per_sm<DIM, 2, REAL>(n, comp);                            \
-      case 3: return stage_blocks_per_sm<DIM, 3, REAL>(n, comp);                            \
+      case 0: return stage_blocks_per_sm<DIM, 0, REAL>(n, comp, kernel);                    \
+      case 1: return stage_blocks_per_sm<DIM, 1, REAL>(n, comp, kernel);                    \
+      case 2: return stage_blocks_per_sm<DIM, 2, REAL>(n, comp, kernel);                    \
+      case 3: return stage_blocks_per_sm<DIM, 3, REAL>(n, comp, kernel);                    \
     }                                                                                       \
     return 0;                                                                               \
   }                                                                                         \

@@ -15,6 +15,7 @@ struct RtTables {
 
 struct RtStage {
   int p, nL, n, zchunk, slots;
+  int kernel;  // 0: the cell-pair kernel where it applies, 1: k_stage
   const void* U;
   const void* Un;
   void* Uout;
@@ -133,6 +134,6 @@ template <int D, typename Real>
 size_t stage_smem_bytes(int p, int n);
 // resident stage CTAs per SM (0: does not fit)
 template <int D, typename Real>
-int stage_occupancy(int p, int n, int comp);
+int stage_occupancy(int p, int n, int comp, int kernel);
 
 }  // namespace dgf

@@ -110,6 +110,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// keeps the compiler from merging two evaluations of the same metric (one
+// for the face normals before the face fluxes, one for the volume points
+// after them), so the metric is not held in registers across the fluxes
+__device__ __forceinline__ void reload_fence() { asm volatile("" ::: "memory"); }
+
 // ------------------------------------------------------------- Euler, x2
 // F . a for a pair of states (Eq. (2)); also returns v.a, p and 1/rho
 __device__ __forceinline__ void flux2(const float2 (&u)[5], const float2 (&a)[3], float2 gm1, float2 (&F)[5],
@@ -419,11 +424,20 @@ __global__ void __launch_bounds__(pairk::PairCfg<P>::NT, pairk::PairCfg<P>::MINB
             tp[v] = fma2(f2(T.lp[qx]), x, tp[v]);
           }
         }
-        LineGeo2<0> lg;
-        if (!aff) {
+        // face normals at xi_x = -1 (both cells) and +1; the metric along the
+        // line is evaluated again for the volume points below
+        float2 Jm[3], Jp[3];
+        if (aff) {
+#pragma unroll
+          for (int jj = 0; jj < 3; ++jj) Jm[jj] = Jp[jj] = f2(sam[jj]);
+        } else {
+          LineGeo2<0> lg;
           const float xi[3] = {0.f, xa, xb};
           lg.init(Gc, cl, xi);
+          lg.at(-1.f, Jm);
+          lg.at(1.f, Jp);
         }
+        reload_fence();
         // left face of each cell of the pair: (face i0, face i0+1)
         float2 Fl[NV];
         float Fr[NV];
@@ -434,12 +448,8 @@ __global__ void __launch_bounds__(pairk::PairCfg<P>::NT, pairk::PairCfg<P>::MINB
             const float nb = __shfl_up_sync(0xffffffffu, tp[v].y, 1);
             uL[v] = make_float2(m == 0 ? GTR(0, v, fpX, tg_row) : nb, tp[v].x);
           }
-          if (aff) {
 #pragma unroll
-            for (int jj = 0; jj < 3; ++jj) Ja[jj] = f2(sam[jj]);
-          } else {
-            lg.at(-1.f, Ja);
-          }
+          for (int jj = 0; jj < 3; ++jj) Ja[jj] = Jm[jj];
           lf2(uL, tm, Ja, gam, gm1, Fl);
         }
         if (MORTAR && m == 0 && (fmask & 1)) {
@@ -460,19 +470,17 @@ __global__ void __launch_bounds__(pairk::PairCfg<P>::NT, pairk::PairCfg<P>::MINB
               ul[v] = tp[v].y;
               ur[v] = GTR(1, v, fpX, tg_row);
             }
-            if (aff) {
 #pragma unroll
-              for (int jj = 0; jj < 3; ++jj) Jr[jj] = sam[jj];
-            } else {
-              float2 J2[3];
-              lg.at(1.f, J2);
-#pragma unroll
-              for (int jj = 0; jj < 3; ++jj) Jr[jj] = J2[jj].y;
-            }
+            for (int jj = 0; jj < 3; ++jj) Jr[jj] = Jp[jj].y;
             lf_flux<3, float>(ul, ur, Jr, A.gamma, Fh);
 #pragma unroll
             for (int v = 0; v < NV; ++v) Fr[v] = Fh[v];
           }
+        }
+        LineGeo2<0> lg;
+        if (!aff) {
+          const float xi[3] = {0.f, xa, xb};
+          lg.init(Gc, cl, xi);
         }
         float2 r[N][NV];
 #pragma unroll
@@ -520,11 +528,18 @@ __global__ void __launch_bounds__(pairk::PairCfg<P>::NT, pairk::PairCfg<P>::MINB
             tp[v] = fma2(f2(T.lp[qy]), x, tp[v]);
           }
         }
-        LineGeo2<1> lg;
-        if (!aff) {
+        float2 Jm[3], Jp[3];
+        if (aff) {
+#pragma unroll
+          for (int jj = 0; jj < 3; ++jj) Jm[jj] = Jp[jj] = f2(sam[3 + jj]);
+        } else {
+          LineGeo2<1> lg;
           const float xi[3] = {xa, 0.f, xb};
           lg.init(Gc, cl, xi);
+          lg.at(-1.f, Jm);
+          lg.at(1.f, Jp);
         }
+        reload_fence();
         // bottom face of my row: the row below's top trace, or the guard trace
         float2 Fb[NV], Ft[NV];
         {
@@ -534,12 +549,8 @@ __global__ void __launch_bounds__(pairk::PairCfg<P>::NT, pairk::PairCfg<P>::MINB
             const float2 nb = shfl_up2(tp[v], 4);
             uL[v] = j == 0 ? lds2(&GTR(2, v, fpY, tg_col)) : nb;
           }
-          if (aff) {
 #pragma unroll
-            for (int jj = 0; jj < 3; ++jj) Ja[jj] = f2(sam[3 + jj]);
-          } else {
-            lg.at(-1.f, Ja);
-          }
+          for (int jj = 0; jj < 3; ++jj) Ja[jj] = Jm[jj];
           lf2(uL, tm, Ja, gam, gm1, Fb);
         }
         if (MORTAR && j == 0 && (fmask & 4)) {
@@ -556,15 +567,13 @@ __global__ void __launch_bounds__(pairk::PairCfg<P>::NT, pairk::PairCfg<P>::MINB
 #pragma unroll
             for (int v = 0; v < NV; ++v) Ft[v] = ur[v];
           } else {
-            float2 Jt[3];
-            if (aff) {
-#pragma unroll
-              for (int jj = 0; jj < 3; ++jj) Jt[jj] = f2(sam[3 + jj]);
-            } else {
-              lg.at(1.f, Jt);
-            }
-            lf2(tp, ur, Jt, gam, gm1, Ft);
+            lf2(tp, ur, Jp, gam, gm1, Ft);
           }
+        }
+        LineGeo2<1> lg;
+        if (!aff) {
+          const float xi[3] = {xa, 0.f, xb};
+          lg.init(Gc, cl, xi);
         }
         float2 r[N][NV];
 #pragma unroll
@@ -610,11 +619,6 @@ __global__ void __launch_bounds__(pairk::PairCfg<P>::NT, pairk::PairCfg<P>::MINB
 #pragma unroll
           for (int qz = 0; qz < N; ++qz) tp[v] = fma2(f2(T.lp[qz]), lds2(Uc + (v * Q + fpZ + NFP * qz) * LAY + cl), tp[v]);
         }
-        LineGeo2<2> lg;
-        if (!aff) {
-          const float xi[3] = {xa, xb, 0.f};
-          lg.init(Gc, cl, xi);
-        }
         {
           // the next layer's bottom trace (same arithmetic as at a chunk start)
           float2 th[NV], Ja[3];
@@ -636,13 +640,22 @@ __global__ void __launch_bounds__(pairk::PairCfg<P>::NT, pairk::PairCfg<P>::MINB
 #pragma unroll
             for (int jj = 0; jj < 3; ++jj) Ja[jj] = f2(sam[6 + jj]);
           } else {
+            LineGeo2<2> lg;
+            const float xi[3] = {xa, xb, 0.f};
+            lg.init(Gc, cl, xi);
             lg.at(1.f, Ja);
           }
+          reload_fence();
           lf2(tp, th, Ja, gam, gm1, Ft);
           if (MORTAR && k == n - 1 && (fmask & 32)) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) Ft[v] = th[v];  // the z+ face flux itself
           }
+        }
+        LineGeo2<2> lg;
+        if (!aff) {
+          const float xi[3] = {xa, xb, 0.f};
+          lg.init(Gc, cl, xi);
         }
         float2 r[N][NV], iJ[N];
 #pragma unroll

@@ -268,18 +268,21 @@ def test_compensated_state_drifts_less_than_plain_fp32(dgf):
 
 
 # ----------------------------------------------------- tiling invariance
-@pytest.mark.parametrize("prec", ["fp32", "fp64", "fp32_comp"])
-def test_chunk_length_does_not_change_bits(dgf, prec, monkeypatch):
+@pytest.mark.parametrize("prec,kernel", [("fp32", "pair"), ("fp32", "classic"), ("fp64", "classic"),
+                                         ("fp32_comp", "classic")])
+def test_chunk_length_does_not_change_bits(dgf, prec, kernel, monkeypatch):
     """The stage kernel's z-chunk length (a tiling choice, tuned by timing)
     leaves every bit of the residual and of the stepped state unchanged, also
-    with a ragged last chunk, so results are reproducible run to run."""
+    with a ragged last chunk, so results are reproducible run to run; for
+    each stage kernel (the cell-pair FP32 kernel and the layer-sweep one)."""
     w = W.jitter3d_forest(seed=2)
     U0 = W.random_modal_state(71, 3, 8, 2, seed=11)
+    monkeypatch.setenv("DGF_STAGE_KERNEL", kernel)
     out = []
     for z in (8, 4, 3, 1):
         monkeypatch.setenv("DGF_ZCHUNK", str(z))
         f = dgf.Forest.from_workload(w, p=2, precision=prec)
-        assert f.tuning()["zchunk"] == z
+        assert f.tuning()["zchunk"] == z and f.tuning()["stage_kernel"] == kernel
         f.set_state(U0)
         R = f.dg_residual()
         f.run(2)

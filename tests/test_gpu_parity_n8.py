@@ -22,7 +22,11 @@ from test_gpu_parity import TOL, assert_matches, rel
 
 pytestmark = pytest.mark.gpu
 
-CONFIGS = [("fp32", 1), ("fp32", 2), ("fp32", 3), ("fp64", 1), ("fp64", 2), ("fp32_comp", 2)]
+# (precision, p, stage kernel): FP32 at p = 1, 2 has two stage kernels (the
+# cell-pair kernel and the layer-sweep kernel; the autotuner picks one by
+# timing), both are compared
+CONFIGS = [("fp32", 1, "pair"), ("fp32", 1, "classic"), ("fp32", 2, "pair"), ("fp32", 2, "classic"),
+           ("fp32", 3, "classic"), ("fp64", 1, "classic"), ("fp64", 2, "classic"), ("fp32_comp", 2, "classic")]
 
 
 @pytest.fixture(scope="module")
@@ -39,12 +43,13 @@ def two_root_forest():
 
 
 @pytest.mark.parametrize("mode", ["paper", "mortar"])
-@pytest.mark.parametrize("prec,p", CONFIGS)
-def test_n8_residual_and_step_match_oracle(dgf, prec, p, mode):
+@pytest.mark.parametrize("prec,p,kernel", CONFIGS)
+def test_n8_residual_and_step_match_oracle(dgf, prec, p, kernel, mode, monkeypatch):
+    monkeypatch.setenv("DGF_STAGE_KERNEL", kernel)
     w = two_root_forest()
     pr = {"fp64": dgf.FP64, "fp32": dgf.FP32, "fp32_comp": dgf.FP32_COMP}[prec]
     f = dgf.Forest.from_workload(w, p=p, precision=pr, cfl=0.2, nonconforming=mode)
-    assert f.n_leaves == 9 and f.n_seg == 8
+    assert f.n_leaves == 9 and f.n_seg == 8 and f.tuning()["stage_kernel"] == kernel
     S = dg.Solver(FO.build(w), p, cfl=0.2, nonconforming=mode)
     U = W.random_modal_state(f.n_leaves, 3, 8, p, seed=10 * p + (mode == "mortar"))
     if prec == "fp32":
@@ -54,6 +59,7 @@ def test_n8_residual_and_step_match_oracle(dgf, prec, p, mode):
     dt = S.dt(U)
     assert abs(f.compute_dt() - dt) <= (1e-13 if prec == "fp64" else 1e-5) * dt
     f.rk_step()
+    assert f.tuning()["stage_kernel"] == kernel
     U1 = S.ssp_rk3_step(U, dt)
     assert rel(f.get_state(), U1) < TOL["fp64" if prec == "fp64" else "fp32"]
     assert f.status_word() == 0
