@@ -26,6 +26,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -289,7 +290,8 @@ def run_ours(args):
         f.project(vortex)
         return f
 
-    f32 = make(pkg.FP32)
+    f32 = make({"fp32": pkg.FP32, "fp64": pkg.FP64, "fp32_comp": pkg.FP32_COMP}[args.precision] if args.quick
+               else pkg.FP32)
     dof = f32.n_leaves * f32.nv * f32.M * f32.nc
     U0 = f32.get_state()
     for _ in range(args.warmup):
@@ -302,7 +304,8 @@ def run_ours(args):
     status = f32.status_word()
     if args.quick:
         if rank == 0:
-            print(json.dumps({"workload": WORKLOADS[_SEL[0]][0], "value": value, "unit": "DOF-updates/s",
+            print(json.dumps({"workload": WORKLOADS[_SEL[0]][0], "precision": args.precision, "value": value,
+                              "unit": "DOF-updates/s", "tuning": f32.tuning(),
                               "ms_per_step": ms / args.steps, "dof": dof, "status_word": status,
                               "nonconforming": _NC[0], "clocks": ck.summary()}))
         return 0
@@ -411,7 +414,7 @@ def run_ours(args):
         # affine periodic cubes far above L2 (each state copy 0.34 / 1.13 GB)
         line["over_l2"] = {k: over_l2_case(k, args, stream, flush, pk, pk_kind, torch, pkg) for k in OVER_L2}
         line["serve"] = run_serve(args, sub=True)
-        line["amr"] = run_amr(args, sub=True)
+        line["amr"] = {f"p{q}": run_amr(args, sub=True, p=q, periods=args.amr_sub_periods) for q in (1, 3)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
@@ -585,10 +588,12 @@ def run_serve(args, sub=False):
 
 
 # ---------------------------------------------------------------- dynamic AMR
-AMR = dict(B=4, n_seg=8, p=1, refine_above=0.05, coarsen_below=0.01, max_level=4, every=10, limiter=1e-6)
+# every 40 steps the blast front has moved far enough that most regrids change
+# the forest; CFL 0.3 / (2p + 1) (0.1 at p = 1, 0.06 at p = 2), 0.02 at p = 3
+AMR = dict(B=4, n_seg=8, p=1, refine_above=0.05, coarsen_below=0.01, max_level=4, every=40, limiter=1e-6)
 
 
-def run_amr(args, sub=False):
+def run_amr(args, sub=False, p=None, periods=None):
     """Blast on a periodic cube of 4^3 roots with dynamic refinement: the
     device indicator and adaptation (2:1 closure, state moved on the device)
     every `every` steps, the positivity limiter after every stage, FP32.
@@ -602,11 +607,13 @@ def run_amr(args, sub=False):
         import torch.distributed as dist
         dist.init_process_group("gloo")
     torch.cuda.set_device(local)
-    cfg = AMR
+    cfg = dict(AMR)
+    cfg["p"] = p if p is not None else args.amr_p
+    cfg["cfl"] = 0.3 / (2 * cfg["p"] + 1) if cfg["p"] < 3 else 0.02
     w = W.periodic_cube_forest(cfg["B"], n_seg=cfg["n_seg"])
     width = 1.0 / (cfg["B"] * cfg["n_seg"] * 2 ** (cfg["max_level"] - 1))
     ic = lambda x: W.blast(x, (0.5, 0.5, 0.5), r0=0.12, width=width)
-    f = pkg.Forest.from_workload(w, p=cfg["p"], precision=pkg.FP32, device=local)
+    f = pkg.Forest.from_workload(w, p=cfg["p"], precision=pkg.FP32, device=local, cfl=cfg["cfl"])
     stream = torch.cuda.Stream()
     f.set_stream(stream)
     f.set_limiter(cfg["limiter"])
@@ -624,10 +631,11 @@ def run_amr(args, sub=False):
     for _ in range(args.warmup):
         f.rk_step()
     torch.cuda.synchronize()
-    steps = (args.amr_sub_periods if sub else args.steps) * cfg["every"]
+    steps = (periods if periods is not None else args.steps) * cfg["every"]
     updates = 0
     leaves = []
     regrid_s = 0.0
+    regrid_changed_s = 0.0
     changes = 0
     with Clocks(local) as ck:
         t0 = time.perf_counter()
@@ -640,19 +648,26 @@ def run_amr(args, sub=False):
                 stream.synchronize()  # time the regrid alone
                 r0 = time.perf_counter()
                 nr, nc = f.adapt(cfg["refine_above"], cfg["coarsen_below"], cfg["max_level"])
-                regrid_s += time.perf_counter() - r0
-                changes += (nr > 0 or nc > 0)
+                if nr > 0 or nc > 0:
+                    f.limit()  # split children of a steep profile can leave the admissible set
+                dtr = time.perf_counter() - r0
+                regrid_s += dtr
+                if nr > 0 or nc > 0:
+                    changes += 1
+                    regrid_changed_s += dtr
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     status = f.status_word()
     amr = {"leaves_min": min(leaves), "leaves_max": max(leaves), "leaves_end": f.n_leaves,
            "regrids": steps // cfg["every"], "regrids_that_changed_the_forest": changes,
            "regrid_s": regrid_s, "regrid_ms_each": 1e3 * regrid_s / max(1, steps // cfg["every"]),
+           "regrid_ms_each_changed": 1e3 * regrid_changed_s / max(1, changes),
+           "regrid_ms_each_unchanged": 1e3 * (regrid_s - regrid_changed_s) / max(1, steps // cfg["every"] - changes),
            "wall_s": wall, "status_word": status, "t_end": f.time}
+    name = f"3d-blast-periodic-cube-4^3-roots-n8-p{cfg['p']}-adaptive-to-level-4"
     if sub:
         f.close()
-        return {"workload": "3d-blast-periodic-cube-4^3-roots-n8-p1-adaptive-to-level-4", "value": updates / wall,
-                "unit": "DOF-updates/s", "steps": steps, **amr, **cfg}
+        return {"workload": name, "value": updates / wall, "unit": "DOF-updates/s", "steps": steps, **amr, **cfg}
     value, ms = job_throughput(updates, 1e3 * wall, ws)
     if rank != 0:
         return 0
@@ -661,11 +676,163 @@ def run_amr(args, sub=False):
         "unit": "DOF-updates/s", "n_gpus": ws, "steps": steps, "warmup": args.warmup,
         "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "3d-blast-periodic-cube-4^3-roots-n8-p1-adaptive-to-level-4", **cfg},
+        "config": {"workload": name, **cfg},
         "amr": amr,
         "clocks": ck.summary(),
     }
     print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- precision sweep
+SWEEP = dict(t_end=0.005, cfl=0.1, vortex_box=20.0, runs=((1, (8, 16, 32)), (2, (8, 16, 32)), (3, (8, 16))))
+
+
+def _cube_points(B, p, torch, dev):
+    """Gauss points of the affine periodic cube of B^3 roots of 8^3 cells, on
+    the device, in the library's nodal order [leaf][cell][point][axis] (leaf
+    = root = bx + B by + B^2 bz, cell = i + 8 j + 64 k, point = qx + N qy +
+    N^2 qz)."""
+    N = p + 1
+    xg = torch.tensor(np.polynomial.legendre.leggauss(N)[0], dtype=torch.float64, device=dev)
+    h = 1.0 / (8 * B)
+    b = torch.arange(B, dtype=torch.float64, device=dev)
+    c = torch.arange(8, dtype=torch.float64, device=dev)
+    # 1D coordinate of (block, cell, point) along one axis
+    ax = (b[:, None, None] / B + c[None, :, None] * h + h * (xg[None, None, :] + 1) / 2)  # [B][8][N]
+    X = ax[None, None, :, None, None, :, None, None, :].expand(B, B, B, 8, 8, 8, N, N, N)
+    Y = ax[None, :, None, None, :, None, None, :, None].expand(B, B, B, 8, 8, 8, N, N, N)
+    Z = ax[:, None, None, :, None, None, :, None, None].expand(B, B, B, 8, 8, 8, N, N, N)
+    # index order above: [bz][by][bx][k][j][i][qz][qy][qx]
+    return torch.stack([X, Y, Z], -1).reshape(B ** 3, 512, N ** 3, 3)
+
+
+def _vortex_t(x, t, torch):
+    """The isentropic vortex of the bench mapped into the unit cube from a
+    20-unit box (so the periodic cut of its Gaussian tail, e^-50, sets no
+    error floor), translated by the free stream to time t, nearest periodic
+    image (as workloads.vortex_exact), on torch tensors: conserved variables
+    [..., 5]."""
+    beta, gamma, scale, period = 5.0, 1.4, 20.0, 20.0
+    cx = (10.0 + t * scale) % period
+    cy = (10.0 + t * scale) % period
+    X = scale * x[..., 0]
+    Y = scale * x[..., 1]
+    dx = torch.remainder(X - cx + period / 2, period) - period / 2
+    dy = torch.remainder(Y - cy + period / 2, period) - period / 2
+    r2 = dx * dx + dy * dy
+    e = torch.exp(0.5 * (1.0 - r2))
+    u = 1.0 - beta / (2 * math.pi) * e * dy
+    v = 1.0 + beta / (2 * math.pi) * e * dx
+    w = torch.ones_like(u)
+    T = 1.0 - (gamma - 1.0) * beta ** 2 / (8.0 * gamma * math.pi ** 2) * torch.exp(1.0 - r2)
+    rho = T ** (1.0 / (gamma - 1.0))
+    pr = rho ** gamma
+    E = pr / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)
+    return torch.stack([rho, rho * u, rho * v, rho * w, E], -1)
+
+
+def _to_nodal_t(K, p, torch):
+    """Modal [leaf][var][mode][cell] -> values at the Gauss points, on the device."""
+    N = p + 1
+    x = np.polynomial.legendre.leggauss(N)[0]
+    V = torch.tensor([[np.polynomial.legendre.legval(xq, [0] * k + [1]) for k in range(N)] for xq in x],
+                     dtype=K.dtype, device=K.device)
+    L, nv, M, nc = K.shape
+    A = K.reshape(L, nv, N, N, N, nc)  # (k_z, k_y, k_x)
+    A = torch.einsum("ak,lvzykc->lvzyac", V, A)
+    A = torch.einsum("ak,lvzkxc->lvzaxc", V, A)
+    A = torch.einsum("ak,lvkyxc->lvayxc", V, A)
+    return A.reshape(L, nv, M, nc)
+
+
+def run_sweep(args):
+    """Accuracy and throughput sweep on periodic cubes of B^3 roots (8^3
+    cells each) with the scaled isentropic vortex: FP64, FP32 and the
+    compensated FP32 form per (p, B); L2 / Linf error against the exact
+    translated vortex (observed order from successive B), FP32 against FP64
+    on the same steps, conservation drift, DOF-updates/s."""
+    import torch
+    import paper_2502_12620_gb300 as pkg
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream()
+    rows = []
+    for p, Bs in SWEEP["runs"]:
+        N = p + 1
+        wq = torch.tensor(np.polynomial.legendre.leggauss(N)[1], dtype=torch.float64, device=dev)
+        W3 = (wq[None, None, :] * wq[None, :, None] * wq[:, None, None]).reshape(-1)  # [q] (qz, qy, qx)
+        for B in Bs:
+            w = W.periodic_cube_forest(B)
+            X = _cube_points(B, p, torch, dev)
+            if B == 8:  # the device points are the library's
+                h = pkg.Forest.from_workload(w, p=p, device=-1)
+                assert np.allclose(h.quad_points(), X.cpu().numpy(), atol=1e-14)
+                h.close()
+            U0 = _vortex_t(X, 0.0, torch).permute(0, 1, 2, 3).contiguous()  # [leaf][cell][q][v]
+            res = {}
+            for name, prec in (("fp64", pkg.FP64), ("fp32", pkg.FP32), ("fp32_comp", pkg.FP32_COMP)):
+                f = pkg.Forest.from_workload(w, p=p, precision=prec, device=local, cfl=SWEEP["cfl"])
+                f.set_stream(stream)
+                f.set_state_nodal(U0)
+                T0 = f.conserved_totals()
+                f.rk_step(t_end=0.0)  # tunes the stage kernel; an increment at t_end is the identity
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                steps = 0
+                with torch.cuda.stream(stream):
+                    e0.record(stream)
+                    while True:
+                        f.rk_step(t_end=SWEEP["t_end"])
+                        steps += 1
+                        if steps % 8 == 0 and f.time >= SWEEP["t_end"] * (1 - 1e-12):
+                            break
+                    e1.record(stream)
+                stream.synchronize()
+                ms = e0.elapsed_time(e1)
+                t = f.time
+                steps = f.step_count
+                T1 = f.conserved_totals()
+                K = torch.empty(f.state_shape, dtype=torch.float64 if prec != pkg.FP32 else torch.float32, device=dev)
+                f.get_state(K)
+                Un = _to_nodal_t(K.double(), p, torch)  # [leaf][var][q][cell]
+                del K
+                ex = _vortex_t(X, t, torch).permute(0, 3, 2, 1)  # [leaf][var][q][cell]
+                d = Un - ex
+                l2 = float(torch.sqrt(torch.einsum("q,lvqc->", W3, d * d) / torch.einsum("q,lvqc->", W3, ex * ex)))
+                linf = float(d.abs().max() / ex.abs().max())
+                del d, ex
+                dof = f.n_leaves * f.nv * f.M * f.nc
+                res[name] = {"l2_vs_exact": l2, "linf_vs_exact": linf, "steps": steps, "t": t,
+                             "dof_updates_per_s": dof * 3 * steps / (ms / 1e3),
+                             "conservation_drift": float(np.max(np.abs(T1 - T0)) / np.max(np.abs(T0))),
+                             "status_word": f.status_word()}
+                if name == "fp64":
+                    U64 = Un
+                else:
+                    dd = Un - U64
+                    res[name]["l2_rel_vs_fp64"] = float(torch.linalg.vector_norm(dd) / torch.linalg.vector_norm(U64))
+                    res[name]["linf_rel_vs_fp64"] = float(dd.abs().max() / U64.abs().max())
+                    del dd
+                del Un
+                f.close()
+                torch.cuda.empty_cache()
+            del U64, U0, X
+            torch.cuda.empty_cache()
+            rows.append({"p": p, "B": B, "leaves": B ** 3, "dof": B ** 3 * 512 * 5 * N ** 3, **res})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    # observed order from successive B (h halves)
+    for i in range(1, len(rows)):
+        a, b = rows[i - 1], rows[i]
+        if a["p"] == b["p"]:
+            for name in ("fp64", "fp32", "fp32_comp"):
+                b[name]["observed_order"] = math.log2(a[name]["l2_vs_exact"] / b[name]["l2_vs_exact"])
+    if rank == 0:
+        print(json.dumps({"metric": "precision sweep: error vs exact vortex, FP32 vs FP64, DOF-updates/s",
+                          "config": {"workload": "3d-euler-periodic-cube-B^3-roots-n8-isentropic-vortex", **SWEEP},
+                          "rows": rows}))
     return 0
 
 
@@ -677,15 +844,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="jitter3d", choices=sorted(WORKLOADS))
-    ap.add_argument("--quick", action="store_true", help="FP32 timed steps only (profiling runs)")
+    ap.add_argument("--quick", action="store_true", help="timed steps only (profiling runs)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_comp"],
+                    help="precision of the --quick run")
     ap.add_argument("--serve", action="store_true", help="continuous-batching run instead of the step benchmark")
     ap.add_argument("--amr", action="store_true", help="dynamic-refinement blast run (steps = regrid periods)")
+    ap.add_argument("--sweep", action="store_true", help="accuracy / precision sweep on periodic vortex cubes")
     ap.add_argument("--nonconforming", default="paper", choices=["paper", "mortar"],
                     help="level jumps: the paper's guard-cell scheme (default) or the conservative mortar repair")
     ap.add_argument("--quick-line", action="store_true",
                     help="the step line without the over-L2, serving and AMR sub-objects")
     ap.add_argument("--serve-sub-requests", type=int, default=16)
-    ap.add_argument("--amr-sub-periods", type=int, default=6)
+    ap.add_argument("--amr-sub-periods", type=int, default=10)
+    ap.add_argument("--amr-p", type=int, default=1, help="degree of the --amr run")
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--serve-active", type=int, default=8)
     args = ap.parse_args()
@@ -699,6 +870,8 @@ def main():
         return run_serve(args)
     if args.amr:
         return run_amr(args)
+    if args.sweep:
+        return run_sweep(args)
     return run_ours(args)
 
 

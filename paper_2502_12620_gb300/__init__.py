@@ -324,6 +324,14 @@ class Forest:
         return a
 
     def set_state_nodal(self, vals):
+        """Point values [leaf][cell][point][var] in FP64 (numpy, or a CUDA tensor)."""
+        if self._is_torch(vals):
+            import torch
+            assert vals.is_cuda and vals.is_contiguous() and vals.dtype == torch.float64
+            assert vals.numel() == self.n_leaves * self.nc * self.M * self.nv
+            torch.cuda.current_stream().synchronize()
+            _check(lib().dgf_set_state_nodal(self.h, ctypes.c_void_p(vals.data_ptr()), 1))
+            return
         v = np.ascontiguousarray(vals, np.float64).reshape(self.n_leaves, self.nc, self.M, self.nv)
         _check(lib().dgf_set_state_nodal(self.h, _ptr(v), 0))
 
