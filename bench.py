@@ -545,8 +545,9 @@ def run_serve(args, sub=False):
     # warm-up: one small solve of every degree (module load, allocator pool)
     warm = [serve.Request(-1 - p, 0.0, W.periodic_cube_forest(2), p, 1e-3, W.smooth_state, pkg.FP32)
             for p in SERVE_MIX["degrees"]]
-    serve.Server(device=local, max_active=4).run(warm)
-    srv = serve.Server(device=local, max_active=args.serve_active, steps_per_round=8)
+    batched = not args.serve_streams
+    serve.Server(device=local, max_active=4, batched=batched).run(warm)
+    srv = serve.Server(device=local, max_active=args.serve_active, steps_per_round=8, batched=batched)
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -558,12 +559,26 @@ def run_serve(args, sub=False):
     sm = serve.summarize(res, wall)
     updates = sum(r.dof * 3 * r.steps for r in res)
     if sub:
-        return {"workload": "serving-mix-periodic-cubes-64-512-blocks-n8-p1-3-blast-or-vortex",
-                "requests": len(res), "value": updates / wall, "unit": "DOF-updates/s",
-                "p50_s": sm["p50_s"], "p99_s": sm["p99_s"], "wall_s": wall, "max_active": args.serve_active,
-                "failed": sum(1 for r in res if r.status != 0), "peak_active": srv.peak_active,
-                "mean_queue_s": float(np.mean([r.admitted - r.arrival for r in res])),
-                "payload_prep_s": t_prep, **{k: list(v) if isinstance(v, tuple) else v for k, v in SERVE_MIX.items()}}
+        out = {"workload": "serving-mix-periodic-cubes-64-512-blocks-n8-p1-3-blast-or-vortex",
+               "requests": len(res), "value": updates / wall, "unit": "DOF-updates/s",
+               "p50_s": sm["p50_s"], "p99_s": sm["p99_s"], "wall_s": wall, "max_active": args.serve_active,
+               "mode": "batched: one launch per kernel and stage for the solves of one degree" if batched
+               else "one stream and graph per solve",
+               "failed": sum(1 for r in res if r.status != 0), "peak_active": srv.peak_active,
+               "mean_queue_s": float(np.mean([r.admitted - r.arrival for r in res])),
+               "payload_prep_s": t_prep, **{k: list(v) if isinstance(v, tuple) else v for k, v in SERVE_MIX.items()}}
+        if batched:
+            # the same requests, one stream and graph per solve (for comparison)
+            srv2 = serve.Server(device=local, max_active=args.serve_active, steps_per_round=8, batched=False)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            res2 = srv2.run(reqs)
+            torch.cuda.synchronize()
+            wall2 = time.perf_counter() - t1
+            sm2 = serve.summarize(res2, wall2)
+            out["per_solve_streams"] = {"value": sum(r.dof * 3 * r.steps for r in res2) / wall2,
+                                        "p50_s": sm2["p50_s"], "p99_s": sm2["p99_s"], "wall_s": wall2}
+        return out
     value, ms = job_throughput(updates, 1e3 * wall, ws)
     if rank != 0:
         return 0
@@ -858,6 +873,8 @@ def main():
     ap.add_argument("--amr-sub-periods", type=int, default=10)
     ap.add_argument("--amr-p", type=int, default=1, help="degree of the --amr run")
     ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-streams", action="store_true",
+                    help="serve with one stream and graph per solve instead of batches per degree")
     ap.add_argument("--serve-active", type=int, default=8)
     args = ap.parse_args()
     _SEL[0] = args.workload

@@ -313,6 +313,40 @@ dgf_status dgf_kernel_times(dgf_forest* f, double* ms, int64_t* launches, int n_
  * the forest's stream. */
 dgf_status dgf_dg_residual_noalloc(dgf_forest* f, const void* U_nodal, void* L_nodal);
 
+/* Batches: several independent forests advanced together, one launch of
+ * each kernel per stage for all of them (the paper's per-block loop of
+ * Sec. 4.3 run over the blocks of every member; the members' kernel
+ * arguments live in device arrays and each work item finds its forest from
+ * prefix sums), one CUDA graph per membership.  Members keep their own
+ * time, end time, time increment (Sec. 4.3 CFL step, reading R5) and CFL
+ * minimum; a member at its end time is left unchanged by further steps, so
+ * a member's result is the one it gets as the only member of a batch.
+ * Members: forests on the batch's device, 3D, n_seg 8, one degree p, FP32
+ * plain form (DGF_FP32), no mortar repair, no limiter, state set
+ * (DGF_EUNSUPPORTED / DGF_EINVAL / DGF_ESTATE otherwise).  The batch owns
+ * small device arrays (cudaMalloc); the forests keep owning their state.
+ *   dgf_batch_create   device ordinal; stream (cudaStream_t) or NULL for an
+ *                      own stream.
+ *   dgf_batch_set      replace the members (n may be 0) and set each
+ *                      member's end time t_end[i]; waits for the members'
+ *                      own streams and the batch stream.  Call again after
+ *                      a member is regridded, refined or destroyed.
+ *   dgf_batch_step     enqueue `steps` time increments of every member on
+ *                      the batch stream (asynchronous).
+ *   dgf_batch_sync     wait for the batch stream (dgf_batch_query: has it
+ *                      finished?); member queries
+ *                      (dgf_get_time, dgf_get_state, ...) run on the
+ *                      member's own stream, so sync the batch first.
+ * No counterpart in the paper beyond the per-block loop (a serving layer). */
+typedef struct dgf_batch dgf_batch;
+dgf_status dgf_batch_create(int32_t device, void* stream, dgf_batch** out);
+dgf_status dgf_batch_destroy(dgf_batch* b);
+dgf_status dgf_batch_set(dgf_batch* b, dgf_forest* const* forests, const double* t_end, int32_t n);
+dgf_status dgf_batch_step(dgf_batch* b, int32_t steps);
+dgf_status dgf_batch_sync(dgf_batch* b);
+/* idle = 1 when all work enqueued on the batch stream has finished (no wait). */
+dgf_status dgf_batch_query(dgf_batch* b, int32_t* idle);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,12 @@ _SIGS = {
     "dgf_stage_kernel": [_P, ctypes.POINTER(ctypes.c_int32)],
     "dgf_kernel_times": [_P, _P, _P, ctypes.c_int],
     "dgf_dg_residual_noalloc": [_P, _P, _P],
+    "dgf_batch_create": [ctypes.c_int32, _P, ctypes.POINTER(_P)],
+    "dgf_batch_destroy": [_P],
+    "dgf_batch_set": [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_double), ctypes.c_int32],
+    "dgf_batch_step": [_P, ctypes.c_int32],
+    "dgf_batch_sync": [_P],
+    "dgf_batch_query": [_P, ctypes.POINTER(ctypes.c_int32)],
 }
 
 
@@ -420,4 +426,48 @@ class Forest:
         return {"dt": (ms[0], int(cnt[0])), "guard": (ms[1], int(cnt[1])), "stage": (ms[2], int(cnt[2]))}
 
 
-__all__ = ["Forest", "DgfError", "lib", "FP64", "FP32", "FP32_COMP", "NC_PAPER", "NC_MORTAR", "LIB_PATH"]
+class Batch:
+    """Forests advanced together: one launch of each kernel per stage for
+    all members (3D FP32 forests of 8^3-cell blocks, one degree, plain form).
+    Each member keeps its own time, end time and time increment."""
+
+    def __init__(self, device=0, stream=None):
+        self.device = int(device)
+        h = _P()
+        raw = None if stream is None else ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+        _check(lib().dgf_batch_create(self.device, raw, ctypes.byref(h)))
+        self.h = h
+        self.members = []
+
+    def set(self, forests, t_ends):
+        """Replace the members; t_ends[i] is member i's end time."""
+        n = len(forests)
+        hs = (_P * max(1, n))(*[f.h for f in forests])
+        te = (ctypes.c_double * max(1, n))(*[float(t) for t in t_ends])
+        _check(lib().dgf_batch_set(self.h, hs, te, n))
+        self.members = list(forests)
+
+    def step(self, steps=1):
+        _check(lib().dgf_batch_step(self.h, int(steps)))
+
+    def sync(self):
+        _check(lib().dgf_batch_sync(self.h))
+
+    def idle(self):
+        v = ctypes.c_int32()
+        _check(lib().dgf_batch_query(self.h, ctypes.byref(v)))
+        return bool(v.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dgf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+__all__ = ["Forest", "Batch", "DgfError", "lib", "FP64", "FP32", "FP32_COMP", "NC_PAPER", "NC_MORTAR", "LIB_PATH"]

@@ -246,8 +246,52 @@ struct StageArgs {
   const float* __restrict__ Din;   // compensated form: delta^(k), null at stage 1
   double* __restrict__ U64out;     // compensated form, last stage: u^(n+1) in FP64
   const unsigned char* __restrict__ fluxmask;  // [b] bit f: gtr holds face f's flux (mortar), or null
+  // batch launch (every forest of a batch in one launch): per-forest
+  // arguments in device memory, work items of forest m in
+  // [istart[m], istart[m+1]); null for a single-forest launch
+  const StageArgs* members;
+  const int* istart;
+  int nmem;
   Tab<P + 1, Real> T;
 };
+
+// index of the batch member whose range [start[m], start[m+1]) holds i
+__device__ __forceinline__ int batch_member(const int* __restrict__ start, int nmem, int i) {
+  int lo = 0, hi = nmem - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&start[mid]) <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// CTA minimum of v (one value per thread) folded into *dst with one atomic;
+// every thread of the CTA calls it
+template <int NTHR>
+__device__ __forceinline__ void cta_min_atomic(double v, unsigned long long* dst) {
+  __shared__ double red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u < v ? u : v;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < (NTHR + 31) / 32 ? red[lane] : 3.0e38;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double u = __shfl_xor_sync(0xffffffffu, v, o);
+      v = u < v ? u : v;
+    }
+    // a CTA whose cells were all inadmissible contributes nothing, so a
+    // broken state leaves no CFL value and the next dt is 0
+    if (lane == 0 && v < 3.0e38) atomicMin(dst, (unsigned long long)__double_as_longlong(v));
+  }
+  __syncthreads();
+}
 
 // Stage input u^(k) at a flat index: one array (plain), or u^n plus the FP32
 // increment delta^(k) (compensated SSP-RK3: the state accumulates in FP64,
@@ -499,10 +543,13 @@ __device__ __forceinline__ int face_point_index(int ax, int fp, int qn) {
 // (each face once); x volume + lift; y volume + lift (and the halo trace of
 // the next layer); z volume + z faces (carried between layers) and 1/J;
 // SSP-RK combination point by point, with the CFL minimum on the last stage.
+// BATCH: one launch for every forest of a batch (A.members; the tables and
+// stage coefficients of A are common to all of them).
 template <int D, int P, int NS, typename Real, bool COMP = false, bool MORTAR = false,
-          int YS = stage_rows<D, P, Real>(NS)>
+          int YS = stage_rows<D, P, Real>(NS), bool BATCH = false>
 __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB)
-    k_stage(const StageArgs<D, P, Real> A) {
+    k_stage(const __grid_constant__ StageArgs<D, P, Real> A) {
+  static_assert(!(BATCH && (COMP || MORTAR)), "batches run the plain form without the mortar repair");
   constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
   constexpr int NG = ((1 << D) - 1) * D;
   constexpr int n = NS;
@@ -517,10 +564,10 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
   const auto& T = A.T;
   const Real gamma = A.gamma;
   const Real gm1 = gamma - Real(1);
-  const Real dt = Real(*A.dtp);
+  Real dt = BATCH ? Real(0) : Real(*A.dtp);  // per forest of a batch: per item
   const int tid = threadIdx.x;
   constexpr int nthr = StageCfg<P, Real>::NT;
-  if (A.mode == 0 && *A.dtp == 0.0) {
+  if (!BATCH && A.mode == 0 && *A.dtp == 0.0) {
     // t_end reached: the increment is the identity and no stage is evaluated
     // (the CFL minimum of the last evaluated stage stays in place)
     if constexpr (COMP) {
@@ -547,7 +594,7 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
 
   Real lam_min = Real(3.0e38);
   bool bad = false;
-  const int items = A.nL * A.nchunks * NYS;
+  const int items = BATCH ? __ldg(&A.istart[A.nmem]) : A.nL * A.nchunks * NYS;
 
 #define US(v, q, c) us[((v) * Q + (q)) * NCL + (c)]
 #define RS(v, q, c) rs[((v) * Q + (q)) * NCL + (c)]
@@ -559,23 +606,36 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
 #define GTR(f, v, fp, t) Tb[(((size_t)(f) * NV + (v)) * NFP + (fp)) * nt + (t)]
 
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    const int b = item / (A.nchunks * NYS);
-    const int chunk = (item / NYS) % A.nchunks;
-    const int j0 = NYS == 1 ? 0 : (item % NYS) * YR;  // first row of the slab
-    const int k0 = D == 3 ? chunk * A.zchunk : 0;
-    const int k1 = D == 3 ? min(n, k0 + A.zchunk) : 1;
-    const Real* __restrict__ Ub = A.U + (size_t)b * NV * Q * nc;
-    const Real* __restrict__ Unb = A.Un + (size_t)b * NV * Q * nc;
+    // the forest of this item (a batch member, or the one forest)
+    const StageArgs<D, P, Real>* Mp = &A;
+    int li = item;
+    if constexpr (BATCH) {
+      const int m = batch_member(A.istart, A.nmem, item);
+      Mp = A.members + m;
+      li = item - __ldg(&A.istart[m]);
+      if (A.mode == 0 && *Mp->dtp == 0.0) continue;  // that forest has reached its end time
+      dt = Real(*Mp->dtp);
+    }
+    const StageArgs<D, P, Real>& M = *Mp;
+    const int b = li / (M.nchunks * NYS);
+    const int chunk = (li / NYS) % M.nchunks;
+    const int j0 = NYS == 1 ? 0 : (li % NYS) * YR;  // first row of the slab
+    const int k0 = D == 3 ? chunk * M.zchunk : 0;
+    const int k1 = D == 3 ? min(n, k0 + M.zchunk) : 1;
+    const Real* __restrict__ Ub = M.U + (size_t)b * NV * Q * nc;
+    const Real* __restrict__ Unb = M.Un + (size_t)b * NV * Q * nc;
     const size_t boff = (size_t)b * NV * Q * nc;
-    const StateIn<Real, COMP> Sb{A.U + boff, COMP ? A.U64 + boff : nullptr, COMP ? A.Uhi + boff : nullptr,
-                                 COMP ? A.Ulo + boff : nullptr, (COMP && A.Din) ? A.Din + boff : nullptr};
-    Real* __restrict__ Ob = A.Uout + (size_t)b * NV * Q * nc;
-    const Real* __restrict__ Gb = A.geo + (size_t)b * NG * nc;
-    const Real* __restrict__ Tb = A.gtr + (size_t)b * 2 * D * NV * NFP * nt;
-    const bool aff = A.affine[b] != 0;
-    const int fmask = MORTAR ? A.fluxmask[b] : 0;  // faces whose flux is given (mortar mode)
+    const StateIn<Real, COMP> Sb{M.U + boff, COMP ? M.U64 + boff : nullptr, COMP ? M.Uhi + boff : nullptr,
+                                 COMP ? M.Ulo + boff : nullptr, (COMP && M.Din) ? M.Din + boff : nullptr};
+    Real* __restrict__ Ob = M.Uout + (size_t)b * NV * Q * nc;
+    const Real* __restrict__ Gb = M.geo + (size_t)b * NG * nc;
+    const Real* __restrict__ Tb = M.gtr + (size_t)b * 2 * D * NV * NFP * nt;
+    const Real* __restrict__ Hb = M.hcell + (size_t)b * nc;
+    double* __restrict__ O64 = COMP ? M.U64out + boff : nullptr;
+    const bool aff = M.affine[b] != 0;
+    const int fmask = MORTAR ? M.fluxmask[b] : 0;  // faces whose flux is given (mortar mode)
     __syncthreads();  // previous item is done with the shared buffers
-    if (aff && tid < D * D + 1) sam[tid] = A.ameta[(size_t)b * (D * D + 1) + tid];
+    if (aff && tid < D * D + 1) sam[tid] = M.ameta[(size_t)b * (D * D + 1) + tid];
 
     for (int k = k0; k < k1; ++k) {
       const int cbase = (D == 3 ? k * LAY : 0) + j0 * n;  // first cell of the slab
@@ -1005,7 +1065,7 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
                 for (int e = 0; e < VEC; e += 2) {
                   const double2 un = __ldcg(reinterpret_cast<const double2*>(Sb.u64 + gi + e));
                   const double2 nw = make_double2(un.x + (double)val[e], un.y + (double)val[e + 1]);
-                  *reinterpret_cast<double2*>(A.U64out + boff + gi + e) = nw;
+                  *reinterpret_cast<double2*>(O64 + gi + e) = nw;
                   val[e] = (Real)nw.x;
                   val[e + 1] = (Real)nw.y;
                 }
@@ -1043,7 +1103,7 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
                 bad = true;
               } else {
                 const Real lam = sv + Real(D) * sqrt(gamma * pr * ri);
-                const Real hv = A.hcell[(size_t)b * nc + cbase + c0 + e] / lam;
+                const Real hv = Hb[cbase + c0 + e] / lam;
                 lam_min = hv < lam_min ? hv : lam_min;
               }
             }
@@ -1051,6 +1111,15 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
         }
       }
       __syncthreads();
+    }
+    if constexpr (BATCH) {
+      // the CFL minimum and the status belong to this item's forest
+      if (A.last) {
+        cta_min_atomic<nthr>((double)lam_min, M.lam_bits);
+        lam_min = Real(3.0e38);
+        if (__syncthreads_or(bad) && tid == 0) atomicExch(M.status, kStatusNonFinite);
+        bad = false;
+      }
     }
   }
 #undef US
@@ -1061,7 +1130,7 @@ __global__ void __launch_bounds__(StageCfg<P, Real>::NT, StageCfg<P, Real>::MINB
 #undef FZ
 #undef GTR
 
-  if (A.last) {
+  if (!BATCH && A.last) {
     // block min of h/lambda -> one atomic per CTA
     double v = (double)lam_min;
 #pragma unroll
@@ -1392,8 +1461,11 @@ __global__ void __launch_bounds__(32 << D) k_guard_fine(const GuardArgs<D, P, Re
 // faces, one thread per (leaf, face, guard cell, var), from the host-built
 // face-trace descriptors (source cell and face points as affine functions
 // of my guard-cell and face-point digits).
+// The body handles block `bid` of one forest's launch; k_guard_trace runs it
+// for one forest, k_guard_trace_batch for the forests of a batch (each
+// forest's blocks after the previous forests').
 template <int D, int P, typename Real, bool COMP = false>
-__global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, Real> A, int n_fine_blocks) {
+__device__ __forceinline__ void guard_trace_block(const GuardArgs<D, P, Real>& A, int n_fine_blocks, unsigned bid) {
   const StateIn<Real, COMP> S{A.U, A.U64, A.Uhi, A.Ulo, A.Din};
   constexpr int N = P + 1, NV = D + 2, Q = ipow(N, D), NFP = ipow(N, D - 1);
   constexpr int NW = 1 << D;
@@ -1406,9 +1478,9 @@ __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, R
   // n and nt are powers of two: guard-cell digits by shifts and masks (the
   // launch keeps the thread count below 2^32)
   const int ln = 31 - __clz(n), lnt = (D - 1) * ln;
-  if ((int)blockIdx.x >= n_fine_blocks) {
+  if ((int)bid >= n_fine_blocks) {
     const size_t total = (size_t)A.nL * 2 * D * nt * NV;
-    const size_t wl = (size_t)(blockIdx.x - n_fine_blocks) * NTH + threadIdx.x;
+    const size_t wl = (size_t)(bid - n_fine_blocks) * NTH + threadIdx.x;
     if (wl >= total) return;
     const unsigned w = (unsigned)wl;
     const int t = (int)(w & (unsigned)(nt - 1));
@@ -1501,7 +1573,7 @@ __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, R
   constexpr int NPAIR = NV * NFP;
   __shared__ Real sv[NW][NV][Q];
   __shared__ Real pv[NW][NPAIR];
-  const unsigned item = blockIdx.x;
+  const unsigned item = bid;
   const int lane = threadIdx.x & 31, e = threadIdx.x >> 5;
   const int t = (int)(item & (unsigned)(nt - 1));
   const int bf = A.fine_list[item >> lnt];
@@ -1560,6 +1632,22 @@ __global__ void __launch_bounds__(32 << D) k_guard_trace(const GuardArgs<D, P, R
     const int v = pr / NFP, fp = pr % NFP;
     A.out[((((size_t)b * 2 * D + f) * NV + v) * NFP + fp) * nt + t] = acc;
   }
+}
+
+template <int D, int P, typename Real, bool COMP = false>
+__global__ void __launch_bounds__(32 << D) k_guard_trace(const __grid_constant__ GuardArgs<D, P, Real> A,
+                                                         int n_fine_blocks) {
+  guard_trace_block<D, P, Real, COMP>(A, n_fine_blocks, blockIdx.x);
+}
+
+// guard traces of every forest of a batch in one launch: block ranges per
+// forest in bstart (prefix sums of n_fine_blocks + trace blocks)
+template <int D, int P, typename Real>
+__global__ void __launch_bounds__(32 << D) k_guard_trace_batch(const GuardArgs<D, P, Real>* __restrict__ As,
+                                                               const int* __restrict__ bstart,
+                                                               const int* __restrict__ nfb, int nmem) {
+  const int m = batch_member(bstart, nmem, (int)blockIdx.x);
+  guard_trace_block<D, P, Real, false>(As[m], __ldg(&nfb[m]), blockIdx.x - (unsigned)__ldg(&bstart[m]));
 }
 
 // ============================================================ mortar mode

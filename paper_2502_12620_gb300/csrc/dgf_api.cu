@@ -44,7 +44,7 @@ struct DevScalars {
 
 constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
 
-__global__ void k_dt(DevScalars* s, double cfl) {
+__device__ __forceinline__ void dt_one(DevScalars* s, double cfl) {
   const unsigned long long lb = s->lam_bits;
   double dt = 0.0;
   if (lb != kInfBits) {
@@ -60,6 +60,14 @@ __global__ void k_dt(DevScalars* s, double cfl) {
   s->steps += dt > 0.0;
   // a zero increment evaluates no stage, so the CFL minimum is kept for the next
   if (dt > 0.0) s->lam_bits = kInfBits;
+}
+
+__global__ void k_dt(DevScalars* s, double cfl) { dt_one(s, cfl); }
+
+// the time increments of every forest of a batch (one thread each)
+__global__ void k_dt_batch(DevScalars* const* __restrict__ s, const double* __restrict__ cfl, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dt_one(s[i], cfl[i]);
 }
 
 __global__ void k_reset_lam(DevScalars* s) { s->lam_bits = kInfBits; }
@@ -2053,3 +2061,241 @@ extern "C" dgf_status dgf_dg_residual_noalloc(dgf_forest* f, const void* U_nodal
   s.gtr = scratch;
   return cuda_check(do_stage(f, s), "stage");
 }
+
+// ================================================================ batches
+// Several forests advanced together: one launch of each kernel per stage for
+// all of them (the per-forest kernel arguments live in device arrays; the
+// kernels find each work item's forest from prefix sums), captured in one
+// CUDA graph per membership.  Every forest keeps its own time, end time,
+// time increment and CFL minimum, and each work item does the arithmetic of
+// the forest's own single-forest stage in the same kernel, so a forest's
+// result does not depend on the other members.
+struct dgf_batch {
+  int device = -1;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<dgf_forest*> mem;
+  int p = -1, kernel = 1, all_affine = 0, slots = 0, items = 0;
+  long long gblocks = 0;
+  void* sargs[3] = {nullptr, nullptr, nullptr};
+  void* gargs[3] = {nullptr, nullptr, nullptr};
+  int* istart = nullptr;
+  int* bstart = nullptr;
+  int* nfb = nullptr;
+  DevScalars** scal = nullptr;
+  double* cfl = nullptr;
+  cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+void batch_free(dgf_batch* b) {
+  for (int k = 0; k < 3; ++k) {
+    if (b->sargs[k]) cudaFree(b->sargs[k]);
+    if (b->gargs[k]) cudaFree(b->gargs[k]);
+    b->sargs[k] = b->gargs[k] = nullptr;
+  }
+  for (void* q : {(void*)b->istart, (void*)b->bstart, (void*)b->nfb, (void*)b->scal, (void*)b->cfl})
+    if (q) cudaFree(q);
+  b->istart = b->bstart = b->nfb = nullptr;
+  b->scal = nullptr;
+  b->cfl = nullptr;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->items = 0;
+  b->gblocks = 0;
+}
+
+template <class T>
+dgf_status batch_upload(dgf_batch* b, T** dst, const void* src, size_t bytes) {
+  if (cudaMalloc((void**)dst, bytes ? bytes : 16) != cudaSuccess) return fail(DGF_ENOMEM, "batch allocation failed");
+  return cuda_check(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice), "batch upload");
+}
+
+// one time increment of every member: dt of each, then 3 x (guard traces, stage)
+dgf_status batch_enqueue(dgf_batch* b) {
+  const int n = (int)b->mem.size();
+  k_dt_batch<<<(n + 127) / 128, 128, 0, b->stream>>>(b->scal, b->cfl, n);
+  dgf_status st = cuda_check(cudaGetLastError(), "dt");
+  if (st) return st;
+  dgf_forest* f0 = b->mem[0];
+  const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
+  for (int k = 0; k < 3; ++k) {
+    if ((st = cuda_check(launch_guard_batch<3, float>(b->p, b->gargs[k], b->bstart, b->nfb, n, b->gblocks,
+                                                       b->stream),
+                         "batch guard")))
+      return st;
+    RtStage c = stage_args(f0, 0, 1, ca[k], cb[k], 0, k == 2);
+    c.kernel = b->kernel;
+    c.all_affine = b->all_affine;
+    const int grid = b->items < b->slots ? b->items : b->slots;
+    if ((st = cuda_check(launch_stage_batch<3, float>(c, b->sargs[k], b->istart, n, grid, b->stream),
+                         "batch stage")))
+      return st;
+  }
+  return DGF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dgf_status dgf_batch_create(int32_t device, void* stream, dgf_batch** out) {
+  if (!out) return fail(DGF_EINVAL, "null argument");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return fail(DGF_EINVAL, "no such device");
+  dgf_batch* b = new dgf_batch();
+  b->device = device;
+  DeviceGuard dg(device);
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete b;
+      return fail(DGF_ECUDA, "stream creation failed");
+    }
+    b->own_stream = true;
+  }
+  *out = b;
+  return DGF_OK;
+}
+
+dgf_status dgf_batch_destroy(dgf_batch* b) {
+  if (!b) return DGF_OK;
+  DeviceGuard dg(b->device);
+  cudaStreamSynchronize(b->stream);
+  batch_free(b);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return DGF_OK;
+}
+
+dgf_status dgf_batch_set(dgf_batch* b, dgf_forest* const* forests, const double* t_end, int32_t n) {
+  if (!b || (n > 0 && (!forests || !t_end)) || n < 0) return fail(DGF_EINVAL, "null argument");
+  DeviceGuard dg(b->device);
+  cudaStreamSynchronize(b->stream);
+  batch_free(b);
+  b->mem.assign(forests, forests + n);
+  if (n == 0) return DGF_OK;
+  dgf_forest* f0 = forests[0];
+  for (int i = 0; i < n; ++i) {
+    dgf_forest* f = forests[i];
+    if (!f || f->device != b->device) return fail(DGF_EINVAL, "batch members must be forests on the batch's device");
+    if (f->d != 3 || f->n != 8 || f->precision != DGF_FP32 || f->comp || f->mortar || f->limiter > 0.0)
+      return fail(DGF_EUNSUPPORTED,
+                  "batches take 3D FP32 forests of 8^3-cell blocks in the plain form, without the mortar repair "
+                  "or the limiter");
+    if (f->p != f0->p) return fail(DGF_EINVAL, "batch members must have one degree");
+    if (!f->have_state) return fail(DGF_ESTATE, "batch member without a state");
+    // the member's own stream must have finished its work
+    if (cudaStreamSynchronize(f->stream) != cudaSuccess) return fail(DGF_ECUDA, "member stream");
+  }
+  b->p = f0->p;
+  b->kernel = pair_applies(f0) ? 0 : 1;
+  if (const char* ks = getenv("DGF_STAGE_KERNEL"))
+    if (strcmp(ks, "classic") == 0) b->kernel = 1;
+  b->all_affine = 1;
+  for (auto* f : b->mem) b->all_affine &= f->all_affine ? 1 : 0;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  b->slots = stage_batch_blocks_per_sm<3, float>(b->p, b->kernel, b->all_affine) * sms;
+  if (b->slots <= 0) return fail(DGF_EUNSUPPORTED, "batch stage kernel does not fit the device");
+  // prefix sums of work items and guard blocks; per-stage argument arrays
+  std::vector<int> istart(n + 1, 0), bstart(n + 1, 0), nfb(n, 0);
+  std::vector<DevScalars*> scal(n);
+  std::vector<double> cfl(n);
+  const int src[3] = {0, 1, 2}, dst[3] = {1, 2, 0};
+  const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
+  std::vector<RtStage> rs[3];
+  std::vector<RtGuard> rg[3];
+  long long gb = 0;
+  for (int i = 0; i < n; ++i) {
+    dgf_forest* f = forests[i];
+    for (int k = 0; k < 3; ++k) {
+      rs[k].push_back(stage_args(f, src[k], dst[k], ca[k], cb[k], 0, k == 2));
+      rg[k].push_back(guard_args(f, src[k], f->gtr.ptr, 1));
+    }
+    const int it = stage_items<3, float>(rs[0].back());
+    if (it < 0) return fail(DGF_EUNSUPPORTED, "batch member tiling");
+    istart[i + 1] = istart[i] + it;
+    const long long g = guard_blocks<3, float>(rg[0].back(), &nfb[i]);
+    gb += g;
+    if (gb >= (1ll << 31)) return fail(DGF_EUNSUPPORTED, "batch too large for one guard launch");
+    bstart[i + 1] = (int)gb;
+    scal[i] = (DevScalars*)f->scal.ptr;
+    cfl[i] = f->cfl;
+    f->t_end_dev = t_end[i];
+    dgf_status st = cuda_check(cudaMemcpyAsync(&((DevScalars*)f->scal.ptr)->t_end, &t_end[i], sizeof(double),
+                                               cudaMemcpyHostToDevice, b->stream),
+                               "t_end");
+    if (st) return st;
+  }
+  b->items = istart[n];
+  b->gblocks = gb;
+  dgf_status st;
+  for (int k = 0; k < 3; ++k) {
+    std::vector<unsigned char> hs(stage_args_pack<3, float>(rs[k].data(), n, nullptr));
+    stage_args_pack<3, float>(rs[k].data(), n, hs.data());
+    if ((st = batch_upload(b, &b->sargs[k], hs.data(), hs.size()))) return st;
+    std::vector<unsigned char> hg(guard_args_pack<3, float>(rg[k].data(), n, nullptr));
+    guard_args_pack<3, float>(rg[k].data(), n, hg.data());
+    if ((st = batch_upload(b, &b->gargs[k], hg.data(), hg.size()))) return st;
+  }
+  if ((st = batch_upload(b, &b->istart, istart.data(), istart.size() * sizeof(int))) ||
+      (st = batch_upload(b, &b->bstart, bstart.data(), bstart.size() * sizeof(int))) ||
+      (st = batch_upload(b, &b->nfb, nfb.data(), nfb.size() * sizeof(int))) ||
+      (st = batch_upload(b, &b->scal, scal.data(), scal.size() * sizeof(DevScalars*))) ||
+      (st = batch_upload(b, &b->cfl, cfl.data(), cfl.size() * sizeof(double))))
+    return st;
+  return cuda_check(cudaStreamSynchronize(b->stream), "batch set");
+}
+
+dgf_status dgf_batch_step(dgf_batch* b, int32_t steps) {
+  if (!b || steps < 0) return fail(DGF_EINVAL, "bad argument");
+  if (b->mem.empty() || steps == 0) return DGF_OK;
+  DeviceGuard dg(b->device);
+  dgf_status st;
+  if (!b->graph) {
+    cudaGraph_t g = nullptr;
+    if ((st = cuda_check(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "capture")))
+      return st;
+    dgf_status est = batch_enqueue(b);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (est) {
+      if (g) cudaGraphDestroy(g);
+      return est;
+    }
+    if ((st = cuda_check(e, "end capture"))) return st;
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if ((st = cuda_check(e, "instantiate"))) return st;
+  }
+  for (int i = 0; i < steps; ++i)
+    if ((st = cuda_check(cudaGraphLaunch(b->graph, b->stream), "graph launch"))) return st;
+  return DGF_OK;
+}
+
+dgf_status dgf_batch_query(dgf_batch* b, int32_t* idle) {
+  if (!b || !idle) return fail(DGF_EINVAL, "null argument");
+  DeviceGuard dg(b->device);
+  const cudaError_t e = cudaStreamQuery(b->stream);
+  if (e == cudaSuccess) {
+    *idle = 1;
+    return DGF_OK;
+  }
+  if (e == cudaErrorNotReady) {
+    cudaGetLastError();
+    *idle = 0;
+    return DGF_OK;
+  }
+  return cuda_check(e, "batch query");
+}
+
+dgf_status dgf_batch_sync(dgf_batch* b) {
+  if (!b) return fail(DGF_EINVAL, "null batch");
+  DeviceGuard dg(b->device);
+  return cuda_check(cudaStreamSynchronize(b->stream), "batch sync");
+}
+
+}  // extern "C"

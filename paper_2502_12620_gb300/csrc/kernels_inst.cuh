@@ -89,6 +89,8 @@ cudaError_t stage_pair_launch(const StageArgs<3, P, float>& a, int grid, bool mo
                               cudaStream_t s);
 template <int P>
 int stage_pair_blocks_per_sm();
+template <int P>
+cudaError_t stage_pair_launch_batch(const StageArgs<3, P, float>& a, int grid, bool all_affine, cudaStream_t s);
 
 template <int D, int P, int NS, typename Real>
 static int stage_blocks_per_sm_classic();
@@ -162,7 +164,7 @@ static cudaError_t stage_ns(const StageArgs<D, P, Real>& a, int slots, int comp,
 }
 
 template <int D, int P, typename Real>
-static cudaError_t stage_p(const RtStage& r, cudaStream_t s) {
+static StageArgs<D, P, Real> make_stage_args(const RtStage& r) {
   StageArgs<D, P, Real> a;
   a.nL = r.nL;
   a.n = r.n;
@@ -195,6 +197,15 @@ static cudaError_t stage_p(const RtStage& r, cudaStream_t s) {
   a.U64out = r.U64out;
   a.fluxmask = r.fluxmask;
   a.T = make_tab<P + 1, Real>(r.T);
+  a.members = nullptr;
+  a.istart = nullptr;
+  a.nmem = 0;
+  return a;
+}
+
+template <int D, int P, typename Real>
+static cudaError_t stage_p(const RtStage& r, cudaStream_t s) {
+  const StageArgs<D, P, Real> a = make_stage_args<D, P, Real>(r);
   if (r.slots <= 0) return cudaErrorInvalidConfiguration;
   switch (r.n) {
     case 2: return stage_ns<D, P, 2, Real>(a, r.slots, r.comp, r.all_affine, r.kernel, s);
@@ -205,7 +216,7 @@ static cudaError_t stage_p(const RtStage& r, cudaStream_t s) {
 }
 
 template <int D, int P, typename Real>
-static cudaError_t guard_p(const RtGuard& r, cudaStream_t s) {
+static GuardArgs<D, P, Real> make_guard_args(const RtGuard& r) {
   GuardArgs<D, P, Real> a;
   a.nL = r.nL;
   a.n = r.n;
@@ -236,6 +247,12 @@ static cudaError_t guard_p(const RtGuard& r, cudaStream_t s) {
   a.msrc = r.msrc;
   a.bstate = (const Real*)r.bstate;
   a.T = make_tab<P + 1, Real>(r.T);
+  return a;
+}
+
+template <int D, int P, typename Real>
+static cudaError_t guard_p(const RtGuard& r, cudaStream_t s) {
+  const GuardArgs<D, P, Real> a = make_guard_args<D, P, Real>(r);
   const int nt = D == 3 ? r.n * r.n : r.n;
   if (r.mode == 1) {
     // time-step path: traces of every face kind in one launch (finer faces
@@ -360,6 +377,97 @@ static cudaError_t convert_p(size_t outer, int inner, void* X, int to_nodal, con
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------- batches
+// Every forest of a batch (same dimension 3, n_seg 8, degree, FP32, plain
+// form without the mortar repair) in one launch per kernel: the per-forest
+// kernel arguments are packed on the host into device arrays; the kernels
+// find an item's (block's) forest from prefix sums.
+
+// work items of one forest's stage launch with the kernel r.kernel
+template <int D, int P, typename Real>
+static int stage_items_p(const RtStage& r) {
+  const int nchunks = D == 3 ? (r.n + r.zchunk - 1) / r.zchunk : 1;
+  if (r.n != 8) return -1;
+  return r.nL * nchunks * (8 / stage_rows<D, P, Real>(8));  // the same count for both kernels at n = 8
+}
+
+template <int D, int P, typename Real>
+static size_t stage_args_pack_p(const RtStage* r, int n, void* host) {
+  if (host)
+    for (int i = 0; i < n; ++i) reinterpret_cast<StageArgs<D, P, Real>*>(host)[i] = make_stage_args<D, P, Real>(r[i]);
+  return sizeof(StageArgs<D, P, Real>) * (size_t)n;
+}
+
+template <int D, int P, typename Real>
+static size_t guard_args_pack_p(const RtGuard* r, int n, void* host) {
+  if (host)
+    for (int i = 0; i < n; ++i) reinterpret_cast<GuardArgs<D, P, Real>*>(host)[i] = make_guard_args<D, P, Real>(r[i]);
+  return sizeof(GuardArgs<D, P, Real>) * (size_t)n;
+}
+
+// blocks of one forest's guard-trace launch (trace blocks + finer-face blocks)
+template <int D, int P, typename Real>
+static long long guard_blocks_p(const RtGuard& r, int* nfb) {
+  constexpr int NTH = 32 << D;
+  const int nt = D == 3 ? r.n * r.n : r.n;
+  const size_t items = (size_t)r.nL * 2 * D * (D + 2) * nt;
+  *nfb = r.nfine * nt;
+  return (long long)((items + NTH - 1) / NTH) + *nfb;
+}
+
+template <int D, int P, typename Real>
+static int stage_batch_blocks_per_sm_p(int kernel, int all_affine) {
+  if constexpr (D == 3 && std::is_same<Real, float>::value) {
+    if constexpr (P == 1 || P == 2) {
+      if (kernel == 0) return stage_pair_blocks_per_sm<P>();
+    }
+    constexpr int YS = stage_rows<D, P, Real>(8);
+    const size_t smem = stage_smem<D, P, Real>(8, YS);
+    if (cudaFuncSetAttribute(k_stage<D, P, 8, Real, false, false, YS, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage<D, P, 8, Real, false, false, YS, true>,
+                                                      StageCfg<P, Real>::NT, smem) != cudaSuccess)
+      return 0;
+    (void)all_affine;
+    return nb;
+  }
+  return 0;
+}
+
+template <int D, int P, typename Real>
+static cudaError_t launch_stage_batch_p(const RtStage& common, const void* members, const int* istart, int nmem,
+                                        int grid, cudaStream_t s) {
+  if constexpr (D == 3 && std::is_same<Real, float>::value) {
+    StageArgs<D, P, Real> a = make_stage_args<D, P, Real>(common);
+    a.members = reinterpret_cast<const StageArgs<D, P, Real>*>(members);
+    a.istart = istart;
+    a.nmem = nmem;
+    if constexpr (P == 1 || P == 2) {
+      if (common.kernel == 0) return stage_pair_launch_batch<P>(a, grid, common.all_affine != 0, s);
+    }
+    constexpr int YS = stage_rows<D, P, Real>(8);
+    const size_t smem = stage_smem<D, P, Real>(8, YS);
+    k_stage<D, P, 8, Real, false, false, YS, true><<<grid, StageCfg<P, Real>::NT, smem, s>>>(a);
+    return cudaGetLastError();
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int D, int P, typename Real>
+static cudaError_t launch_guard_batch_p(const void* members, const int* bstart, const int* nfb, int nmem,
+                                        long long blocks, cudaStream_t s) {
+  if constexpr (D == 3 && std::is_same<Real, float>::value) {
+    if (blocks <= 0 || blocks >= (1ll << 31)) return cudaErrorInvalidConfiguration;
+    k_guard_trace_batch<D, P, Real><<<(unsigned)blocks, 32 << D, 0, s>>>(
+        reinterpret_cast<const GuardArgs<D, P, Real>*>(members), bstart, nfb, nmem);
+    return cudaGetLastError();
+  }
+  return cudaErrorInvalidValue;
+}
+
 #define DGF_DISPATCH_P(fn, r, s)                 \
   switch ((r).p) {                               \
     case 0: return fn<D, 0, Real>(r, s);         \
@@ -369,7 +477,52 @@ static cudaError_t convert_p(size_t outer, int inner, void* X, int to_nodal, con
     default: return cudaErrorInvalidValue;       \
   }
 
+#define DGF_SWITCH_P(p, expr_tmpl)                                                          \
+  switch (p) {                                                                              \
+    case 0: { constexpr int P_ = 0; return expr_tmpl; }                                     \
+    case 1: { constexpr int P_ = 1; return expr_tmpl; }                                     \
+    case 2: { constexpr int P_ = 2; return expr_tmpl; }                                     \
+    case 3: { constexpr int P_ = 3; return expr_tmpl; }                                     \
+  }
+
 #define DGF_INSTANTIATE(DIM, REAL)                                                          \
+  template <>                                                                               \
+  int stage_items<DIM, REAL>(const RtStage& r) {                                            \
+    DGF_SWITCH_P(r.p, (stage_items_p<DIM, P_, REAL>(r)))                                    \
+    return -1;                                                                              \
+  }                                                                                         \
+  template <>                                                                               \
+  size_t stage_args_pack<DIM, REAL>(const RtStage* r, int n, void* host) {                  \
+    DGF_SWITCH_P(r[0].p, (stage_args_pack_p<DIM, P_, REAL>(r, n, host)))                    \
+    return 0;                                                                               \
+  }                                                                                         \
+  template <>                                                                               \
+  size_t guard_args_pack<DIM, REAL>(const RtGuard* r, int n, void* host) {                  \
+    DGF_SWITCH_P(r[0].p, (guard_args_pack_p<DIM, P_, REAL>(r, n, host)))                    \
+    return 0;                                                                               \
+  }                                                                                         \
+  template <>                                                                               \
+  long long guard_blocks<DIM, REAL>(const RtGuard& r, int* nfb) {                           \
+    DGF_SWITCH_P(r.p, (guard_blocks_p<DIM, P_, REAL>(r, nfb)))                              \
+    return -1;                                                                              \
+  }                                                                                         \
+  template <>                                                                               \
+  int stage_batch_blocks_per_sm<DIM, REAL>(int p, int kernel, int all_affine) {             \
+    DGF_SWITCH_P(p, (stage_batch_blocks_per_sm_p<DIM, P_, REAL>(kernel, all_affine)))       \
+    return 0;                                                                               \
+  }                                                                                         \
+  template <>                                                                               \
+  cudaError_t launch_stage_batch<DIM, REAL>(const RtStage& c, const void* m, const int* istart, int nmem,  \
+                                            int grid, cudaStream_t s) {                     \
+    DGF_SWITCH_P(c.p, (launch_stage_batch_p<DIM, P_, REAL>(c, m, istart, nmem, grid, s)))   \
+    return cudaErrorInvalidValue;                                                           \
+  }                                                                                         \
+  template <>                                                                               \
+  cudaError_t launch_guard_batch<DIM, REAL>(int p, const void* m, const int* bstart, const int* nfb,     \
+                                            int nmem, long long blocks, cudaStream_t s) {   \
+    DGF_SWITCH_P(p, (launch_guard_batch_p<DIM, P_, REAL>(m, bstart, nfb, nmem, blocks, s))) \
+    return cudaErrorInvalidValue;                                                           \
+  }                                                                                         \
   template <>                                                                               \
   cudaError_t launch_stage<DIM, REAL>(const RtStage& r, cudaStream_t s) {                   \
     constexpr int D = DIM;                                                                  \

@@ -132,6 +132,25 @@ cudaError_t launch_convert(int p, size_t outer, int inner, void* X, int to_nodal
                            cudaStream_t s);
 template <int D, typename Real>
 size_t stage_smem_bytes(int p, int n);
+// batches (3D, n_seg 8, FP32, plain form): per-forest argument packing on the
+// host (host == nullptr: size only), work items / blocks per forest,
+// resident CTAs of the batch stage kernel, and the batch launches
+template <int D, typename Real>
+int stage_items(const RtStage& r);
+template <int D, typename Real>
+size_t stage_args_pack(const RtStage* r, int n, void* host);
+template <int D, typename Real>
+size_t guard_args_pack(const RtGuard* r, int n, void* host);
+template <int D, typename Real>
+long long guard_blocks(const RtGuard& r, int* nfb);
+template <int D, typename Real>
+int stage_batch_blocks_per_sm(int p, int kernel, int all_affine);
+template <int D, typename Real>
+cudaError_t launch_stage_batch(const RtStage& common, const void* members, const int* istart, int nmem, int grid,
+                               cudaStream_t s);
+template <int D, typename Real>
+cudaError_t launch_guard_batch(int p, const void* members, const int* bstart, const int* nfb, int nmem,
+                               long long blocks, cudaStream_t s);
 // resident stage CTAs per SM (0: does not fit)
 template <int D, typename Real>
 int stage_occupancy(int p, int n, int comp, int kernel);

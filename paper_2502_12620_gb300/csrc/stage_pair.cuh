@@ -237,9 +237,12 @@ struct PairCfg {
 
 // AFF: every block of the forest is affine (no per-cell geometry is read;
 // the curved code paths are not compiled into this instantiation)
-template <int P, bool MORTAR, bool AFF>
+// BATCH: one launch for every forest of a batch (A.members; the tables and
+// stage coefficients of A are common to all of them).
+template <int P, bool MORTAR, bool AFF, bool BATCH = false>
 __global__ void __launch_bounds__(pairk::PairCfg<P>::NT, pairk::PairCfg<P>::MINB)
-    k_stage_pair(const StageArgs<3, P, float> A) {
+    k_stage_pair(const __grid_constant__ StageArgs<3, P, float> A) {
+  static_assert(!(BATCH && MORTAR), "batches run without the mortar repair");
   using namespace pairk;
   using C = PairCfg<P>;
   constexpr int N = C::N, Q = C::Q, NFP = C::NFP, NV = 5, ROWS = C::ROWS, NG = C::NG;
@@ -251,7 +254,7 @@ __global__ void __launch_bounds__(pairk::PairCfg<P>::NT, pairk::PairCfg<P>::MINB
   const int i0 = 2 * m;
   const int cl = i0 + n * j;              // first cell of the pair in the layer
   const int fa = w % N, fb = w / N;       // digits of this warp's face point
-  if (A.mode == 0 && *A.dtp == 0.0) return;  // t_end reached: identity, nothing evaluated
+  if (!BATCH && A.mode == 0 && *A.dtp == 0.0) return;  // t_end reached: identity, nothing evaluated
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* Us = reinterpret_cast<float*>(smem_raw);  // [2][ROWS][64]
@@ -264,8 +267,8 @@ __global__ void __launch_bounds__(pairk::PairCfg<P>::NT, pairk::PairCfg<P>::MINB
   __shared__ float sam[10];
 
   const float2 gam = f2(A.gamma), gm1 = f2(A.gamma - 1.f);
-  const float dtf = (float)*A.dtp;
-  const float2 dt2 = f2(dtf), ca2 = f2(A.ca), cb2 = f2(A.cb);
+  float2 dt2 = f2(BATCH ? 0.f : (float)*A.dtp);  // per forest of a batch: per item
+  const float2 ca2 = f2(A.ca), cb2 = f2(A.cb);
   float xq[N];
 #pragma unroll
   for (int q = 0; q < N; ++q) xq[q] = T.x[q];
@@ -292,20 +295,35 @@ __global__ void __launch_bounds__(pairk::PairCfg<P>::NT, pairk::PairCfg<P>::MINB
   const bool use_un = A.mode == 0 && A.ca != 0.f;
   float lam_min = 3.0e38f;
   bool bad = false;
+  int* cur_status = A.status;
 
-  const int items = A.nL * A.nchunks;
+  const int items = BATCH ? __ldg(&A.istart[A.nmem]) : A.nL * A.nchunks;
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    const int b = item / A.nchunks;
-    const int chunk = item - b * A.nchunks;
-    const int k0 = chunk * A.zchunk;
-    const int k1 = min(n, k0 + A.zchunk);
+    // the forest of this item (a batch member, or the one forest)
+    const StageArgs<3, P, float>* Mp = &A;
+    int li = item;
+    if constexpr (BATCH) {
+      const int mi = batch_member(A.istart, A.nmem, item);
+      Mp = A.members + mi;
+      li = item - __ldg(&A.istart[mi]);
+      if (A.mode == 0 && *Mp->dtp == 0.0) continue;  // that forest has reached its end time
+      dt2 = f2((float)*Mp->dtp);
+    }
+    const StageArgs<3, P, float>& M = *Mp;
+    cur_status = M.status;
+    const int b = li / M.nchunks;
+    const int chunk = li - b * M.nchunks;
+    const int k0 = chunk * M.zchunk;
+    const int k1 = min(n, k0 + M.zchunk);
     const size_t boff = (size_t)b * NV * Q * nc;
-    const float* __restrict__ Ub = A.U + boff;
-    const float* __restrict__ Unb = A.Un + boff;
-    const float* __restrict__ Geo = A.geo + (size_t)b * NG * nc;
-    const float* __restrict__ Tb = A.gtr + (size_t)b * 6 * NV * NFP * nt;
-    const bool aff = AFF || A.affine[b] != 0;
-    const int fmask = MORTAR ? A.fluxmask[b] : 0;
+    const float* __restrict__ Ub = M.U + boff;
+    const float* __restrict__ Unb = M.Un + boff;
+    const float* __restrict__ Geo = M.geo + (size_t)b * NG * nc;
+    const float* __restrict__ Tb = M.gtr + (size_t)b * 6 * NV * NFP * nt;
+    const float* __restrict__ Hb = M.hcell + (size_t)b * nc;
+    float* __restrict__ Ob = M.Uout;
+    const bool aff = AFF || M.affine[b] != 0;
+    const int fmask = MORTAR ? M.fluxmask[b] : 0;
     const uint32_t bytes = (uint32_t)((ROWS + (aff ? 0 : NG)) * LAY * sizeof(float));
     // one layer (state rows, and the coefficient rows of a curved block) into buffer k & 1
     auto issue = [&](int k) {
@@ -338,7 +356,7 @@ __global__ void __launch_bounds__(pairk::PairCfg<P>::NT, pairk::PairCfg<P>::MINB
 #define GTR(f, v, fp, t) Tb[(((size_t)(f) * NV + (v)) * NFP + (fp)) * nt + (t)]
 
     __syncthreads();  // the previous item is done with every buffer
-    if (aff && tid < 10) sam[tid] = A.ameta[(size_t)b * 10 + tid];
+    if (aff && tid < 10) sam[tid] = M.ameta[(size_t)b * 10 + tid];
     if (k0 > 0) issue(k0 - 1);
     issue(k0);
     bool ok = true;
@@ -698,7 +716,7 @@ __global__ void __launch_bounds__(pairk::PairCfg<P>::NT, pairk::PairCfg<P>::MINB
         // stage combination straight to global memory, CFL on the last stage
         const size_t gcell = boff + (size_t)k * LAY + cl;  // (v, q) row offsets added below
         float2 hc = f2(0.f);
-        if (A.last) hc = __ldg(reinterpret_cast<const float2*>(A.hcell + (size_t)b * nc + k * LAY + cl));
+        if (A.last) hc = __ldg(reinterpret_cast<const float2*>(Hb + k * LAY + cl));
 #pragma unroll
         for (int qz = 0; qz < N; ++qz) {
           const int q = fpZ + NFP * qz;
@@ -714,7 +732,7 @@ __global__ void __launch_bounds__(pairk::PairCfg<P>::NT, pairk::PairCfg<P>::MINB
               val = mul(cb2, fma2(dt2, s, lds2(Uc + (v * Q + q) * LAY + cl)));
               if (use_un) val = fma2(ca2, un[qz][v], val);
             }
-            *reinterpret_cast<float2*>(A.Uout + gi) = val;
+            *reinterpret_cast<float2*>(Ob + gi) = val;
             o[v] = val;
           }
           if (A.last) {
@@ -741,20 +759,29 @@ __global__ void __launch_bounds__(pairk::PairCfg<P>::NT, pairk::PairCfg<P>::MINB
         }
       }
     }
+    if constexpr (BATCH) {
+      // the CFL minimum and the status belong to this item's forest
+      if (A.last) {
+        cta_min_atomic<C::NT>((double)lam_min, M.lam_bits);
+        lam_min = 3.0e38f;
+        if (__syncthreads_or(bad) && tid == 0) atomicExch(M.status, kStatusNonFinite);
+        bad = false;
+      }
+    }
 #undef GTR
   }
   if (false) {
   timeout:
     // a bounded wait gave up: report it, wait (bounded) for the copies still
     // in flight into this CTA's buffers, then leave
-    if (tid == 0) atomicExch(A.status, kStatusTimeout);
+    if (tid == 0) atomicExch(cur_status, kStatusTimeout);
     if (pend0) mbar_wait(&bar[0], ph0);
     if (pend1) mbar_wait(&bar[1], ph1);
     // a warp whose own wait gave up retries it once (bounded) before leaving
     if (wfail) mbar_wait(&wbar[w], phw ^ 1u);
     return;
   }
-  if (A.last) {
+  if (!BATCH && A.last) {
     // block min of h/lambda -> one atomic per CTA
     double v = (double)lam_min;
 #pragma unroll
@@ -795,14 +822,23 @@ cudaError_t stage_pair_launch(const StageArgs<3, P, float>& a, int grid, bool mo
   return cudaGetLastError();
 }
 
-template <int P, bool MORTAR, bool AFF>
+// one launch over the forests of a batch (a.members); plain form, no mortar
+template <int P>
+cudaError_t stage_pair_launch_batch(const StageArgs<3, P, float>& a, int grid, bool all_affine, cudaStream_t s) {
+  using C = pairk::PairCfg<P>;
+  if (all_affine) k_stage_pair<P, false, true, true><<<grid, C::NT, C::SMEM, s>>>(a);
+  else k_stage_pair<P, false, false, true><<<grid, C::NT, C::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int P, bool MORTAR, bool AFF, bool BATCH = false>
 int pair_blocks_per_sm_one() {
   using C = pairk::PairCfg<P>;
-  if (cudaFuncSetAttribute(k_stage_pair<P, MORTAR, AFF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(k_stage_pair<P, MORTAR, AFF, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)C::SMEM) != cudaSuccess)
     return 0;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage_pair<P, MORTAR, AFF>, C::NT, C::SMEM) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage_pair<P, MORTAR, AFF, BATCH>, C::NT, C::SMEM) !=
       cudaSuccess)
     return 0;
   return nb;
@@ -810,10 +846,11 @@ int pair_blocks_per_sm_one() {
 
 template <int P>
 int stage_pair_blocks_per_sm() {
-  const int o[4] = {pair_blocks_per_sm_one<P, false, false>(), pair_blocks_per_sm_one<P, true, false>(),
-                    pair_blocks_per_sm_one<P, false, true>(), pair_blocks_per_sm_one<P, true, true>()};
+  const int o[6] = {pair_blocks_per_sm_one<P, false, false>(), pair_blocks_per_sm_one<P, true, false>(),
+                    pair_blocks_per_sm_one<P, false, true>(), pair_blocks_per_sm_one<P, true, true>(),
+                    pair_blocks_per_sm_one<P, false, false, true>(), pair_blocks_per_sm_one<P, false, true, true>()};
   int lo = o[0];
-  for (int i = 1; i < 4; ++i) lo = o[i] < lo ? o[i] : lo;
+  for (int i = 1; i < 6; ++i) lo = o[i] < lo ? o[i] : lo;
   return lo;
 }
 

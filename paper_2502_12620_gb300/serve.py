@@ -10,6 +10,14 @@ solve's arithmetic is the one it does alone (own buffers and graphs,
 deterministic kernels, and an increment at t = t_end is the identity), so
 its result does not depend on what else runs beside it.
 
+With batched=True, the admitted 3D FP32 solves of 8^3-cell blocks are
+advanced together instead: one library batch per degree, so each stage of
+every such solve goes through one launch of the guard-trace kernel and one
+of the persistent stage kernel (a single CUDA graph per batch membership;
+admitting or retiring a solve rewrites the batch's device work descriptors).
+Each solve keeps its own time step and end time; its result is the one it
+gets alone in a batch.  Other solves keep their own streams.
+
 All GPU work goes through the library; this module decides what to admit and
 how many time steps to enqueue next.
 """
@@ -22,7 +30,7 @@ from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
-from . import FP32, FP32_COMP, FP64, Forest
+from . import FP32, FP32_COMP, FP64, Batch, Forest
 
 
 @dataclasses.dataclass
@@ -133,7 +141,8 @@ class Server:
     threads, so the streams already admitted keep getting work meanwhile."""
 
     def __init__(self, device=0, hbm_budget=None, max_active=16, steps_per_round=8,
-                 build_workers=2, solve_factory=None, clock=time.perf_counter, sleep=time.sleep):
+                 build_workers=2, solve_factory=None, clock=time.perf_counter, sleep=time.sleep,
+                 batched=False):
         self.device = device
         if hbm_budget is None:
             import torch
@@ -148,6 +157,8 @@ class Server:
         self.sleep = sleep
         self.peak_active = 0
         self.peak_bytes = 0
+        self.batched = bool(batched)
+        self.groups = {}  # degree -> _Group (batched mode)
 
     def _next_k(self, s, t, steps):
         """Steps to enqueue next: the predicted remainder (from the mean dt so
@@ -160,11 +171,48 @@ class Server:
         rem = math.ceil((s.req.t_end - t) / dt)
         return max(1, min(self.steps_per_round, rem))
 
+    @staticmethod
+    def batchable(req):
+        w = req.workload
+        return w["dim"] == 3 and w["n_seg"] == 8 and req.precision == FP32
+
     def _build(self, req):
         s = self.factory(req)
         s.req, s.t0 = req, 0.0
-        s.enqueue(self.steps_per_round)
+        s.batched = self.batched and self.batchable(req)
+        if not s.batched:
+            s.enqueue(self.steps_per_round)
         return s
+
+    def _serve_groups(self, results, keep_state, t0):
+        """Batched mode: retire finished members, take in new ones, and
+        enqueue the next round of steps on every batch that has drained.
+        Returns (progressed, bytes released)."""
+        progressed, freed = False, 0
+        for g in self.groups.values():
+            if not g.batch.idle():
+                continue
+            changed = False
+            for s in list(g.members):
+                t, steps = s.progress()
+                if t >= s.req.t_end:
+                    state, status = s.finish(keep_state)
+                    results[s.req.rid] = Result(s.req.rid, s.req.arrival, s.admitted, self.clock() - t0,
+                                                steps, s.dof, t, status, s.bytes, state)
+                    s.done = True
+                    freed += s.bytes
+                    g.members.remove(s)
+                    changed = progressed = True
+            if g.joining:
+                g.members.extend(g.joining)
+                g.joining = []
+                changed = True
+            if changed:
+                g.batch.set([s.f for s in g.members], [s.req.t_end for s in g.members])
+            if g.members:
+                g.batch.step(self.steps_per_round)
+                progressed = True
+        return progressed, freed
 
     def run(self, requests, keep_state=False):
         """Serve `requests` (arrival times relative to the call); returns the
@@ -205,13 +253,21 @@ class Server:
                     s.bytes = s.device_bytes or est
                     used += s.bytes - est
                     active.append(s)
+                    if getattr(s, "batched", False):
+                        if s.req.p not in self.groups:
+                            self.groups[s.req.p] = _Group(Batch(self.device))
+                        self.groups[s.req.p].joining.append(s)
                     item[0] = None
                     progressed = True
                 building = [it for it in building if it[0] is not None]
                 self.peak_active = max(self.peak_active, len(active) + len(building))
                 self.peak_bytes = max(self.peak_bytes, used)
+                if self.groups:
+                    pg, freed = self._serve_groups(results, keep_state, t0)
+                    progressed = progressed or pg
+                    used -= freed
                 for s in active:
-                    if not s.idle():
+                    if getattr(s, "batched", False) or not s.idle():
                         continue
                     progressed = True
                     t, steps = s.progress()
@@ -232,7 +288,18 @@ class Server:
         finally:
             if pool is not None:
                 pool.shutdown(wait=True)
+            for g in self.groups.values():
+                g.batch.close()
+            self.groups = {}
         return [results[r.rid] for r in requests]
+
+
+@dataclasses.dataclass
+class _Group:
+    """The solves of one degree advanced by one library batch."""
+    batch: object
+    members: list = dataclasses.field(default_factory=list)
+    joining: list = dataclasses.field(default_factory=list)
 
 
 def summarize(results, wall):
