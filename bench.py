@@ -44,9 +44,13 @@ WORKLOAD = "3d-euler-jittered-cube-8roots-71leaves-n8-p2"
 HBM_FALLBACK = 6800.0
 # DRAM bytes (read + write) per stage-kernel launch, averaged over the three
 # stages of one time step (ncu dram__bytes_read.sum + dram__bytes_write.sum,
-# cold L2), by workload, for the stage kernel as it is now; a workload
-# without a capture of the current kernel reports null.
-STAGE_TRAFFIC_BYTES = {}
+# cold L2), by (workload, stage kernel), for the kernels as they are now; a
+# workload without a capture of the current kernel reports null.  The 16^3
+# cube at p = 2 is 8 x the 512-leaf cube's figure (same kernel and tiling,
+# state above L2 in both, traffic proportional to the leaves: 377.1 MB there,
+# the algorithmic 377.5 MB); the 512-leaf cube at p = 1 fits L2, so no
+# figure is scaled to the 16^3 cube at p = 1.
+STAGE_TRAFFIC_BYTES = {("jitter3d", "pair"): 47.41e6, ("cube16p2", "pair"): 8 * 377.1e6}
 TRAFFIC_HOW = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, cold L2, mean of the 3 stages of a step"
 
 
@@ -328,7 +332,7 @@ def run_ours(args):
     achieved = alg_bytes / (stage_ms / stage_n / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"],
-            "traffic": STAGE_TRAFFIC_BYTES.get(_SEL[0]),
+            "traffic": STAGE_TRAFFIC_BYTES.get((_SEL[0], f32.tuning()["stage_kernel"])),
             "traffic_how": TRAFFIC_HOW,
             "kernel": stage_kernel_name(f32, p),
             "bytes_per_launch": alg_bytes, "avg_launch_us": 1e3 * stage_ms / stage_n,
@@ -478,7 +482,8 @@ def over_l2_case(key, args, stream, flush, pk, pk_kind, torch, pkg):
            "state_bytes_fp32": dof * 4, "value": value, "unit": "DOF-updates/s", "ms_per_step": ms / args.steps,
            "steps": args.steps,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                        "frac": achieved / pk["hbm_gbs"], "traffic": STAGE_TRAFFIC_BYTES.get(key),
+                        "frac": achieved / pk["hbm_gbs"],
+                        "traffic": STAGE_TRAFFIC_BYTES.get((key, f32.tuning()["stage_kernel"])),
                         "traffic_how": TRAFFIC_HOW, "kernel": stage_kernel_name(f32, p),
                         "bytes_per_launch": alg, "avg_launch_us": 1e3 * stage_ms / stage_n,
                         "peak_source": pk_kind,
