@@ -499,15 +499,20 @@ def over_l2_case(key, args, stream, flush, pk, pk_kind, torch, pkg):
 
 
 # ---------------------------------------------------------------- serving
-SERVE_MIX = dict(rate=20.0, seed=0, blocks=(64, 512), degrees=(1, 2, 3), t_end=(0.05, 0.5), t_scale=0.1)
+# the serving mix of the bench line: SURVEY's block range and arrival rate,
+# end times scaled by 0.01 so that the run takes seconds; --serve-full runs
+# 256 requests with end times scaled by 0.1
+SERVE_MIX = dict(rate=20.0, seed=0, blocks=(64, 8192), degrees=(1, 2, 3), t_end=(0.05, 0.5), t_scale=0.01)
 
 
 def run_serve(args, sub=False):
     """Continuous batching: Poisson arrivals of independent solves (blast or
-    vortex, periodic cubes of 64-512 blocks, p in 1..3, FP32), each admitted
-    by its device footprint, built on a worker thread (forest, upload of its
-    initial values, projection on the device) and advanced on its own stream.  Reports the aggregate
-    DOF-update rate over the whole run and p50/p99 time to solution."""
+    vortex, periodic cubes of 64-8192 blocks, p in 1..3, FP32), each admitted
+    by its device footprint, built on a worker thread (forest, initial values
+    computed on the GPU at its Gauss points) and advanced in the batch of its
+    degree (or on its own stream with --serve-streams).  Reports the
+    aggregate DOF-update rate over the whole run and p50/p99 time to
+    solution."""
     import torch
     import paper_2502_12620_gb300 as pkg
     from paper_2502_12620_gb300 import serve
@@ -517,36 +522,15 @@ def run_serve(args, sub=False):
         import torch.distributed as dist
         dist.init_process_group("gloo")
     torch.cuda.set_device(local)
-    mix = W.serving_mix(args.serve_sub_requests if sub else args.serve_requests, **SERVE_MIX)
-    # request payloads, made before the run: each solve's initial values at its
-    # quadrature points (the vortex payload is shared by requests of one shape)
-    t_prep = time.perf_counter()
-    qp, vort = {}, {}
-    for m in mix:
-        key = (m["B"], m["p"])
-        if key not in qp:
-            h = pkg.Forest.from_workload(W.periodic_cube_forest(m["B"], n_seg=m["n_seg"]), p=m["p"], device=-1)
-            qp[key] = h.quad_points()
-            h.close()
-
-    def payload(m):
-        key = (m["B"], m["p"])
-        if m["kind"] == "vortex":
-            if key not in vort:
-                vort[key] = W.serving_initial(m)(qp[key])
-            return vort[key]
-        return W.serving_initial(m)(qp[key])
-
-    from concurrent.futures import ThreadPoolExecutor
-    for m in mix:  # vortex payloads first, once per shape
-        if m["kind"] == "vortex":
-            payload(m)
-    with ThreadPoolExecutor(8) as ex:
-        vals = list(ex.map(payload, mix))
-    qp.clear()
-    t_prep = time.perf_counter() - t_prep
+    dev = torch.device("cuda", local)
+    mix_cfg = dict(SERVE_MIX)
+    n_req = args.serve_sub_requests if sub else args.serve_requests
+    if args.serve_full and not sub:
+        n_req, mix_cfg["t_scale"] = 256, 0.1
+    mix = W.serving_mix(n_req, **mix_cfg)
+    t_prep = 0.0
     reqs = [serve.Request(m["rid"], m["arrival"], W.periodic_cube_forest(m["B"], n_seg=m["n_seg"]), m["p"],
-                          m["t_end"], ("nodal", v), pkg.FP32) for m, v in zip(mix, vals)]
+                          m["t_end"], ("device", serving_device_init(m, torch, dev)), pkg.FP32) for m in mix]
     # warm-up: one small solve of every degree (module load, allocator pool)
     warm = [serve.Request(-1 - p, 0.0, W.periodic_cube_forest(2), p, 1e-3, W.smooth_state, pkg.FP32)
             for p in SERVE_MIX["degrees"]]
@@ -558,26 +542,31 @@ def run_serve(args, sub=False):
     torch.cuda.synchronize()
     with Clocks(local) as ck:
         t0 = time.perf_counter()
-        res = srv.run(reqs)
+        res = srv.run(reqs, deadline=args.serve_deadline)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-    sm = serve.summarize(res, wall)
+    done = [r for r in res if r.status == 0]
+    sm = serve.summarize(done or res, wall)
     updates = sum(r.dof * 3 * r.steps for r in res)
     if sub:
-        out = {"workload": "serving-mix-periodic-cubes-64-512-blocks-n8-p1-3-blast-or-vortex",
+        out = {"workload": "serving-mix-periodic-cubes-64-8192-blocks-n8-p1-3-blast-or-vortex",
                "requests": len(res), "value": updates / wall, "unit": "DOF-updates/s",
                "p50_s": sm["p50_s"], "p99_s": sm["p99_s"], "wall_s": wall, "max_active": args.serve_active,
                "mode": "batched: one launch per kernel and stage for the solves of one degree" if batched
                else "one stream and graph per solve",
-               "failed": sum(1 for r in res if r.status != 0), "peak_active": srv.peak_active,
+               "failed": sum(1 for r in res if r.status not in (0, -100, -101)),
+               "unfinished_at_deadline": sum(1 for r in res if r.status in (-100, -101)),
+               "failed_requests": [dict(rid=m["rid"], B=m["B"], p=m["p"], kind=m["kind"], status=r.status)
+                                   for m, r in zip(mix, res) if r.status not in (0, -100, -101)],
+               "peak_active": srv.peak_active,
                "mean_queue_s": float(np.mean([r.admitted - r.arrival for r in res])),
-               "payload_prep_s": t_prep, **{k: list(v) if isinstance(v, tuple) else v for k, v in SERVE_MIX.items()}}
+               "blocks_max": max(m["B"] ** 3 for m in mix), **{k: list(v) if isinstance(v, tuple) else v for k, v in mix_cfg.items()}}
         if batched:
             # the same requests, one stream and graph per solve (for comparison)
             srv2 = serve.Server(device=local, max_active=args.serve_active, steps_per_round=8, batched=False)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-            res2 = srv2.run(reqs)
+            res2 = srv2.run(reqs, deadline=args.serve_deadline)
             torch.cuda.synchronize()
             wall2 = time.perf_counter() - t1
             sm2 = serve.summarize(res2, wall2)
@@ -591,16 +580,18 @@ def run_serve(args, sub=False):
         "metric": "serving: aggregate DG DOF-updates/s per RK stage", "value": value, "unit": "DOF-updates/s",
         "n_gpus": ws, "steps": len(res), "warmup": len(warm), "ms_per_step": ms / max(1, len(res)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "serving-mix-periodic-cubes-64-512-blocks-n8-p1-3-blast-or-vortex",
-                   "requests": len(res), **{k: list(v) if isinstance(v, tuple) else v for k, v in SERVE_MIX.items()},
+        "config": {"workload": "serving-mix-periodic-cubes-64-8192-blocks-n8-p1-3-blast-or-vortex",
+                   "requests": len(res), **{k: list(v) if isinstance(v, tuple) else v for k, v in mix_cfg.items()},
                    "max_active": args.serve_active, "hbm_budget_bytes": srv.budget},
         "serve": {"p50_s": sm["p50_s"], "p99_s": sm["p99_s"], "wall_s": wall,
                   "peak_active": srv.peak_active, "peak_bytes": srv.peak_bytes,
-                  "failed": sum(1 for r in res if r.status != 0),
+                  "failed": sum(1 for r in res if r.status not in (0, -100, -101)),
+                  "unfinished_at_deadline": sum(1 for r in res if r.status in (-100, -101)),
+                  "failed_requests": [dict(rid=m["rid"], B=m["B"], p=m["p"], kind=m["kind"], status=r.status)
+                                      for m, r in zip(mix, res) if r.status not in (0, -100, -101)],
                   "mean_queue_s": float(np.mean([r.admitted - r.arrival for r in res])),
                   "dof_updates": updates,
-                  "payload": "initial values at the quadrature points, FP64, made before the run",
-                  "payload_prep_s": t_prep},
+                  "payload": "initial values computed on the GPU by the build worker (inside the timed run)"},
         "clocks": ck.summary(),
     }
     print(json.dumps(line))
@@ -727,15 +718,16 @@ def _cube_points(B, p, torch, dev):
     return torch.stack([X, Y, Z], -1).reshape(B ** 3, 512, N ** 3, 3)
 
 
-def _vortex_t(x, t, torch):
+def _vortex_t(x, t, torch, scale=20.0):
     """The isentropic vortex of the bench mapped into the unit cube from a
-    20-unit box (so the periodic cut of its Gaussian tail, e^-50, sets no
-    error floor), translated by the free stream to time t, nearest periodic
-    image (as workloads.vortex_exact), on torch tensors: conserved variables
-    [..., 5]."""
-    beta, gamma, scale, period = 5.0, 1.4, 20.0, 20.0
-    cx = (10.0 + t * scale) % period
-    cy = (10.0 + t * scale) % period
+    box of `scale` units centred on it (20 in the sweep, so the periodic cut
+    of its Gaussian tail, e^-50, sets no error floor; 10 in the serving mix,
+    as workloads.serving_initial), translated by the free stream to time t,
+    nearest periodic image (as workloads.vortex_exact), on torch tensors:
+    conserved variables [..., 5]."""
+    beta, gamma, period = 5.0, 1.4, scale
+    cx = (scale / 2 + t * scale) % period
+    cy = (scale / 2 + t * scale) % period
     X = scale * x[..., 0]
     Y = scale * x[..., 1]
     dx = torch.remainder(X - cx + period / 2, period) - period / 2
@@ -750,6 +742,34 @@ def _vortex_t(x, t, torch):
     pr = rho ** gamma
     E = pr / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)
     return torch.stack([rho, rho * u, rho * v, rho * w, E], -1)
+
+
+def _blast_t(x, centre, r0, width, torch):
+    """workloads.blast on torch tensors: (rho, p) = (8, 10) inside r0, (1, 1)
+    outside, at rest, tanh interface of the given width."""
+    c = torch.tensor(np.asarray(centre, float), dtype=x.dtype, device=x.device)
+    r = torch.sqrt(((x - c) ** 2).sum(-1))
+    sh = 0.5 * (1.0 - torch.tanh((r - r0) / width))
+    rho = 1.0 + 7.0 * sh
+    pr = 1.0 + 9.0 * sh
+    z = torch.zeros_like(rho)
+    return torch.stack([rho, z, z, z, pr / 0.4], -1)
+
+
+def serving_device_init(m, torch, dev):
+    """Initial values of a serving_mix request computed on the GPU at the
+    forest's Gauss points (the same formulas as workloads.serving_initial)."""
+    def init(f):
+        with torch.no_grad():
+            X = _cube_points(m["B"], m["p"], torch, dev)
+            if m["kind"] == "blast":
+                U = _blast_t(X, m["centre"], 0.1, 1.0 / (m["B"] * m["n_seg"]), torch)
+            else:
+                U = _vortex_t(X, 0.0, torch, scale=10.0)
+            del X
+            f.set_state_nodal(U.contiguous())
+            del U
+    return init
 
 
 def _to_nodal_t(K, p, torch):
@@ -874,10 +894,13 @@ def main():
                     help="level jumps: the paper's guard-cell scheme (default) or the conservative mortar repair")
     ap.add_argument("--quick-line", action="store_true",
                     help="the step line without the over-L2, serving and AMR sub-objects")
-    ap.add_argument("--serve-sub-requests", type=int, default=16)
+    ap.add_argument("--serve-sub-requests", type=int, default=48)
     ap.add_argument("--amr-sub-periods", type=int, default=10)
     ap.add_argument("--amr-p", type=int, default=1, help="degree of the --amr run")
     ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-full", action="store_true", help="256 requests, end times scaled by 0.1")
+    ap.add_argument("--serve-deadline", type=float, default=120.0,
+                    help="seconds after which a serving run stops (unfinished requests are reported)")
     ap.add_argument("--serve-streams", action="store_true",
                     help="serve with one stream and graph per solve instead of batches per degree")
     ap.add_argument("--serve-active", type=int, default=8)

@@ -41,7 +41,9 @@ class Request:
     p: int
     t_end: float
     init: object            # fun(x[..., d]) -> conserved values, ("nodal", values at the
-                            # quadrature points), or a modal state array
+                            # quadrature points), ("device", fn) with fn(forest) setting the
+                            # state itself (e.g. from values computed on the GPU), or a
+                            # modal state array
     precision: int = FP32
 
 
@@ -105,6 +107,8 @@ class GpuSolve:
             self.f.project(req.init)
         elif isinstance(req.init, tuple) and req.init[0] == "nodal":
             self.f.set_state_nodal(req.init[1])
+        elif isinstance(req.init, tuple) and req.init[0] == "device":
+            req.init[1](self.f)
         else:
             self.f.set_state(req.init)
         self.dof = self.f.n_leaves * self.f.nv * self.f.M * self.f.nc
@@ -122,6 +126,11 @@ class GpuSolve:
 
     def progress(self):
         return self.f.time, self.f.step_count
+
+    def failed(self):
+        """A non-finite state stops the solve's clock (its time increment is
+        0 from then on), so it is retired as failed instead of waited for."""
+        return self.f.status_word() != 0
 
     def finish(self, keep_state):
         state = self.f.get_state() if keep_state else None
@@ -195,7 +204,7 @@ class Server:
             changed = False
             for s in list(g.members):
                 t, steps = s.progress()
-                if t >= s.req.t_end:
+                if t >= s.req.t_end or _failed(s):
                     state, status = s.finish(keep_state)
                     results[s.req.rid] = Result(s.req.rid, s.req.arrival, s.admitted, self.clock() - t0,
                                                 steps, s.dof, t, status, s.bytes, state)
@@ -214,9 +223,12 @@ class Server:
                 progressed = True
         return progressed, freed
 
-    def run(self, requests, keep_state=False):
+    def run(self, requests, keep_state=False, deadline=None):
         """Serve `requests` (arrival times relative to the call); returns the
-        per-request results in request order."""
+        per-request results in request order.  With a deadline (seconds), the
+        run stops admitting once it is passed, retires the active solves where
+        they are (status -100) and reports the requests never admitted with
+        status -101."""
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
         queue, building, active, results = [], [], [], {}
         used = 0
@@ -225,6 +237,19 @@ class Server:
         try:
             while pending or queue or building or active:
                 now = self.clock() - t0
+                if deadline is not None and now > deadline and not building:
+                    for g in self.groups.values():
+                        g.batch.sync()
+                    for s in active:
+                        if getattr(s, "done", False):
+                            continue
+                        t, steps = s.progress()
+                        state, _ = s.finish(keep_state)
+                        results[s.req.rid] = Result(s.req.rid, s.req.arrival, s.admitted, now, steps, s.dof, t,
+                                                    -100, s.bytes, state)
+                    for r in pending + queue:
+                        results[r.rid] = Result(r.rid, r.arrival, now, now, 0, 0, 0.0, -101)
+                    break
                 while pending and pending[0].arrival <= now:
                     queue.append(pending.pop(0))
                 # admission: first come first served, by slot count and footprint
@@ -271,7 +296,7 @@ class Server:
                         continue
                     progressed = True
                     t, steps = s.progress()
-                    if t >= s.req.t_end:
+                    if t >= s.req.t_end or _failed(s):
                         state, status = s.finish(keep_state)
                         results[s.req.rid] = Result(s.req.rid, s.req.arrival, s.admitted, self.clock() - t0,
                                                     steps, s.dof, t, status, s.bytes, state)
@@ -292,6 +317,11 @@ class Server:
                 g.batch.close()
             self.groups = {}
         return [results[r.rid] for r in requests]
+
+
+def _failed(s):
+    f = getattr(s, "failed", None)
+    return bool(f()) if f is not None else False
 
 
 @dataclasses.dataclass
