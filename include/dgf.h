@@ -346,6 +346,10 @@ dgf_status dgf_batch_step(dgf_batch* b, int32_t steps);
 dgf_status dgf_batch_sync(dgf_batch* b);
 /* idle = 1 when all work enqueued on the batch stream has finished (no wait). */
 dgf_status dgf_batch_query(dgf_batch* b, int32_t* idle);
+/* Time, step count (increments with dt > 0) and status word of every member,
+ * in member order, after the work enqueued so far (waits for the batch
+ * stream): one gather on the device, one copy. */
+dgf_status dgf_batch_progress(dgf_batch* b, double* t, int64_t* steps, int32_t* status);
 
 #ifdef __cplusplus
 }

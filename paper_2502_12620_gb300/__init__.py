@@ -94,6 +94,7 @@ _SIGS = {
     "dgf_batch_step": [_P, ctypes.c_int32],
     "dgf_batch_sync": [_P],
     "dgf_batch_query": [_P, ctypes.POINTER(ctypes.c_int32)],
+    "dgf_batch_progress": [_P, _P, _P, _P],
 }
 
 
@@ -457,6 +458,16 @@ class Batch:
         v = ctypes.c_int32()
         _check(lib().dgf_batch_query(self.h, ctypes.byref(v)))
         return bool(v.value)
+
+    def progress(self):
+        """(time, steps, status) arrays of the members, in member order."""
+        n = len(self.members)
+        t = np.zeros(n)
+        st = np.zeros(n, np.int64)
+        ss = np.zeros(n, np.int32)
+        if n:
+            _check(lib().dgf_batch_progress(self.h, _ptr(t), _ptr(st), _ptr(ss)))
+        return t, st, ss
 
     def close(self):
         if getattr(self, "h", None):

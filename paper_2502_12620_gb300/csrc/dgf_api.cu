@@ -64,6 +64,16 @@ __device__ __forceinline__ void dt_one(DevScalars* s, double cfl) {
 
 __global__ void k_dt(DevScalars* s, double cfl) { dt_one(s, cfl); }
 
+// time, step count and status word of every forest of a batch
+__global__ void k_batch_progress(DevScalars* const* __restrict__ s, int n, double* t, long long* steps, int* status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    t[i] = s[i]->t;
+    steps[i] = s[i]->steps;
+    status[i] = s[i]->status;
+  }
+}
+
 // the time increments of every forest of a batch (one thread each)
 __global__ void k_dt_batch(DevScalars* const* __restrict__ s, const double* __restrict__ cfl, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2077,6 +2087,17 @@ struct dgf_batch {
   std::vector<dgf_forest*> mem;
   int p = -1, kernel = 1, all_affine = 0, slots = 0, items = 0;
   long long gblocks = 0;
+  // device arrays, kept and grown (never shrunk) across membership changes,
+  // so that admitting or retiring a member frees nothing (cudaFree would
+  // synchronise the whole device); written by one copy on the batch stream
+  // from a pinned host staging buffer
+  void* dev = nullptr;
+  size_t dev_cap = 0;
+  void* host = nullptr;
+  size_t host_cap = 0;
+  void* prog_dev = nullptr;   // progress gather: [n] t, [n] steps, [n] status
+  void* prog_host = nullptr;  // pinned
+  int prog_cap = 0;
   void* sargs[3] = {nullptr, nullptr, nullptr};
   void* gargs[3] = {nullptr, nullptr, nullptr};
   int* istart = nullptr;
@@ -2089,14 +2110,9 @@ struct dgf_batch {
 
 namespace {
 
-void batch_free(dgf_batch* b) {
-  for (int k = 0; k < 3; ++k) {
-    if (b->sargs[k]) cudaFree(b->sargs[k]);
-    if (b->gargs[k]) cudaFree(b->gargs[k]);
-    b->sargs[k] = b->gargs[k] = nullptr;
-  }
-  for (void* q : {(void*)b->istart, (void*)b->bstart, (void*)b->nfb, (void*)b->scal, (void*)b->cfl})
-    if (q) cudaFree(q);
+// forget the members' arrays and graph (the allocations stay for reuse)
+void batch_reset(dgf_batch* b) {
+  for (int k = 0; k < 3; ++k) b->sargs[k] = b->gargs[k] = nullptr;
   b->istart = b->bstart = b->nfb = nullptr;
   b->scal = nullptr;
   b->cfl = nullptr;
@@ -2106,10 +2122,15 @@ void batch_free(dgf_batch* b) {
   b->gblocks = 0;
 }
 
-template <class T>
-dgf_status batch_upload(dgf_batch* b, T** dst, const void* src, size_t bytes) {
-  if (cudaMalloc((void**)dst, bytes ? bytes : 16) != cudaSuccess) return fail(DGF_ENOMEM, "batch allocation failed");
-  return cuda_check(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice), "batch upload");
+void batch_release(dgf_batch* b) {
+  batch_reset(b);
+  if (b->dev) cudaFree(b->dev);
+  if (b->host) cudaFreeHost(b->host);
+  if (b->prog_dev) cudaFree(b->prog_dev);
+  if (b->prog_host) cudaFreeHost(b->prog_host);
+  b->dev = b->host = b->prog_dev = b->prog_host = nullptr;
+  b->dev_cap = b->host_cap = 0;
+  b->prog_cap = 0;
 }
 
 // one time increment of every member: dt of each, then 3 x (guard traces, stage)
@@ -2165,7 +2186,7 @@ dgf_status dgf_batch_destroy(dgf_batch* b) {
   if (!b) return DGF_OK;
   DeviceGuard dg(b->device);
   cudaStreamSynchronize(b->stream);
-  batch_free(b);
+  batch_release(b);
   if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;
   return DGF_OK;
@@ -2175,7 +2196,7 @@ dgf_status dgf_batch_set(dgf_batch* b, dgf_forest* const* forests, const double*
   if (!b || (n > 0 && (!forests || !t_end)) || n < 0) return fail(DGF_EINVAL, "null argument");
   DeviceGuard dg(b->device);
   cudaStreamSynchronize(b->stream);
-  batch_free(b);
+  batch_reset(b);
   b->mem.assign(forests, forests + n);
   if (n == 0) return DGF_OK;
   dgf_forest* f0 = forests[0];
@@ -2214,6 +2235,9 @@ dgf_status dgf_batch_set(dgf_batch* b, dgf_forest* const* forests, const double*
     dgf_forest* f = forests[i];
     for (int k = 0; k < 3; ++k) {
       rs[k].push_back(stage_args(f, src[k], dst[k], ca[k], cb[k], 0, k == 2));
+      // a batch has work items enough to fill the GPU: whole blocks per item
+      // (no chunk-start overhead; the result does not depend on the chunk)
+      rs[k].back().zchunk = f->n;
       rg[k].push_back(guard_args(f, src[k], f->gtr.ptr, 1));
     }
     const int it = stage_items<3, float>(rs[0].back());
@@ -2233,21 +2257,55 @@ dgf_status dgf_batch_set(dgf_batch* b, dgf_forest* const* forests, const double*
   }
   b->items = istart[n];
   b->gblocks = gb;
-  dgf_status st;
-  for (int k = 0; k < 3; ++k) {
-    std::vector<unsigned char> hs(stage_args_pack<3, float>(rs[k].data(), n, nullptr));
-    stage_args_pack<3, float>(rs[k].data(), n, hs.data());
-    if ((st = batch_upload(b, &b->sargs[k], hs.data(), hs.size()))) return st;
-    std::vector<unsigned char> hg(guard_args_pack<3, float>(rg[k].data(), n, nullptr));
-    guard_args_pack<3, float>(rg[k].data(), n, hg.data());
-    if ((st = batch_upload(b, &b->gargs[k], hg.data(), hg.size()))) return st;
+  // one device allocation holds every array (256-byte aligned pieces)
+  const size_t ss = stage_args_pack<3, float>(rs[0].data(), n, nullptr);
+  const size_t gs = guard_args_pack<3, float>(rg[0].data(), n, nullptr);
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t sz[5] = {istart.size() * sizeof(int), bstart.size() * sizeof(int), nfb.size() * sizeof(int),
+                        scal.size() * sizeof(DevScalars*), cfl.size() * sizeof(double)};
+  size_t total = 3 * al(ss) + 3 * al(gs);
+  for (size_t x : sz) total += al(x);
+  if (total > b->dev_cap) {
+    const size_t cap = std::max(total, 2 * b->dev_cap) + (64 << 10);
+    if (b->dev) cudaFree(b->dev);
+    b->dev = nullptr;
+    b->dev_cap = 0;
+    if (cudaMalloc(&b->dev, cap) != cudaSuccess) return fail(DGF_ENOMEM, "batch allocation failed");
+    b->dev_cap = cap;
   }
-  if ((st = batch_upload(b, &b->istart, istart.data(), istart.size() * sizeof(int))) ||
-      (st = batch_upload(b, &b->bstart, bstart.data(), bstart.size() * sizeof(int))) ||
-      (st = batch_upload(b, &b->nfb, nfb.data(), nfb.size() * sizeof(int))) ||
-      (st = batch_upload(b, &b->scal, scal.data(), scal.size() * sizeof(DevScalars*))) ||
-      (st = batch_upload(b, &b->cfl, cfl.data(), cfl.size() * sizeof(double))))
-    return st;
+  if (total > b->host_cap) {
+    const size_t cap = std::max(total, 2 * b->host_cap) + (64 << 10);
+    if (b->host) cudaFreeHost(b->host);
+    b->host = nullptr;
+    b->host_cap = 0;
+    if (cudaMallocHost(&b->host, cap) != cudaSuccess) return fail(DGF_ENOMEM, "batch staging allocation failed");
+    b->host_cap = cap;
+  }
+  unsigned char* h = (unsigned char*)b->host;
+  unsigned char* d = (unsigned char*)b->dev;
+  size_t off = 0;
+  for (int k = 0; k < 3; ++k) {
+    stage_args_pack<3, float>(rs[k].data(), n, h + off);
+    b->sargs[k] = d + off;
+    off += al(ss);
+    guard_args_pack<3, float>(rg[k].data(), n, h + off);
+    b->gargs[k] = d + off;
+    off += al(gs);
+  }
+  const void* srcs[5] = {istart.data(), bstart.data(), nfb.data(), scal.data(), cfl.data()};
+  void* dsts[5];
+  for (int i = 0; i < 5; ++i) {
+    memcpy(h + off, srcs[i], sz[i]);
+    dsts[i] = d + off;
+    off += al(sz[i]);
+  }
+  b->istart = (int*)dsts[0];
+  b->bstart = (int*)dsts[1];
+  b->nfb = (int*)dsts[2];
+  b->scal = (DevScalars**)dsts[3];
+  b->cfl = (double*)dsts[4];
+  dgf_status st = cuda_check(cudaMemcpyAsync(b->dev, b->host, off, cudaMemcpyHostToDevice, b->stream), "batch upload");
+  if (st) return st;
   return cuda_check(cudaStreamSynchronize(b->stream), "batch set");
 }
 
@@ -2273,6 +2331,43 @@ dgf_status dgf_batch_step(dgf_batch* b, int32_t steps) {
   }
   for (int i = 0; i < steps; ++i)
     if ((st = cuda_check(cudaGraphLaunch(b->graph, b->stream), "graph launch"))) return st;
+  return DGF_OK;
+}
+
+dgf_status dgf_batch_progress(dgf_batch* b, double* t, int64_t* steps, int32_t* status) {
+  if (!b || (!b->mem.empty() && (!t || !steps || !status))) return fail(DGF_EINVAL, "null argument");
+  const int n = (int)b->mem.size();
+  if (n == 0) return DGF_OK;
+  DeviceGuard dg(b->device);
+  const size_t bytes = (size_t)n * (sizeof(double) + sizeof(long long) + sizeof(int));
+  if (n > b->prog_cap) {
+    const int cap = std::max(n, 2 * b->prog_cap);
+    const size_t cb = (size_t)cap * (sizeof(double) + sizeof(long long) + sizeof(int));
+    if (b->prog_dev) cudaFree(b->prog_dev);
+    if (b->prog_host) cudaFreeHost(b->prog_host);
+    b->prog_dev = b->prog_host = nullptr;
+    b->prog_cap = 0;
+    if (cudaMalloc(&b->prog_dev, cb) != cudaSuccess || cudaMallocHost(&b->prog_host, cb) != cudaSuccess)
+      return fail(DGF_ENOMEM, "batch progress buffers");
+    b->prog_cap = cap;
+  }
+  double* dt_ = (double*)b->prog_dev;
+  long long* ds = (long long*)(dt_ + n);
+  int* dst = (int*)(ds + n);
+  k_batch_progress<<<(n + 127) / 128, 128, 0, b->stream>>>(b->scal, n, dt_, ds, dst);
+  dgf_status st = cuda_check(cudaGetLastError(), "batch progress");
+  if (!st) st = cuda_check(cudaMemcpyAsync(b->prog_host, b->prog_dev, bytes, cudaMemcpyDeviceToHost, b->stream),
+                           "batch progress copy");
+  if (!st) st = cuda_check(cudaStreamSynchronize(b->stream), "batch progress sync");
+  if (st) return st;
+  const double* ht = (const double*)b->prog_host;
+  const long long* hs = (const long long*)(ht + n);
+  const int* hst = (const int*)(hs + n);
+  for (int i = 0; i < n; ++i) {
+    t[i] = ht[i];
+    steps[i] = hs[i];
+    status[i] = hst[i];
+  }
   return DGF_OK;
 }
 

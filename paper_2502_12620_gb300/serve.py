@@ -11,7 +11,9 @@ deterministic kernels, and an increment at t = t_end is the identity), so
 its result does not depend on what else runs beside it.
 
 With batched=True, the admitted 3D FP32 solves of 8^3-cell blocks are
-advanced together instead: one library batch per degree, so each stage of
+advanced together instead: one library batch per degree and size class
+(below / above large_dof unknowns, so that small solves do not wait for the
+rounds of large ones), so each stage of
 every such solve goes through one launch of the guard-trace kernel and one
 of the persistent stage kernel (a single CUDA graph per batch membership;
 admitting or retiring a solve rewrites the batch's device work descriptors).
@@ -151,7 +153,7 @@ class Server:
 
     def __init__(self, device=0, hbm_budget=None, max_active=16, steps_per_round=8,
                  build_workers=2, solve_factory=None, clock=time.perf_counter, sleep=time.sleep,
-                 batched=False):
+                 batched=False, batch_steps=8, large_dof=64 << 20):
         self.device = device
         if hbm_budget is None:
             import torch
@@ -167,7 +169,9 @@ class Server:
         self.peak_active = 0
         self.peak_bytes = 0
         self.batched = bool(batched)
-        self.groups = {}  # degree -> _Group (batched mode)
+        self.batch_steps = int(batch_steps)
+        self.large_dof = int(large_dof)
+        self.groups = {}  # (degree, large) -> _Group (batched mode)
 
     def _next_k(self, s, t, steps):
         """Steps to enqueue next: the predicted remainder (from the mean dt so
@@ -193,6 +197,12 @@ class Server:
             s.enqueue(self.steps_per_round)
         return s
 
+    def _group_key(self, s):
+        """Batches by degree and size class: a small solve does not wait for
+        the rounds of large ones (a round is batch_steps steps of every
+        member of the batch)."""
+        return (s.req.p, s.dof > self.large_dof)
+
     def _serve_groups(self, results, keep_state, t0):
         """Batched mode: retire finished members, take in new ones, and
         enqueue the next round of steps on every batch that has drained.
@@ -202,9 +212,10 @@ class Server:
             if not g.batch.idle():
                 continue
             changed = False
-            for s in list(g.members):
-                t, steps = s.progress()
-                if t >= s.req.t_end or _failed(s):
+            ts, nsteps, stats = g.batch.progress() if g.members else ((), (), ())
+            for s, t, steps, stw in list(zip(g.members, ts, nsteps, stats)):
+                t, steps = float(t), int(steps)
+                if t >= s.req.t_end or stw != 0:
                     state, status = s.finish(keep_state)
                     results[s.req.rid] = Result(s.req.rid, s.req.arrival, s.admitted, self.clock() - t0,
                                                 steps, s.dof, t, status, s.bytes, state)
@@ -219,7 +230,7 @@ class Server:
             if changed:
                 g.batch.set([s.f for s in g.members], [s.req.t_end for s in g.members])
             if g.members:
-                g.batch.step(self.steps_per_round)
+                g.batch.step(self.batch_steps)
                 progressed = True
         return progressed, freed
 
@@ -279,9 +290,10 @@ class Server:
                     used += s.bytes - est
                     active.append(s)
                     if getattr(s, "batched", False):
-                        if s.req.p not in self.groups:
-                            self.groups[s.req.p] = _Group(Batch(self.device))
-                        self.groups[s.req.p].joining.append(s)
+                        key = self._group_key(s)
+                        if key not in self.groups:
+                            self.groups[key] = _Group(Batch(self.device))
+                        self.groups[key].joining.append(s)
                     item[0] = None
                     progressed = True
                 building = [it for it in building if it[0] is not None]
@@ -326,7 +338,7 @@ def _failed(s):
 
 @dataclasses.dataclass
 class _Group:
-    """The solves of one degree advanced by one library batch."""
+    """The solves of one degree and size class advanced by one library batch."""
     batch: object
     members: list = dataclasses.field(default_factory=list)
     joining: list = dataclasses.field(default_factory=list)
