@@ -144,3 +144,32 @@ def test_adapt_then_steps_run(dgf):
             for _ in range(5):
                 U1 = S1.ssp_rk3_step(U1, S1.dt(U1))
             assert rel(f.get_state(), U1) < TOL["fp64"]
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_transfer_at_n8_matches_oracle(dgf, p):
+    """State transfer of a refinement and a coarsening at the block size of
+    the adaptive runs (8^3 cells) and p = 1, 3, FP32, against the oracle's
+    data inheritance (Sec. 3.4): split children (Eqs. (11)-(12)) and
+    combined parents (Eqs. (13)-(14)) of a blast profile."""
+    w = W.periodic_cube_forest(2)
+    ic = lambda x: W.blast(x, (0.4, 0.5, 0.55), r0=0.2, width=0.05)
+    f = dgf.Forest.from_workload(w, p=p, precision=dgf.FP32)
+    S = dg.Solver(FO.build(w), p)
+    U = S.project(ic).astype(np.float32).astype(np.float64)
+    f.set_state(U)
+    g = np.zeros(8)
+    g[[0, 5]] = 1.0
+    assert f.adapt(0.5, -1.0, 3, indicator=g) == (2, 0)
+    S1, U1, nr, nc = A.adapt(S, U, 0.5, -1.0, 3, g=g)
+    assert nr == 2 and _tables_equal(f, S1)
+    assert rel(f.get_state(), U1) < TOL["fp32"]
+    # coarsen the first refined root again
+    T = f.leaf_table()
+    g1 = np.array([0.0 if (int(T["root"][i]) == 0 and int(T["level"][i]) == 2) else 1.0
+                   for i in range(f.n_leaves)])
+    U1g = f.get_state().astype(np.float64)
+    nr2, nc2 = f.adapt(np.inf, 0.5, 3, indicator=g1)
+    S2, U2, _, _ = A.adapt(S1, U1g, np.inf, 0.5, 3, g=g1)
+    assert nc2 == 1 and _tables_equal(f, S2)
+    assert rel(f.get_state(), U2) < TOL["fp32"]
