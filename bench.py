@@ -545,8 +545,7 @@ def run_serve(args, sub=False):
     srv = serve.Server(device=local, max_active=args.serve_active, steps_per_round=8, batched=batched)
     # grow the caching allocator's pool to the serving budget before the timed
     # run (first-time device allocations of many GB would otherwise be timed)
-    pool = torch.empty(int(0.9 * srv.budget), dtype=torch.uint8, device=dev)
-    del pool
+    pkg.reserve_memory(int(0.9 * srv.budget), local)
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()

@@ -116,7 +116,14 @@ typedef struct {
 } dgf_forest_desc;
 
 /* Optional device allocator.  alloc returns NULL on failure; free is given
- * the size and stream of the matching alloc. */
+ * the size and stream of the matching alloc.  The library uses the memory
+ * on its forest's stream and on batch streams, in no order the allocator
+ * knows of: alloc must return memory that no work pending on any stream
+ * still touches (a caching allocator must not hand out a block freed on a
+ * stream that has work queued after the free, and should serve the
+ * library from a stream of its own).  Before it calls free the library
+ * synchronises the forest's stream; a batch holding the forest must be
+ * synchronised by the caller before the forest is regridded or destroyed. */
 typedef struct {
   void* ctx;
   void* (*alloc)(void* ctx, size_t bytes, void* stream);
@@ -325,6 +332,9 @@ dgf_status dgf_dg_residual_noalloc(dgf_forest* f, const void* U_nodal, void* L_n
  * plain form (DGF_FP32), no mortar repair, no limiter, state set
  * (DGF_EUNSUPPORTED / DGF_EINVAL / DGF_ESTATE otherwise).  The batch owns
  * small device arrays (cudaMalloc); the forests keep owning their state.
+ * Work items are z-chunks of blocks, one chunk length for the batch chosen
+ * from its total block count to fill the persistent grid (DGF_ZCHUNK fixes
+ * it); like the single-forest tiling it changes no bit of any result.
  *   dgf_batch_create   device ordinal; stream (cudaStream_t) or NULL for an
  *                      own stream.
  *   dgf_batch_set      replace the members (n may be 0) and set each

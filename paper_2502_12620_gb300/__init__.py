@@ -125,20 +125,50 @@ def _ptr(a):
     return ctypes.c_void_p(a.ctypes.data) if a is not None else None
 
 
+_LIB_STREAMS = {}
+_LIB_STREAMS_LOCK = __import__("threading").Lock()
+
+
+def library_stream(device=0):
+    """The stream the library's device memory is drawn on from torch's
+    caching allocator.  Nothing runs on it: torch hands a freed block to a
+    new allocation of the same stream at once, even while kernels queued
+    there may still touch it, and the library uses its memory on its own
+    streams, which torch does not order against.  Drawing on a stream of
+    its own keeps the library's blocks apart from every tensor's; the
+    library synchronises its stream before it frees a block."""
+    import torch
+    with _LIB_STREAMS_LOCK:
+        s = _LIB_STREAMS.get(device)
+        if s is None:
+            s = _LIB_STREAMS[device] = torch.cuda.Stream(device=device)
+    return s
+
+
+def reserve_memory(nbytes, device=0):
+    """Grow torch's cached pool of the library's stream by nbytes (allocated
+    and released at once), so that later forest allocations are served from
+    it without new device allocations."""
+    import torch
+    with torch.cuda.stream(library_stream(device)):
+        t = torch.empty(int(nbytes), dtype=torch.uint8, device=torch.device("cuda", device))
+        del t
+
+
 class _TorchAllocator:
-    """Device memory for the library from torch's caching allocator."""
+    """Device memory for the library from torch's caching allocator, on the
+    library's own stream (library_stream)."""
 
     def __init__(self, device):
         import torch
         self.torch = torch
         self.device = device
         self.live = {}
+        lib_stream = library_stream(device)
 
         def _alloc(ctx, nbytes, stream):
-            # blocks belong to torch's current stream; the library synchronises
-            # its own stream before it frees or reuses any of them
             try:
-                p = torch.cuda.caching_allocator_alloc(int(nbytes), device)
+                p = torch.cuda.caching_allocator_alloc(int(nbytes), device, lib_stream)
             except Exception:
                 return None
             self.live[p] = nbytes

@@ -82,6 +82,23 @@ __global__ void k_dt_batch(DevScalars* const* __restrict__ s, const double* __re
 
 __global__ void k_reset_lam(DevScalars* s) { s->lam_bits = kInfBits; }
 
+__global__ void k_set_t_end(DevScalars* s, double t_end) { s->t_end = t_end; }
+
+__global__ void k_set_time(DevScalars* s, double t) {
+  s->t = t;
+  s->steps = 0;
+}
+
+// t = 0, no step taken, no end time, no CFL value yet, status 0
+__global__ void k_init_scalars(DevScalars* s) {
+  s->t = 0.0;
+  s->dt = 0.0;
+  s->t_end = __longlong_as_double((long long)kInfBits);
+  s->lam_bits = kInfBits;
+  s->status = 0;
+  s->steps = 0;
+}
+
 // compensated form: u^n as the FP32 pair hi = fl(u^n), lo = fl(u^n - hi)
 // (u^n - hi is exact in FP64), so hi + lo carries u^n to about 48 bits
 __global__ void k_split(const double* __restrict__ u, float* __restrict__ hi, float* __restrict__ lo, size_t n) {
@@ -232,8 +249,14 @@ void* dev_alloc(dgf_forest* f, size_t bytes) {
 
 void dev_free(dgf_forest* f, dgf_forest::Buf& b) {
   if (!b.ptr) return;
-  if (f->has_alloc) f->alloc.free(f->alloc.ctx, b.ptr, b.bytes, (void*)f->stream);
-  else cudaFree(b.ptr);
+  if (f->has_alloc) {
+    // the caller's allocator may hand the block out again at once: nothing
+    // of this forest's may still touch it
+    cudaStreamSynchronize(f->stream);
+    f->alloc.free(f->alloc.ctx, b.ptr, b.bytes, (void*)f->stream);
+  } else {
+    cudaFree(b.ptr);
+  }
   b.ptr = nullptr;
   b.bytes = 0;
 }
@@ -268,10 +291,14 @@ template <typename V>
 dgf_status upload(dgf_forest* f, dgf_forest::Buf& b, const V& v) {
   using T = typename V::value_type;
   if (!ensure(f, b, sizeof(T) * std::max<size_t>(v.size(), 1))) return fail(DGF_ENOMEM, "device allocation failed");
-  if (!v.empty())
-    return cuda_check(cudaMemcpyAsync(b.ptr, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, f->stream),
-                      "upload");
-  return DGF_OK;
+  if (v.empty()) return DGF_OK;
+  // v is often a temporary: the copy from pageable memory may read it after
+  // the call returns (the documented semantics allow it, and on a host whose
+  // memory the GPU reaches directly it does), so wait before v goes away
+  dgf_status st = cuda_check(
+      cudaMemcpyAsync(b.ptr, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, f->stream), "upload");
+  if (st) return st;
+  return cuda_check(cudaStreamSynchronize(f->stream), "upload");
 }
 
 template <typename Fn>
@@ -1168,8 +1195,10 @@ dgf_status set_t_end(dgf_forest* f, double t_end) {
   if (f->t_end_dev == t_end) return DGF_OK;
   DevScalars* s = (DevScalars*)f->scal.ptr;
   f->t_end_dev = t_end;
-  return cuda_check(cudaMemcpyAsync(&s->t_end, &f->t_end_dev, sizeof(double), cudaMemcpyHostToDevice, f->stream),
-                    "t_end");
+  // a kernel argument, not a copy from host memory: stream-ordered, and no
+  // host value has to outlive the call
+  k_set_t_end<<<1, 1, 0, f->stream>>>(s, t_end);
+  return cuda_check(cudaGetLastError(), "t_end");
 }
 
 dgf_status copy_state(dgf_forest* f, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
@@ -1262,11 +1291,15 @@ dgf_status dgf_forest_create(const dgf_forest_desc* desc, const dgf_allocator* a
       dgf_forest_destroy(f);
       return fail(DGF_ENOMEM, "device allocation failed");
     }
-    DevScalars s0{};
-    s0.t_end = INFINITY;
-    s0.lam_bits = kInfBits;
     f->t_end_dev = INFINITY;
-    cudaMemcpy(f->scal.ptr, &s0, sizeof(s0), cudaMemcpyHostToDevice);
+    // initialised by a kernel on the forest's stream (a cudaMemcpy from host
+    // memory would run on the legacy stream, which the forest's non-blocking
+    // stream is not ordered against, and may land after its first kernels)
+    k_init_scalars<<<1, 1, 0, f->stream>>>((DevScalars*)f->scal.ptr);
+    if (cudaGetLastError() != cudaSuccess) {
+      dgf_forest_destroy(f);
+      return fail(DGF_ECUDA, "device scalars");
+    }
   }
   dgf_status st = build_device(f);
   if (st) {
@@ -1498,6 +1531,9 @@ dgf_status dgf_set_state(dgf_forest* f, const void* src, int is_device) {
       cudaMemcpyAsync(U, src, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, f->stream),
       "set_state");
   if (st) return st;
+  // a host source is read by the copy engine possibly after the copy call
+  // returns: wait before the caller may release it
+  if (!is_device && (st = cuda_check(cudaStreamSynchronize(f->stream), "set_state"))) return st;
   // the device holds values at the Gauss points: u = V K per (leaf, var, cell)
   if ((st = cuda_check(do_convert(f, U, (size_t)f->nL, f->nc, 1, state_f64(f)), "to nodal"))) return st;
   f->have_state = true;
@@ -1631,12 +1667,10 @@ dgf_status dgf_get_time(dgf_forest* f, double* t) {
 dgf_status dgf_set_time(dgf_forest* f, double t) {
   if (dgf_status st = require_device(f)) return st;
   DeviceGuard dg(f->device);
-  DevScalars* s = (DevScalars*)f->scal.ptr;
-  double tt = t;
-  dgf_status st = copy_state(f, &s->t, &tt, sizeof(double), cudaMemcpyHostToDevice);
+  k_set_time<<<1, 1, 0, f->stream>>>((DevScalars*)f->scal.ptr, t);
+  dgf_status st = cuda_check(cudaGetLastError(), "set_time");
   if (st) return st;
-  int zero = 0;
-  return copy_state(f, &s->steps, &zero, sizeof(int), cudaMemcpyHostToDevice);
+  return cuda_check(cudaStreamSynchronize(f->stream), "set_time");
 }
 
 dgf_status dgf_step_count(dgf_forest* f, int64_t* steps) {
@@ -2085,7 +2119,7 @@ struct dgf_batch {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<dgf_forest*> mem;
-  int p = -1, kernel = 1, all_affine = 0, slots = 0, items = 0;
+  int p = -1, kernel = 1, all_affine = 0, slots = 0, items = 0, zchunk = 8;
   long long gblocks = 0;
   // device arrays, kept and grown (never shrunk) across membership changes,
   // so that admitting or retiring a member frees nothing (cudaFree would
@@ -2149,7 +2183,11 @@ dgf_status batch_enqueue(dgf_batch* b) {
     RtStage c = stage_args(f0, 0, 1, ca[k], cb[k], 0, k == 2);
     c.kernel = b->kernel;
     c.all_affine = b->all_affine;
-    const int grid = b->items < b->slots ? b->items : b->slots;
+    // one CTA per work item, not a persistent grid: a batch stage of several
+    // large members runs for tens of ms, and CTAs that retire after each
+    // item let work of other streams (a solve being built, on a stream of
+    // higher priority) onto the SMs meanwhile
+    const int grid = b->items;
     if ((st = cuda_check(launch_stage_batch<3, float>(c, b->sargs[k], b->istart, n, grid, b->stream),
                          "batch stage")))
       return st;
@@ -2231,13 +2269,32 @@ dgf_status dgf_batch_set(dgf_batch* b, dgf_forest* const* forests, const double*
   std::vector<RtStage> rs[3];
   std::vector<RtGuard> rg[3];
   long long gb = 0;
+  // one z-chunk length for the batch, from its total block count and the
+  // persistent grid: a chunk costs its layers plus ~0.6 layer of start-up
+  // (the lower layer's load and trace), the value that reproduces the
+  // single-forest autotuner's choices from 64 to 4096 blocks at p = 1..3;
+  // the result does not depend on it
+  b->zchunk = f0->n;
+  {
+    int64_t blocks = 0;
+    for (auto* f : b->mem) blocks += f->nL;
+    double best = 1e300;
+    for (int z = f0->n; z >= 1; z /= 2) {
+      const int64_t items = blocks * ((f0->n + z - 1) / z);
+      const double cost = (double)((items + b->slots - 1) / b->slots) * (z + 0.6);
+      if (cost < best - 1e-9) {
+        best = cost;
+        b->zchunk = z;
+      }
+      if (z == 1) break;
+    }
+    if (const char* zc = getenv("DGF_ZCHUNK")) b->zchunk = std::max(1, std::min(f0->n, atoi(zc)));
+  }
   for (int i = 0; i < n; ++i) {
     dgf_forest* f = forests[i];
     for (int k = 0; k < 3; ++k) {
       rs[k].push_back(stage_args(f, src[k], dst[k], ca[k], cb[k], 0, k == 2));
-      // a batch has work items enough to fill the GPU: whole blocks per item
-      // (no chunk-start overhead; the result does not depend on the chunk)
-      rs[k].back().zchunk = f->n;
+      rs[k].back().zchunk = b->zchunk;
       rg[k].push_back(guard_args(f, src[k], f->gtr.ptr, 1));
     }
     const int it = stage_items<3, float>(rs[0].back());
@@ -2250,9 +2307,8 @@ dgf_status dgf_batch_set(dgf_batch* b, dgf_forest* const* forests, const double*
     scal[i] = (DevScalars*)f->scal.ptr;
     cfl[i] = f->cfl;
     f->t_end_dev = t_end[i];
-    dgf_status st = cuda_check(cudaMemcpyAsync(&((DevScalars*)f->scal.ptr)->t_end, &t_end[i], sizeof(double),
-                                               cudaMemcpyHostToDevice, b->stream),
-                               "t_end");
+    k_set_t_end<<<1, 1, 0, b->stream>>>((DevScalars*)f->scal.ptr, t_end[i]);
+    dgf_status st = cuda_check(cudaGetLastError(), "t_end");
     if (st) return st;
   }
   b->items = istart[n];

@@ -99,20 +99,26 @@ def footprint_bytes(workload, p, precision=FP32):
 class GpuSolve:
     """One admitted request: a forest on its own stream."""
 
+    # solve streams take precedence over batch streams (created at the
+    # default, lowest priority): the kernels of a solve being built get SMs
+    # as soon as CTAs of a running batch stage retire
+    PRIORITY = -1
+
     def __init__(self, req, device=0):
         import torch
         self.req = req
-        self.stream = torch.cuda.Stream(device=device)
+        self.stream = torch.cuda.Stream(device=device, priority=self.PRIORITY)
         self.f = Forest.from_workload(req.workload, p=req.p, precision=req.precision, device=device)
         self.f.set_stream(self.stream)
-        if callable(req.init):
-            self.f.project(req.init)
-        elif isinstance(req.init, tuple) and req.init[0] == "nodal":
-            self.f.set_state_nodal(req.init[1])
-        elif isinstance(req.init, tuple) and req.init[0] == "device":
-            req.init[1](self.f)
-        else:
-            self.f.set_state(req.init)
+        with torch.cuda.stream(self.stream):  # initial values computed on the solve's stream
+            if callable(req.init):
+                self.f.project(req.init)
+            elif isinstance(req.init, tuple) and req.init[0] == "nodal":
+                self.f.set_state_nodal(req.init[1])
+            elif isinstance(req.init, tuple) and req.init[0] == "device":
+                req.init[1](self.f)
+            else:
+                self.f.set_state(req.init)
         self.dof = self.f.n_leaves * self.f.nv * self.f.M * self.f.nc
 
     @property
@@ -213,6 +219,7 @@ class Server:
                 continue
             changed = False
             ts, nsteps, stats = g.batch.progress() if g.members else ((), (), ())
+            prog = {id(s): (float(t), int(k)) for s, t, k in zip(g.members, ts, nsteps)}
             for s, t, steps, stw in list(zip(g.members, ts, nsteps, stats)):
                 t, steps = float(t), int(steps)
                 if t >= s.req.t_end or stw != 0:
@@ -230,9 +237,22 @@ class Server:
             if changed:
                 g.batch.set([s.f for s in g.members], [s.req.t_end for s in g.members])
             if g.members:
-                g.batch.step(self.batch_steps)
+                g.batch.step(self._round_steps(g.members, prog))
                 progressed = True
         return progressed, freed
+
+    def _round_steps(self, members, prog):
+        """Steps of a batch's next round: the fewest predicted remaining steps
+        of any member (from its mean dt so far), so that the first member to
+        finish is retired when the round ends; at least batch_steps (also for
+        a member without steps yet), at most 8 batch_steps."""
+        k = 8 * self.batch_steps
+        for s in members:
+            t, steps = prog.get(id(s), (0.0, 0))
+            dt = (t - s.t0) / steps if steps > 0 else 0.0
+            rem = math.ceil((s.req.t_end - t) / dt) if dt > 0 else self.batch_steps
+            k = min(k, rem)
+        return max(self.batch_steps, k)
 
     def run(self, requests, keep_state=False, deadline=None):
         """Serve `requests` (arrival times relative to the call); returns the

@@ -109,3 +109,27 @@ def test_batched_server_mixed_equals_alone(dgf):
         alone = Server(hbm_budget=8 << 30, max_active=1, steps_per_round=4, batched=True).run([q], keep_state=True)[0]
         assert r.status == 0 and r.t == q.t_end
         assert r.steps == alone.steps and np.array_equal(r.state, alone.state), r.rid
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_batch_chunk_length_changes_no_bit(dgf, p, monkeypatch):
+    """The batch's z-chunk length (chosen from its total block count, or
+    fixed by DGF_ZCHUNK) is a tiling choice: whole blocks, a ragged chunk of
+    3 layers and single layers give the same states bit for bit."""
+    specs = _members(dgf, p)
+    outs = []
+    for z in (8, 3, 1):
+        monkeypatch.setenv("DGF_ZCHUNK", str(z))
+        fs = [_forest(dgf, w, p) for w, _ in specs]
+        b = dgf.Batch()
+        b.set(fs, [t for _, t in specs])
+        b.step(6)
+        b.sync()
+        outs.append([f.get_state() for f in fs])
+        assert all(f.status_word() == 0 for f in fs)
+        b.close()
+        for f in fs:
+            f.close()
+    for o in outs[1:]:
+        for a, c in zip(o, outs[0]):
+            assert np.array_equal(a, c)

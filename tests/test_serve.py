@@ -214,3 +214,18 @@ def test_step_past_t_end_is_identity(prec):
     f.set_time(0.0)
     assert f.step_count == 0
     f.close()
+
+
+def test_batch_round_length_follows_the_first_member_to_finish():
+    from types import SimpleNamespace as NS
+    srv = Server(hbm_budget=1 << 30, batched=True, batch_steps=8)
+    a = NS(t0=0.0, req=NS(t_end=1.0))  # dt 0.05 so far: 10 steps left
+    b = NS(t0=0.0, req=NS(t_end=1.0))  # dt 0.01 so far: 90 steps left
+    c = NS(t0=0.0, req=NS(t_end=1.0))  # just joined: no steps yet
+    prog = {id(a): (0.5, 10), id(b): (0.1, 10)}
+    assert srv._round_steps([a, b], prog) == 10
+    assert srv._round_steps([b], prog) == 64         # at most 8 rounds of batch_steps
+    assert srv._round_steps([a, b, c], prog) == 8    # a new member: batch_steps
+    assert srv._round_steps([NS(t0=0.0, req=NS(t_end=0.52))], {}) == 8
+    done = NS(t0=0.0, req=NS(t_end=0.5))
+    assert srv._round_steps([done], {id(done): (0.5, 10)}) == 8  # at least batch_steps
