@@ -537,15 +537,23 @@ def run_serve(args, sub=False):
     t_prep = 0.0
     reqs = [serve.Request(m["rid"], m["arrival"], W.periodic_cube_forest(m["B"], n_seg=m["n_seg"]), m["p"],
                           m["t_end"], ("device", serving_device_init(m, torch, dev)), pkg.FP32) for m in mix]
-    # warm-up: one small solve of every degree (module load, allocator pool)
-    warm = [serve.Request(-1 - p, 0.0, W.periodic_cube_forest(2), p, 1e-3, W.smooth_state, pkg.FP32)
-            for p in SERVE_MIX["degrees"]]
+    # warm-up: a small solve of every degree and initial condition, with its
+    # initial values computed on the device like the timed requests' (module
+    # load, allocator pools, and the first-use compilation of torch's
+    # elementwise kernels for this GPU, which on a fresh machine takes seconds)
+    warm = []
+    for p in SERVE_MIX["degrees"]:
+        for kind in ("blast", "vortex"):
+            wm = dict(B=2, n_seg=8, p=p, kind=kind, centre=np.array([0.5, 0.5, 0.5]))
+            warm.append(serve.Request(-1 - len(warm), 0.0, W.periodic_cube_forest(2), p, 1e-3,
+                                      ("device", serving_device_init(wm, torch, dev)), pkg.FP32))
     batched = not args.serve_streams
     serve.Server(device=local, max_active=4, batched=batched).run(warm)
     srv = serve.Server(device=local, max_active=args.serve_active, steps_per_round=8, batched=batched)
     # grow the caching allocator's pool to the serving budget before the timed
     # run (first-time device allocations of many GB would otherwise be timed)
     pkg.reserve_memory(int(0.9 * srv.budget), local)
+    serve.reserve_init_memory(int(0.25 * srv.budget), local)
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -712,23 +720,26 @@ def run_amr(args, sub=False, p=None, periods=None):
 SWEEP = dict(t_end=0.005, cfl=0.1, vortex_box=20.0, runs=((1, (8, 16, 32)), (2, (8, 16, 32)), (3, (8, 16))))
 
 
-def _cube_points(B, p, torch, dev):
+def _cube_points(B, p, torch, dev, z0=0, z1=None):
     """Gauss points of the affine periodic cube of B^3 roots of 8^3 cells, on
     the device, in the library's nodal order [leaf][cell][point][axis] (leaf
     = root = bx + B by + B^2 bz, cell = i + 8 j + 64 k, point = qx + N qy +
-    N^2 qz)."""
+    N^2 qz); with z0, z1 only the roots of the slab z0 <= bz < z1 (leaves
+    z0 B^2 .. z1 B^2 - 1)."""
     N = p + 1
+    z1 = B if z1 is None else z1
     xg = torch.tensor(np.polynomial.legendre.leggauss(N)[0], dtype=torch.float64, device=dev)
     h = 1.0 / (8 * B)
     b = torch.arange(B, dtype=torch.float64, device=dev)
     c = torch.arange(8, dtype=torch.float64, device=dev)
     # 1D coordinate of (block, cell, point) along one axis
     ax = (b[:, None, None] / B + c[None, :, None] * h + h * (xg[None, None, :] + 1) / 2)  # [B][8][N]
-    X = ax[None, None, :, None, None, :, None, None, :].expand(B, B, B, 8, 8, 8, N, N, N)
-    Y = ax[None, :, None, None, :, None, None, :, None].expand(B, B, B, 8, 8, 8, N, N, N)
-    Z = ax[:, None, None, :, None, None, :, None, None].expand(B, B, B, 8, 8, 8, N, N, N)
+    nz = z1 - z0
+    X = ax[None, None, :, None, None, :, None, None, :].expand(nz, B, B, 8, 8, 8, N, N, N)
+    Y = ax[None, :, None, None, :, None, None, :, None].expand(nz, B, B, 8, 8, 8, N, N, N)
+    Z = ax[z0:z1, None, None, :, None, None, :, None, None].expand(nz, B, B, 8, 8, 8, N, N, N)
     # index order above: [bz][by][bx][k][j][i][qz][qy][qx]
-    return torch.stack([X, Y, Z], -1).reshape(B ** 3, 512, N ** 3, 3)
+    return torch.stack([X, Y, Z], -1).reshape(nz * B * B, 512, N ** 3, 3)
 
 
 def _vortex_t(x, t, torch, scale=20.0):
@@ -771,16 +782,24 @@ def _blast_t(x, centre, r0, width, torch):
 
 def serving_device_init(m, torch, dev):
     """Initial values of a serving_mix request computed on the GPU at the
-    forest's Gauss points (the same formulas as workloads.serving_initial)."""
+    forest's Gauss points (the same formulas as workloads.serving_initial),
+    one slab of roots at a time into the result (about 64 roots a slab), so
+    that the formulas' temporaries stay small against the state."""
     def init(f):
+        B, N = m["B"], m["p"] + 1
         with torch.no_grad():
-            X = _cube_points(m["B"], m["p"], torch, dev)
-            if m["kind"] == "blast":
-                U = _blast_t(X, m["centre"], 0.1, 1.0 / (m["B"] * m["n_seg"]), torch)
-            else:
-                U = _vortex_t(X, 0.0, torch, scale=10.0)
-            del X
-            f.set_state_nodal(U.contiguous())
+            U = torch.empty((B ** 3, 512, N ** 3, 5), dtype=torch.float64, device=dev)
+            zs = max(1, 64 // (B * B))
+            for z0 in range(0, B, zs):
+                z1 = min(B, z0 + zs)
+                X = _cube_points(B, m["p"], torch, dev, z0, z1)
+                if m["kind"] == "blast":
+                    V = _blast_t(X, m["centre"], 0.1, 1.0 / (B * m["n_seg"]), torch)
+                else:
+                    V = _vortex_t(X, 0.0, torch, scale=10.0)
+                U[z0 * B * B:z1 * B * B] = V
+                del X, V
+            f.set_state_nodal(U)
             del U
     return init
 

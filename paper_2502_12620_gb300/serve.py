@@ -27,6 +27,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import threading
 import time
 from concurrent.futures import ThreadPoolExecutor
 
@@ -96,21 +97,44 @@ def footprint_bytes(workload, p, precision=FP32):
     return int(state + geo + guard + L * 2 * d * 40 + (1 << 20))
 
 
+# solve and initial-value streams take precedence over batch streams
+# (created at the default, lowest priority): the kernels of a solve being
+# built get SMs as soon as CTAs of a running batch stage retire
+PRIORITY = -1
+_INIT_STREAMS = {}
+_INIT_LOCK = threading.Lock()
+
+
+def init_stream(device=0):
+    """The stream on which solves compute their initial values, shared by
+    the build workers, so that torch's cached blocks of one build serve the
+    next (a stream of its own per solve would grow a pool per solve)."""
+    import torch
+    with _INIT_LOCK:
+        s = _INIT_STREAMS.get(device)
+        if s is None:
+            s = _INIT_STREAMS[device] = torch.cuda.Stream(device=device, priority=PRIORITY)
+    return s
+
+
+def reserve_init_memory(nbytes, device=0):
+    """Grow torch's cached pool of the initial-value stream by nbytes."""
+    import torch
+    with torch.cuda.stream(init_stream(device)):
+        t = torch.empty(int(nbytes), dtype=torch.uint8, device=torch.device("cuda", device))
+        del t
+
+
 class GpuSolve:
     """One admitted request: a forest on its own stream."""
-
-    # solve streams take precedence over batch streams (created at the
-    # default, lowest priority): the kernels of a solve being built get SMs
-    # as soon as CTAs of a running batch stage retire
-    PRIORITY = -1
 
     def __init__(self, req, device=0):
         import torch
         self.req = req
-        self.stream = torch.cuda.Stream(device=device, priority=self.PRIORITY)
+        self.stream = torch.cuda.Stream(device=device, priority=PRIORITY)
         self.f = Forest.from_workload(req.workload, p=req.p, precision=req.precision, device=device)
         self.f.set_stream(self.stream)
-        with torch.cuda.stream(self.stream):  # initial values computed on the solve's stream
+        with torch.cuda.stream(init_stream(device)):  # initial values (the binding waits for them)
             if callable(req.init):
                 self.f.project(req.init)
             elif isinstance(req.init, tuple) and req.init[0] == "nodal":
