@@ -505,9 +505,9 @@ def over_l2_case(key, args, stream, flush, pk, pk_kind, torch, pkg):
 
 
 # ---------------------------------------------------------------- serving
-# the serving mix of the bench line: SURVEY's block range and arrival rate,
-# end times scaled by 0.01 so that the run takes seconds; --serve-full runs
-# 256 requests with end times scaled by 0.1
+# the serving mix: 256 Poisson arrivals at 20/s of periodic cubes of 64-8192
+# blocks at p = 1..3, end times drawn in [0.05, 0.5] and scaled by 0.01 in the
+# bench line (so that it takes seconds) or by 0.1 with --serve-full
 SERVE_MIX = dict(rate=20.0, seed=0, blocks=(64, 8192), degrees=(1, 2, 3), t_end=(0.05, 0.5), t_scale=0.01)
 
 
@@ -618,7 +618,7 @@ def run_serve(args, sub=False):
 # ---------------------------------------------------------------- dynamic AMR
 # every 40 steps the blast front has moved far enough that most regrids change
 # the forest; CFL 0.3 / (2p + 1) (0.1 at p = 1, 0.06 at p = 2), 0.02 at p = 3
-AMR = dict(B=4, n_seg=8, p=1, refine_above=0.05, coarsen_below=0.01, max_level=4, every=40, limiter=1e-6)
+AMR = dict(B=4, n_seg=8, p=1, refine_above=0.05, coarsen_below=0.01, max_level=4, every=40, limiter=1e-6, r0=0.12)
 
 
 def run_amr(args, sub=False, p=None, periods=None):
@@ -644,7 +644,10 @@ def run_amr(args, sub=False, p=None, periods=None):
     # admissible set, which no limiter can repair)
     width = (1.0 if cfg["p"] < 3 else 3.0) / (cfg["B"] * cfg["n_seg"] * 2 ** (cfg["max_level"] - 1))
     cfg["interface_cells"] = 1 if cfg["p"] < 3 else 3
-    ic = lambda x: W.blast(x, (0.5, 0.5, 0.5), r0=0.12, width=width)
+    # at p = 3 (CFL 0.02) the blast moves a few cells over the run: a wider
+    # initial blast gives its interface a leaf count in the 2k-20k range
+    cfg["r0"] = AMR["r0"] if cfg["p"] < 3 else 0.2
+    ic = lambda x: W.blast(x, (0.5, 0.5, 0.5), r0=cfg["r0"], width=width)
     f = pkg.Forest.from_workload(w, p=cfg["p"], precision=pkg.FP32, device=local, cfl=cfg["cfl"])
     stream = torch.cuda.Stream()
     f.set_stream(stream)
@@ -926,7 +929,7 @@ def main():
                     help="level jumps: the paper's guard-cell scheme (default) or the conservative mortar repair")
     ap.add_argument("--quick-line", action="store_true",
                     help="the step line without the over-L2, serving and AMR sub-objects")
-    ap.add_argument("--serve-sub-requests", type=int, default=48)
+    ap.add_argument("--serve-sub-requests", type=int, default=256)
     ap.add_argument("--amr-sub-periods", type=int, default=30)
     ap.add_argument("--amr-p", type=int, default=1, help="degree of the --amr run")
     ap.add_argument("--serve-requests", type=int, default=32)
