@@ -264,7 +264,8 @@ dgf_status dgf_status_word(dgf_forest* f, int32_t* status, int reset);
 /* Tile of the stage kernel: a work item is a z-chunk of zchunk cell layers
  * of one block (3D), resident_ctas the persistent grid size.  The first
  * dgf_rk_step of a 3D forest times one residual evaluation for every chunk
- * length n_seg, n_seg/2, ..., 1 and keeps the fastest; later forests of the
+ * length n_seg, n_seg/2, ..., 1 (with each stage kernel and grid, see
+ * dgf_stage_kernel and dgf_stage_grid) and keeps the fastest; later forests of the
  * same device, dimension, degree, n_seg, precision and leaf count in the
  * process reuse that choice, and a regrid keeps it (the environment variable
  * DGF_ZCHUNK fixes it instead).  The chunk length changes no bit of any result.  Not a paper
@@ -282,6 +283,13 @@ dgf_status dgf_tuning(const dgf_forest* f, int32_t* zchunk, int32_t* resident_ct
  * and independent of the z-chunk length.  The paper has no counterpart (a
  * tuning report). */
 dgf_status dgf_stage_kernel(const dgf_forest* f, int32_t* kernel);
+
+/* The stage kernel's grid (host value, no sync): *per_item = 0 for the
+ * persistent grid (resident_ctas CTAs of dgf_tuning walking the work items),
+ * 1 for one CTA per work item (the hardware scheduler hands out the items).
+ * Timed by the autotuner with the kernel and the chunk length;
+ * DGF_STAGE_GRID=persistent|items pins it.  Changes no bit of any result. */
+dgf_status dgf_stage_grid(const dgf_forest* f, int32_t* per_item);
 
 /* Kernel timing: when on, rk_step launches stage by stage (no graph) with
  * CUDA events around every kernel; dgf_kernel_times synchronises and returns

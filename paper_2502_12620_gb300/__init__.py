@@ -86,6 +86,7 @@ _SIGS = {
     "dgf_set_timing": [_P, ctypes.c_int],
     "dgf_tuning": [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
     "dgf_stage_kernel": [_P, ctypes.POINTER(ctypes.c_int32)],
+    "dgf_stage_grid": [_P, ctypes.POINTER(ctypes.c_int32)],
     "dgf_kernel_times": [_P, _P, _P, ctypes.c_int],
     "dgf_dg_residual_noalloc": [_P, _P, _P],
     "dgf_batch_create": [ctypes.c_int32, _P, ctypes.POINTER(_P)],
@@ -445,7 +446,10 @@ class Forest:
         _check(lib().dgf_tuning(self.h, ctypes.byref(z), ctypes.byref(c)))
         k = ctypes.c_int32()
         _check(lib().dgf_stage_kernel(self.h, ctypes.byref(k)))
-        return {"zchunk": z.value, "resident_ctas": c.value, "stage_kernel": ("pair", "classic")[k.value]}
+        g = ctypes.c_int32()
+        _check(lib().dgf_stage_grid(self.h, ctypes.byref(g)))
+        return {"zchunk": z.value, "resident_ctas": c.value, "stage_kernel": ("pair", "classic")[k.value],
+                "stage_grid": ("persistent", "items")[g.value]}
 
     def set_timing(self, on):
         _check(lib().dgf_set_timing(self.h, int(on)))

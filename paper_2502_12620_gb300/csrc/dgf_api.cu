@@ -13,6 +13,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <climits>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -221,6 +222,7 @@ struct dgf_forest {
   int slots = 0;            // resident CTAs of the chosen stage kernel
   int slots_k[2] = {0, 0};  // resident CTAs: [0] the cell-pair kernel where it applies, [1] k_stage
   int kernel = 0;           // stage kernel: 0 the cell-pair kernel where it applies, 1 k_stage
+  bool grid_items = false;  // stage grid: one CTA per work item instead of the persistent CTAs
   bool have_state = false;
   bool graph_valid = false;
   cudaGraphExec_t graph = nullptr;
@@ -359,6 +361,13 @@ bool chol_solve(int M, std::vector<double>& A, std::vector<double>& B, int nrhs)
     }
   }
   return true;
+}
+
+// DGF_STAGE_GRID=persistent|items fixes the stage grid; otherwise dflt
+bool grid_env(bool dflt) {
+  const char* g = getenv("DGF_STAGE_GRID");
+  if (!g) return dflt;
+  return strcmp(g, "items") == 0;
 }
 
 // the cell-pair FP32 stage kernel covers 3D forests of 8^3-cell blocks at
@@ -873,7 +882,9 @@ dgf_status build_device(dgf_forest* f) {
       if (const char* zc = getenv("DGF_ZCHUNK")) f->zchunk = std::max(1, std::min(n, atoi(zc)));
     }
   }
-  f->tuned = d != 3 || (getenv("DGF_ZCHUNK") != nullptr && getenv("DGF_STAGE_KERNEL") != nullptr);
+  f->grid_items = grid_env(false);
+  f->tuned = d != 3 || (getenv("DGF_ZCHUNK") != nullptr && getenv("DGF_STAGE_KERNEL") != nullptr &&
+                        getenv("DGF_STAGE_GRID") != nullptr);
   if (f->graph) {
     cudaGraphExecDestroy(f->graph);
     f->graph = nullptr;
@@ -892,7 +903,7 @@ RtStage stage_args(dgf_forest* f, int src, int dst, double ca, double cb, int mo
   r.nL = (int)f->nL;
   r.n = f->n;
   r.zchunk = f->zchunk;
-  r.slots = f->slots;
+  r.slots = f->grid_items ? INT_MAX : f->slots;  // the launch takes min(items, slots) CTAs
   r.kernel = f->kernel;
   r.affine = (const unsigned char*)f->affine.ptr;
   r.all_affine = f->all_affine ? 1 : 0;
@@ -1078,7 +1089,11 @@ dgf_status init_lambda(dgf_forest* f) {
 // a shape already timed in this process takes the earlier choice.
 // DGF_ZCHUNK fixes the chunk length, DGF_STAGE_KERNEL=classic|pair the kernel.
 std::mutex g_tune_mutex;
-std::map<std::vector<long long>, std::pair<int, int>> g_tune_cache;
+struct TuneChoice {
+  int zchunk, kernel;
+  bool grid_items;
+};
+std::map<std::vector<long long>, TuneChoice> g_tune_cache;
 
 dgf_status autotune(dgf_forest* f) {
   f->tuned = true;
@@ -1088,8 +1103,9 @@ dgf_status autotune(dgf_forest* f) {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      if (!getenv("DGF_ZCHUNK")) f->zchunk = it->second.first;
-      if (!getenv("DGF_STAGE_KERNEL")) f->kernel = it->second.second;
+      if (!getenv("DGF_ZCHUNK")) f->zchunk = it->second.zchunk;
+      if (!getenv("DGF_STAGE_KERNEL")) f->kernel = it->second.kernel;
+      f->grid_items = grid_env(it->second.grid_items);
       f->slots = f->slots_k[f->kernel];
       return DGF_OK;
     }
@@ -1106,16 +1122,22 @@ dgf_status autotune(dgf_forest* f) {
   if (getenv("DGF_ZCHUNK")) zs.push_back(f->zchunk);
   else
     for (int z = f->n; z >= 1; z /= 2) zs.push_back(z);
+  std::vector<int> grids;  // 0 persistent CTAs, 1 one CTA per work item
+  if (getenv("DGF_STAGE_GRID")) grids.push_back(grid_env(false) ? 1 : 0);
+  else grids = {0, 1};
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   int best_z = f->zchunk, best_k = f->kernel;
+  bool best_g = f->grid_items;
   float best = 1e30f;
   for (int kk : kernels) {
     f->kernel = kk;
     f->slots = f->slots_k[kk];
+    for (int gm : grids)
     for (int z : zs) {
       f->zchunk = z;
+      f->grid_items = gm != 0;
       float t[3];
       for (int r = 0; r < 4; ++r) {
         cudaEventRecord(a, f->stream);
@@ -1137,6 +1159,7 @@ dgf_status autotune(dgf_forest* f) {
         best = tt;
         best_z = z;
         best_k = kk;
+        best_g = gm != 0;
       }
     }
   }
@@ -1144,9 +1167,10 @@ dgf_status autotune(dgf_forest* f) {
   cudaEventDestroy(b);
   f->zchunk = best_z;
   f->kernel = best_k;
+  f->grid_items = best_g;
   f->slots = f->slots_k[best_k];
   std::lock_guard<std::mutex> lock(g_tune_mutex);
-  g_tune_cache[key] = {best_z, best_k};
+  g_tune_cache[key] = {best_z, best_k, best_g};
   return DGF_OK;
 }
 
@@ -1738,6 +1762,12 @@ dgf_status dgf_stage_kernel(const dgf_forest* f, int32_t* kernel) {
   return DGF_OK;
 }
 
+dgf_status dgf_stage_grid(const dgf_forest* f, int32_t* per_item) {
+  if (!f || !per_item) return fail(DGF_EINVAL, "null argument");
+  *per_item = f->grid_items ? 1 : 0;
+  return DGF_OK;
+}
+
 dgf_status dgf_set_limiter(dgf_forest* f, double eps) {
   if (dgf_status st = require_device(f)) return st;
   if (f->comp && eps > 0.0) return fail(DGF_EUNSUPPORTED, "the limiter is not available for DGF_FP32_COMP");
@@ -1852,12 +1882,14 @@ static dgf_status regrid(dgf_forest* f, const std::vector<uint64_t>& old_leaves)
   live = dgf_forest::Buf();
   const bool was_tuned = f->tuned;
   const int tuned_z = f->zchunk, tuned_k = f->kernel;
+  const bool tuned_g = f->grid_items;
   dgf_status st = build_device(f);
   if (was_tuned && f->d == 3) {
     // a regrid keeps the tuned stage kernel and chunk length (re-timing every
     // regrid costs more than it gains)
     f->tuned = true;
     if (!getenv("DGF_ZCHUNK")) f->zchunk = tuned_z;
+    f->grid_items = grid_env(tuned_g);
     if (!getenv("DGF_STAGE_KERNEL")) {
       f->kernel = tuned_k;
       f->slots = f->slots_k[tuned_k];

@@ -292,6 +292,27 @@ def test_chunk_length_does_not_change_bits(dgf, prec, kernel, monkeypatch):
         assert np.array_equal(R, out[0][0]) and np.array_equal(U, out[0][1])
 
 
+@pytest.mark.parametrize("prec,kernel", [("fp32", "pair"), ("fp32", "classic"), ("fp64", "classic")])
+def test_stage_grid_does_not_change_bits(dgf, prec, kernel, monkeypatch):
+    """The stage grid (persistent CTAs walking the work items, or one CTA per
+    item; a launch choice the autotuner times) leaves every bit unchanged."""
+    w = W.jitter3d_forest(seed=2)
+    U0 = W.random_modal_state(71, 3, 8, 2, seed=12)
+    monkeypatch.setenv("DGF_STAGE_KERNEL", kernel)
+    monkeypatch.setenv("DGF_ZCHUNK", "2")
+    out = []
+    for grid in ("persistent", "items"):
+        monkeypatch.setenv("DGF_STAGE_GRID", grid)
+        f = dgf.Forest.from_workload(w, p=2, precision=prec)
+        assert f.tuning()["stage_grid"] == grid
+        f.set_state(U0)
+        R = f.dg_residual()
+        f.run(2)
+        out.append((R, f.get_state()))
+        f.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
 # ----------------------------------------------------- mortar mode (R15)
 @pytest.mark.parametrize("case", sorted(SMALL))
 @pytest.mark.parametrize("p", [0, 1, 2, 3])
