@@ -46,11 +46,12 @@ HBM_FALLBACK = 6800.0
 # stages of one time step (ncu dram__bytes_read.sum + dram__bytes_write.sum,
 # cold L2), by (workload, stage kernel), for the kernels as they are now; a
 # workload without a capture of the current kernel reports null.  The 16^3
-# cube at p = 2 is 8 x the 512-leaf cube's figure (same kernel and tiling,
-# state above L2 in both, traffic proportional to the leaves: 377.1 MB there,
-# the algorithmic 377.5 MB); the 512-leaf cube at p = 1 fits L2, so no
-# figure is scaled to the 16^3 cube at p = 1.
-STAGE_TRAFFIC_BYTES = {("jitter3d", "pair"): 47.41e6, ("cube16p2", "pair"): 8 * 377.1e6}
+# cube at p = 2 is 8 x the 512-leaf cube's figure (same kernel, tiling and
+# grid of one CTA per work item, state above L2 in both, traffic
+# proportional to the leaves: 377.0 MB there, the algorithmic 377.5 MB); the
+# 512-leaf cube at p = 1 fits L2, so no figure is scaled to the 16^3 cube at
+# p = 1.
+STAGE_TRAFFIC_BYTES = {("jitter3d", "pair"): 47.8e6, ("cube16p2", "pair"): 8 * 377.0e6}
 TRAFFIC_HOW = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, cold L2, mean of the 3 stages of a step"
 
 
