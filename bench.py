@@ -57,8 +57,11 @@ TRAFFIC_HOW = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, cold
 
 def stage_kernel_name(f, p):
     """The stage kernel the forest's time step launches (after tuning)."""
-    if f.tuning()["stage_kernel"] == "pair":
+    k = f.tuning()["stage_kernel"]
+    if k == "pair":
         return f"k_stage_pair<{p}>"
+    if k == "pair5":
+        return f"k_stage_pair<{p}> (five CTAs per SM)"
     return f"k_stage<3,{p},8,float>"
 
 

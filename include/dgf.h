@@ -274,10 +274,12 @@ dgf_status dgf_tuning(const dgf_forest* f, int32_t* zchunk, int32_t* resident_ct
 
 /* Which stage kernel the forest's time step launches (host value, no sync):
  * 0 = the cell-pair FP32 kernel (3D forests of 8^3-cell blocks at p = 1, 2
- * in plain FP32: f32x2 arithmetic on cell pairs, TMA-staged layers), 1 =
- * the general layer-sweep kernel.  The first dgf_rk_step of a 3D forest
- * times both where both apply and keeps the faster (the z-chunk length is
- * tuned with it); DGF_STAGE_KERNEL=pair|classic in the environment pins the
+ * in plain FP32: f32x2 arithmetic on cell pairs, TMA-staged layers; four
+ * CTAs per SM at p = 1), 1 = the general layer-sweep kernel, 2 = the
+ * cell-pair kernel in its five-CTA shape (p = 1 only: more warps, fewer
+ * registers).  The first dgf_rk_step of a 3D forest times every kernel that
+ * applies and keeps the fastest (the z-chunk length and the grid are tuned
+ * with it); DGF_STAGE_KERNEL=pair|pair5|classic in the environment pins the
  * choice.  The two kernels round differently, so results agree within the
  * FP32 tolerance, not bit for bit; a given kernel is bitwise reproducible
  * and independent of the z-chunk length.  The paper has no counterpart (a

@@ -448,7 +448,7 @@ class Forest:
         _check(lib().dgf_stage_kernel(self.h, ctypes.byref(k)))
         g = ctypes.c_int32()
         _check(lib().dgf_stage_grid(self.h, ctypes.byref(g)))
-        return {"zchunk": z.value, "resident_ctas": c.value, "stage_kernel": ("pair", "classic")[k.value],
+        return {"zchunk": z.value, "resident_ctas": c.value, "stage_kernel": ("pair", "classic", "pair5")[k.value],
                 "stage_grid": ("persistent", "items")[g.value]}
 
     def set_timing(self, on):

@@ -220,7 +220,9 @@ struct dgf_forest {
   std::vector<double> bstate_h;
   Buf bstate;
   int slots = 0;            // resident CTAs of the chosen stage kernel
-  int slots_k[2] = {0, 0};  // resident CTAs: [0] the cell-pair kernel where it applies, [1] k_stage
+  // resident CTAs: [0] the cell-pair kernel where it applies, [1] k_stage,
+  // [2] the cell-pair kernel's five-CTA shape (p = 1; 0 elsewhere)
+  int slots_k[3] = {0, 0, 0};
   int kernel = 0;           // stage kernel: 0 the cell-pair kernel where it applies, 1 k_stage
   bool grid_items = false;  // stage grid: one CTA per work item instead of the persistent CTAs
   bool have_state = false;
@@ -850,7 +852,7 @@ dgf_status build_device(dgf_forest* f) {
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device);
     const int cp = f->comp ? 1 : 0;
-    for (int kk = 0; kk < 2; ++kk) {
+    for (int kk = 0; kk < 3; ++kk) {
       int occ = 0;
       if (d == 2)
         occ = f->precision == DGF_FP64 ? stage_occupancy<2, double>(f->p, n, cp, kk)
@@ -860,11 +862,15 @@ dgf_status build_device(dgf_forest* f) {
                                        : stage_occupancy<3, float>(f->p, n, cp, kk);
       f->slots_k[kk] = occ * sms;
     }
+    if (!(pair_applies(f) && f->p == 1)) f->slots_k[2] = 0;
     // the cell-pair kernel unless it does not apply (its slots equal k_stage's
-    // then) or DGF_STAGE_KERNEL=classic; the autotuner may still pick k_stage
+    // then) or DGF_STAGE_KERNEL=classic|pair5; the autotuner may still pick
+    // another
     f->kernel = pair_applies(f) ? 0 : 1;
-    if (const char* ks = getenv("DGF_STAGE_KERNEL"))
+    if (const char* ks = getenv("DGF_STAGE_KERNEL")) {
       if (strcmp(ks, "classic") == 0) f->kernel = 1;
+      if (strcmp(ks, "pair5") == 0 && f->slots_k[2] > 0) f->kernel = 2;
+    }
     f->slots = f->slots_k[f->kernel];
     f->zchunk = 1;
     if (d == 3 && f->slots > 0) {
@@ -1115,9 +1121,13 @@ dgf_status autotune(dgf_forest* f) {
   if (st) return st;
   std::vector<int> kernels;
   const char* ks = getenv("DGF_STAGE_KERNEL");
-  // the cell-pair kernel is a candidate only where it applies (distinct slots)
-  if (!(ks && strcmp(ks, "classic") == 0) && pair_applies(f) && f->slots_k[0] > 0) kernels.push_back(0);
-  if (!(ks && strcmp(ks, "pair") == 0) || kernels.empty()) kernels.push_back(1);
+  // the cell-pair kernel is a candidate only where it applies (distinct
+  // slots), its five-CTA shape at p = 1; DGF_STAGE_KERNEL=pair|pair5|classic
+  // keeps one
+  const bool any = ks == nullptr;
+  if ((any || strcmp(ks, "pair") == 0) && pair_applies(f) && f->slots_k[0] > 0) kernels.push_back(0);
+  if ((any || strcmp(ks, "pair5") == 0) && f->slots_k[2] > 0) kernels.push_back(2);
+  if (any || strcmp(ks, "classic") == 0 || kernels.empty()) kernels.push_back(1);
   std::vector<int> zs;
   if (getenv("DGF_ZCHUNK")) zs.push_back(f->zchunk);
   else

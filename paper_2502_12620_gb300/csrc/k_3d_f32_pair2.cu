@@ -2,7 +2,7 @@
 #include "stage_pair.cuh"
 
 namespace dgf {
-template cudaError_t stage_pair_launch<2>(const StageArgs<3, 2, float>&, int, bool, bool, cudaStream_t);
-template int stage_pair_blocks_per_sm<2>();
+template cudaError_t stage_pair_launch<2>(const StageArgs<3, 2, float>&, int, bool, bool, cudaStream_t, int);
+template int stage_pair_blocks_per_sm<2>(int);
 template cudaError_t stage_pair_launch_batch<2>(const StageArgs<3, 2, float>&, int, bool, cudaStream_t);
 }  // namespace dgf

@@ -83,12 +83,13 @@ template <int D, int P, int NS, typename Real>
 constexpr bool pair_shape() {
   return D == 3 && NS == 8 && (P == 1 || P == 2) && std::is_same<Real, float>::value;
 }
-// launch and occupancy of the cell-pair kernel (k_3d_f32_pair<P>.cu)
+// launch and occupancy of the cell-pair kernel (k_3d_f32_pair<P>.cu); v
+// selects its CTA shape (p = 1: 0 four CTAs per SM, 1 five)
 template <int P>
 cudaError_t stage_pair_launch(const StageArgs<3, P, float>& a, int grid, bool mortar, bool all_affine,
-                              cudaStream_t s);
+                              cudaStream_t s, int v);
 template <int P>
-int stage_pair_blocks_per_sm();
+int stage_pair_blocks_per_sm(int v);
 template <int P>
 cudaError_t stage_pair_launch_batch(const StageArgs<3, P, float>& a, int grid, bool all_affine, cudaStream_t s);
 
@@ -98,10 +99,12 @@ static int stage_blocks_per_sm_classic();
 template <int D, int P, int NS, typename Real>
 static int stage_blocks_per_sm_ns(int comp, int kernel) {
   if constexpr (pair_shape<D, P, NS, Real>()) {
-    if (!comp && kernel == 0) {
-      const int nb = stage_pair_blocks_per_sm<P>();
+    // kernel 2 (the five-CTA shape) exists at p = 1 only
+    if (!comp && (kernel == 0 || (kernel == 2 && P == 1))) {
+      const int nb = stage_pair_blocks_per_sm<P>(kernel == 2);
       if (nb > 0) return nb;
     }
+    if (kernel == 2) return 0;
   }
   return stage_blocks_per_sm_classic<D, P, NS, Real>();
 }
@@ -146,9 +149,10 @@ static cudaError_t stage_ns(const StageArgs<D, P, Real>& a, int slots, int comp,
   const int items = a.nL * a.nchunks * (NS / stage_rows<D, P, Real>(NS));
   const int grid = items < slots ? items : slots;
   if constexpr (pair_shape<D, P, NS, Real>()) {
-    if (!comp && kernel == 0) {
+    if (!comp && (kernel == 0 || kernel == 2)) {
       const int g = a.nL * a.nchunks < slots ? a.nL * a.nchunks : slots;
-      if constexpr (P == 1 || P == 2) return stage_pair_launch<P>(a, g, a.fluxmask != nullptr, all_affine != 0, s);
+      if constexpr (P == 1 || P == 2)
+        return stage_pair_launch<P>(a, g, a.fluxmask != nullptr, all_affine != 0, s, kernel == 2 ? 1 : 0);
     }
   }
   if (a.fluxmask) return stage_mortar_launch<D, P, NS, Real>(a, grid, smem, comp, s);
@@ -420,7 +424,7 @@ template <int D, int P, typename Real>
 static int stage_batch_blocks_per_sm_p(int kernel, int all_affine) {
   if constexpr (D == 3 && std::is_same<Real, float>::value) {
     if constexpr (P == 1 || P == 2) {
-      if (kernel == 0) return stage_pair_blocks_per_sm<P>();
+      if (kernel == 0) return stage_pair_blocks_per_sm<P>(0);
     }
     constexpr int YS = stage_rows<D, P, Real>(8);
     const size_t smem = stage_smem<D, P, Real>(8, YS);

@@ -216,10 +216,9 @@ struct LineGeo2 {
   }
 };
 
-#ifndef DGF_PAIR_MINB_P1
-#define DGF_PAIR_MINB_P1 4
-#endif
-template <int P>
+// V selects the CTA shape at p = 1 (0: four CTAs per SM, 1: five); one
+// shape at p = 2
+template <int P, int V = 0>
 struct PairCfg {
   static constexpr int N = P + 1, Q = N * N * N, NFP = N * N, NV = 5;
   static constexpr int NT = 32 * NFP;  // one warp per face point
@@ -229,8 +228,9 @@ struct PairCfg {
   static constexpr size_t SMEM = (size_t)(2 * ROWS * 64 + 2 * NG * 64 + ROWS * 64) * sizeof(float);
   // resident CTAs per SM: shared memory allows 2 at p = 2 (about 114 KB each)
   // and 5 at p = 1; at p = 1 four CTAs leave 128 registers per thread (16
-  // warps, 4 per scheduler), five only 96
-  static constexpr int MINB = P <= 1 ? DGF_PAIR_MINB_P1 : 2;
+  // warps, 4 per scheduler), five only 96 (more warps, more spills: the
+  // autotuner times both)
+  static constexpr int MINB = P <= 1 ? (V ? 5 : 4) : 2;
 };
 
 }  // namespace pairk
@@ -239,12 +239,12 @@ struct PairCfg {
 // the curved code paths are not compiled into this instantiation)
 // BATCH: one launch for every forest of a batch (A.members; the tables and
 // stage coefficients of A are common to all of them).
-template <int P, bool MORTAR, bool AFF, bool BATCH = false>
-__global__ void __launch_bounds__(pairk::PairCfg<P>::NT, pairk::PairCfg<P>::MINB)
+template <int P, bool MORTAR, bool AFF, bool BATCH = false, int V = 0>
+__global__ void __launch_bounds__(pairk::PairCfg<P, V>::NT, pairk::PairCfg<P, V>::MINB)
     k_stage_pair(const __grid_constant__ StageArgs<3, P, float> A) {
   static_assert(!(BATCH && MORTAR), "batches run without the mortar repair");
   using namespace pairk;
-  using C = PairCfg<P>;
+  using C = PairCfg<P, V>;
   constexpr int N = C::N, Q = C::Q, NFP = C::NFP, NV = 5, ROWS = C::ROWS, NG = C::NG;
   constexpr int n = 8, LAY = 64, nc = 512, nt = 64;
   const auto& T = A.T;
@@ -806,20 +806,29 @@ __global__ void __launch_bounds__(pairk::PairCfg<P>::NT, pairk::PairCfg<P>::MINB
   }
 }
 
-// launch (grid = persistent CTAs) and resident CTAs per SM, for the launch
-// layer in kernels_inst.cuh
-template <int P>
-cudaError_t stage_pair_launch(const StageArgs<3, P, float>& a, int grid, bool mortar, bool all_affine,
-                              cudaStream_t s) {
-  using C = pairk::PairCfg<P>;
+// launch (grid = persistent CTAs, or one per work item) and resident CTAs
+// per SM, for the launch layer in kernels_inst.cuh; v = the CTA shape
+template <int P, int V>
+cudaError_t stage_pair_launch_v(const StageArgs<3, P, float>& a, int grid, bool mortar, bool all_affine,
+                                cudaStream_t s) {
+  using C = pairk::PairCfg<P, V>;
   if (mortar) {
-    if (all_affine) k_stage_pair<P, true, true><<<grid, C::NT, C::SMEM, s>>>(a);
-    else k_stage_pair<P, true, false><<<grid, C::NT, C::SMEM, s>>>(a);
+    if (all_affine) k_stage_pair<P, true, true, false, V><<<grid, C::NT, C::SMEM, s>>>(a);
+    else k_stage_pair<P, true, false, false, V><<<grid, C::NT, C::SMEM, s>>>(a);
   } else {
-    if (all_affine) k_stage_pair<P, false, true><<<grid, C::NT, C::SMEM, s>>>(a);
-    else k_stage_pair<P, false, false><<<grid, C::NT, C::SMEM, s>>>(a);
+    if (all_affine) k_stage_pair<P, false, true, false, V><<<grid, C::NT, C::SMEM, s>>>(a);
+    else k_stage_pair<P, false, false, false, V><<<grid, C::NT, C::SMEM, s>>>(a);
   }
   return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t stage_pair_launch(const StageArgs<3, P, float>& a, int grid, bool mortar, bool all_affine,
+                              cudaStream_t s, int v) {
+  if constexpr (P == 1) {
+    if (v) return stage_pair_launch_v<P, 1>(a, grid, mortar, all_affine, s);
+  }
+  return stage_pair_launch_v<P, 0>(a, grid, mortar, all_affine, s);
 }
 
 // one launch over the forests of a batch (a.members); plain form, no mortar
@@ -831,24 +840,38 @@ cudaError_t stage_pair_launch_batch(const StageArgs<3, P, float>& a, int grid, b
   return cudaGetLastError();
 }
 
-template <int P, bool MORTAR, bool AFF, bool BATCH = false>
+template <int P, bool MORTAR, bool AFF, bool BATCH = false, int V = 0>
 int pair_blocks_per_sm_one() {
-  using C = pairk::PairCfg<P>;
-  if (cudaFuncSetAttribute(k_stage_pair<P, MORTAR, AFF, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  using C = pairk::PairCfg<P, V>;
+  if (cudaFuncSetAttribute(k_stage_pair<P, MORTAR, AFF, BATCH, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)C::SMEM) != cudaSuccess)
     return 0;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage_pair<P, MORTAR, AFF, BATCH>, C::NT, C::SMEM) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage_pair<P, MORTAR, AFF, BATCH, V>, C::NT, C::SMEM) !=
       cudaSuccess)
     return 0;
   return nb;
 }
 
+// the fewest resident CTAs over the instantiations one forest may launch
+// (shape v; the batch instantiations have shape 0)
 template <int P>
-int stage_pair_blocks_per_sm() {
-  const int o[6] = {pair_blocks_per_sm_one<P, false, false>(), pair_blocks_per_sm_one<P, true, false>(),
-                    pair_blocks_per_sm_one<P, false, true>(), pair_blocks_per_sm_one<P, true, true>(),
-                    pair_blocks_per_sm_one<P, false, false, true>(), pair_blocks_per_sm_one<P, false, true, true>()};
+int stage_pair_blocks_per_sm(int v) {
+  int o[6];
+  if (P == 1 && v) {
+    o[0] = pair_blocks_per_sm_one<P, false, false, false, 1>();
+    o[1] = pair_blocks_per_sm_one<P, true, false, false, 1>();
+    o[2] = pair_blocks_per_sm_one<P, false, true, false, 1>();
+    o[3] = pair_blocks_per_sm_one<P, true, true, false, 1>();
+    o[4] = o[5] = o[0];
+  } else {
+    o[0] = pair_blocks_per_sm_one<P, false, false>();
+    o[1] = pair_blocks_per_sm_one<P, true, false>();
+    o[2] = pair_blocks_per_sm_one<P, false, true>();
+    o[3] = pair_blocks_per_sm_one<P, true, true>();
+    o[4] = pair_blocks_per_sm_one<P, false, false, true>();
+    o[5] = pair_blocks_per_sm_one<P, false, true, true>();
+  }
   int lo = o[0];
   for (int i = 1; i < 6; ++i) lo = o[i] < lo ? o[i] : lo;
   return lo;

@@ -24,8 +24,10 @@ pytestmark = pytest.mark.gpu
 
 # (precision, p, stage kernel): FP32 at p = 1, 2 has two stage kernels (the
 # cell-pair kernel and the layer-sweep kernel; the autotuner picks one by
-# timing), both are compared
-CONFIGS = [("fp32", 1, "pair"), ("fp32", 1, "classic"), ("fp32", 2, "pair"), ("fp32", 2, "classic"),
+# timing), both are compared, and at p = 1 the cell-pair kernel's two CTA
+# shapes (four and five CTAs per SM)
+CONFIGS = [("fp32", 1, "pair"), ("fp32", 1, "pair5"), ("fp32", 1, "classic"), ("fp32", 2, "pair"),
+           ("fp32", 2, "classic"),
            ("fp32", 3, "classic"), ("fp64", 1, "classic"), ("fp64", 2, "classic"), ("fp32_comp", 2, "classic")]
 
 
@@ -64,3 +66,24 @@ def test_n8_residual_and_step_match_oracle(dgf, prec, p, kernel, mode, monkeypat
     assert rel(f.get_state(), U1) < TOL["fp64" if prec == "fp64" else "fp32"]
     assert f.status_word() == 0
     f.close()
+
+
+@pytest.mark.parametrize("mode", ["paper", "mortar"])
+def test_n8_pair_cta_shapes_give_the_same_bits(dgf, mode, monkeypatch):
+    """The cell-pair kernel's two CTA shapes at p = 1 are one source compiled
+    with different register budgets: the same residual and time step, bit
+    for bit, on the jittered rotated forest with a level jump."""
+    w = two_root_forest()
+    U = W.random_modal_state(9, 3, 8, 1, seed=21).astype(np.float32).astype(np.float64)
+    out = []
+    for kernel in ("pair", "pair5"):
+        monkeypatch.setenv("DGF_STAGE_KERNEL", kernel)
+        f = dgf.Forest.from_workload(w, p=1, precision=dgf.FP32, cfl=0.2, nonconforming=mode)
+        assert f.tuning()["stage_kernel"] == kernel
+        f.set_state(U)
+        R = f.dg_residual()
+        f.rk_step()
+        f.rk_step()
+        out.append((R, f.get_state()))
+        f.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
