@@ -421,6 +421,12 @@ def run_ours(args):
     if not args.quick_line:
         # affine periodic cubes far above L2 (each state copy 0.34 / 1.13 GB)
         line["over_l2"] = {k: over_l2_case(k, args, stream, flush, pk, pk_kind, torch, pkg) for k in OVER_L2}
+        line["batch"] = {}
+        for q in (1, 2):
+            try:
+                line["batch"][f"p{q}"] = batch_case(q, args, flush, pk, pk_kind, torch, pkg)
+            except pkg.DgfError as e:  # reported, not hidden
+                line["batch"][f"p{q}"] = {"error": str(e)}
         line["serve"] = run_serve(args, sub=True)
         line["amr"] = {}
         for q in (1, 3):
@@ -433,6 +439,59 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
     return 0
+
+
+# the batched path: one batch of three affine periodic cubes of 8^3, 10^3 and
+# 12^3 roots (3,240 blocks; 0.27 GB per state copy at p = 1, 0.9 GB at p = 2)
+BATCH_CUBES = (8, 10, 12)
+
+
+def batch_case(p, args, flush, pk, pk_kind, torch, pkg):
+    """DOF-updates/s of one batch of the BATCH_CUBES forests advanced together
+    (one launch per kernel and stage for all three, one CUDA graph per time
+    increment, L2 flushed between timed steps, CUDA events on the batch
+    stream) and the step's fraction of the measured copy peak: the three
+    stage launches' algorithmic bytes (as for a single forest) over the whole
+    step, guard traces and time increments included, so a lower bound of the
+    batch stage kernel's own fraction."""
+    stream = torch.cuda.Stream()
+    fs = []
+    for B in BATCH_CUBES:
+        f = pkg.Forest.from_workload(W.periodic_cube_forest(B), p=p, precision=pkg.FP32, cfl=0.1)
+        f.set_state_nodal(vortex(f.quad_points()))
+        fs.append(f)
+    b = pkg.Batch(stream=stream)
+    b.set(fs, [1e9] * len(fs))
+    b.step(args.warmup)
+    b.sync()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            evs[i][0].record(stream)
+            b.step(1)
+            evs[i][1].record(stream)
+    stream.synchronize()
+    ms = sum(a.elapsed_time(c) for a, c in evs)
+    dof = sum(f.n_leaves * f.nv * f.M * f.nc for f in fs)
+    cells = sum(f.n_leaves * f.nc for f in fs)
+    alg_step = dof * 4 * (2 + 3 + 3) + cells * 4
+    achieved = alg_step / (ms / args.steps / 1e3) / 1e9
+    out = {"workload": f"batch-of-3-periodic-cubes-{'-'.join(f'{B}^3' for B in BATCH_CUBES)}-roots-n8-p{p}",
+           "members": len(fs), "blocks": sum(f.n_leaves for f in fs), "p": p, "dof": dof,
+           "value": dof * 3 * args.steps / (ms / 1e3), "unit": "DOF-updates/s", "ms_per_step": ms / args.steps,
+           "steps": args.steps,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                        "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk_kind,
+                        "scope": "whole batch step (3 stage launches, 3 guard launches, the dt launch)",
+                        "bytes_per_step": alg_step},
+           "status_words": [f.status_word() for f in fs]}
+    b.close()
+    for f in fs:
+        f.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 # affine periodic cubes of B^3 roots of 8^3 cells whose state is far above the
