@@ -8,7 +8,9 @@ memory on a stream of its own.  Here tensors of the sizes of a forest's
 buffers are released while a fill of them is still queued (behind a bounded
 sleep) on the current stream, a forest is built at once and stepped after the
 fill has run: its result must be the one of a forest built with nothing
-pending."""
+pending.  Whether a shared pool would hand the forest those very blocks
+depends on the allocator's choices, so the test sets up the conditions of
+the hazard rather than forcing it; it guards the separation of the pools."""
 import time
 
 import numpy as np
