@@ -179,11 +179,15 @@ class Server:
     request larger than the whole budget runs alone.  steps_per_round is the
     most time steps enqueued on one stream at a time.  With build_workers > 0
     new solves are built (forest, initial state, first steps) on worker
-    threads, so the streams already admitted keep getting work meanwhile."""
+    threads, so the streams already admitted keep getting work meanwhile.
+    With batched=True, 3D FP32 solves of 8^3-cell blocks join the batch of
+    their degree and size class (batch_factory() makes one; default: the
+    library's Batch) and advance in rounds of batch_steps to 8 batch_steps
+    steps; the others keep a stream each."""
 
     def __init__(self, device=0, hbm_budget=None, max_active=16, steps_per_round=8,
                  build_workers=2, solve_factory=None, clock=time.perf_counter, sleep=time.sleep,
-                 batched=False, batch_steps=8, large_dof=64 << 20):
+                 batched=False, batch_steps=8, large_dof=64 << 20, batch_factory=None):
         self.device = device
         if hbm_budget is None:
             import torch
@@ -202,6 +206,7 @@ class Server:
         self.batch_steps = int(batch_steps)
         self.large_dof = int(large_dof)
         self.groups = {}  # (degree, large) -> _Group (batched mode)
+        self.batch_factory = batch_factory or (lambda: Batch(self.device))
 
     def _next_k(self, s, t, steps):
         """Steps to enqueue next: the predicted remainder (from the mean dt so
@@ -336,7 +341,7 @@ class Server:
                     if getattr(s, "batched", False):
                         key = self._group_key(s)
                         if key not in self.groups:
-                            self.groups[key] = _Group(Batch(self.device))
+                            self.groups[key] = _Group(self.batch_factory())
                         self.groups[key].joining.append(s)
                     item[0] = None
                     progressed = True

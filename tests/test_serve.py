@@ -135,6 +135,125 @@ def test_serving_mix_recipe():
                and np.array_equal(a["centre"], b["centre"]) for a, b in zip(R, again))
 
 
+# ------------------------------------------------- batched mode (host logic)
+class FakeForest:
+    """Time, step count and status of one batch member (a stand-in)."""
+
+    def __init__(self, dt, fail_at=None):
+        self.dt, self.fail_at = dt, fail_at
+        self.t, self.steps, self.status, self.t_end = 0.0, 0, 0, math.inf
+
+
+class FakeBatch:
+    """Advances every member like the library's batch: dt clipped to the
+    member's end time, nothing once it is there; a member may turn
+    non-finite (status -4) at a given step, after which its dt is 0."""
+    made = []
+
+    def __init__(self, clock):
+        self.clock, self.members, self.steps_log, self.sets = clock, [], [], []
+        FakeBatch.made.append(self)
+
+    def set(self, forests, t_ends):
+        self.members = list(forests)
+        self.sets.append(len(forests))
+        for f, t in zip(forests, t_ends):
+            f.t_end = t
+
+    def step(self, k):
+        self.steps_log.append(k)
+        for _ in range(k):
+            for f in self.members:
+                d = min(f.dt, f.t_end - f.t) if f.status == 0 else 0.0
+                if d > 0:
+                    f.t += d
+                    f.steps += 1
+                    if f.fail_at is not None and f.steps >= f.fail_at:
+                        f.status = -4
+        self.clock.t += 1e-4 * k
+
+    def idle(self):
+        return True
+
+    def progress(self):
+        return (np.array([f.t for f in self.members]), np.array([f.steps for f in self.members], np.int64),
+                np.array([f.status for f in self.members], np.int32))
+
+    def sync(self):
+        pass
+
+    def close(self):
+        pass
+
+
+class FakeBatchSolve:
+    """A batched solve: its forest is advanced by the batch only."""
+
+    def __init__(self, req, dt=0.01, fail_at=None):
+        self.req, self.f, self.dof = req, FakeForest(dt, fail_at), 100
+        self.device_bytes = footprint_bytes(req.workload, req.p, req.precision)
+
+    def enqueue(self, k):
+        raise AssertionError("a batched solve is never stepped on its own stream")
+
+    def finish(self, keep_state):
+        return None, self.f.status
+
+
+def _fake_steps(t_end, dt=0.01):
+    """Steps the fakes take to reach t_end (the same clipped accumulation)."""
+    t, n = 0.0, 0
+    while min(dt, t_end - t) > 0:
+        t += min(dt, t_end - t)
+        n += 1
+    return n
+
+
+def _breq(rid, arrival, p=1, t_end=0.05, precision=FP32):
+    return Request(rid, arrival, W.periodic_cube_forest(2, n_seg=8), p, t_end, None, precision)
+
+
+def _batched_server(clock, factory, **kw):
+    return Server(hbm_budget=10 ** 12, max_active=6, build_workers=0, solve_factory=factory, clock=clock,
+                  sleep=clock.sleep, batched=True, batch_steps=8, batch_factory=lambda: FakeBatch(clock), **kw)
+
+
+def test_batched_mode_groups_by_degree_and_finishes_every_solve_at_its_end_time():
+    clock = FakeClock()
+    FakeBatch.made = []
+    reqs = [_breq(i, 0.002 * i, p=1 + i % 2, t_end=0.03 + 0.07 * (i % 4)) for i in range(10)]
+    res = _batched_server(clock, lambda r: FakeBatchSolve(r)).run(reqs)
+    for r, q in zip(res, reqs):
+        assert r.status == 0 and abs(r.t - q.t_end) < 1e-12
+        assert r.steps == _fake_steps(q.t_end)
+    assert len(FakeBatch.made) == 2  # one batch per degree (all small)
+    for b in FakeBatch.made:
+        assert all(8 <= k <= 64 for k in b.steps_log)  # rounds of batch_steps .. 8 batch_steps
+        assert b.sets[0] >= 1 and max(b.sets) <= 6
+
+
+def test_batched_mode_retires_a_failed_member_and_serves_the_rest():
+    clock = FakeClock()
+    FakeBatch.made = []
+    reqs = [_breq(i, 0.0, t_end=0.2) for i in range(4)]
+    res = _batched_server(clock, lambda r: FakeBatchSolve(r, fail_at=3 if r.rid == 1 else None)).run(reqs)
+    assert [r.status for r in res] == [0, -4, 0, 0]
+    assert res[1].steps == 3 and res[1].t < reqs[1].t_end
+    assert all(abs(r.t - 0.2) < 1e-12 and r.steps == _fake_steps(0.2) for i, r in enumerate(res) if i != 1)
+
+
+def test_batched_mode_keeps_other_solves_on_their_own_streams():
+    clock = FakeClock()
+    FakeBatch.made = []
+    FakeSolve.log = []
+    reqs = [_breq(0, 0.0), _breq(1, 0.0, precision=FP64), _req(2, 0.0)]  # FP32 8^3, FP64 8^3, FP32 2^3 blocks
+    factory = lambda r: FakeBatchSolve(r) if r.rid == 0 else FakeSolve(r, clock)
+    res = _batched_server(clock, factory).run(reqs)
+    assert all(r.status == 0 and abs(r.t - q.t_end) < 1e-12 for r, q in zip(res, reqs))
+    assert len(FakeBatch.made) == 1 and FakeBatch.made[0].sets[0] == 1
+    assert {rid for ev, rid in FakeSolve.log if ev == "finish"} == {1, 2}
+
+
 # ------------------------------------------------------------------ GPU
 def _gpu_requests():
     # a mix of dimensions, degrees, precisions and refinement
