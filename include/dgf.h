@@ -19,10 +19,11 @@
  *   - A forest is an opaque handle created by dgf_forest_create and owned by
  *     the caller until dgf_forest_destroy.  Device buffers belong to the
  *     forest; they come from the caller's dgf_allocator (if given) or from
- *     cudaMalloc.  Host arrays passed in are copied before the call returns.
- *   - GPU work is enqueued on the stream set by dgf_set_stream (default: the
- *     legacy default stream).  Only calls that return host values
- *     synchronise with that stream.
+ *     cudaMalloc.  Host arrays passed in are copied before the call returns
+ *     (a call that copies one to the device waits for that copy).
+ *   - GPU work is enqueued on the stream set by dgf_set_stream (default: a
+ *     non-blocking stream the forest creates and owns).  Only calls that
+ *     return host values or read host arrays synchronise with that stream.
  *   - Pointers flagged "device" must be device pointers valid on the forest's
  *     device; "host" pointers are plain host memory.  An is_device argument
  *     selects between the two.
@@ -140,7 +141,8 @@ dgf_status dgf_forest_create(const dgf_forest_desc* desc, const dgf_allocator* a
                              dgf_forest** out);
 dgf_status dgf_forest_destroy(dgf_forest* f);
 
-/* Stream for all GPU work of this forest (a cudaStream_t, NULL = legacy). */
+/* Stream for all GPU work of this forest (a cudaStream_t, NULL = legacy);
+ * waits for the work enqueued on the previous one. */
 dgf_status dgf_set_stream(dgf_forest* f, void* stream);
 
 /* Refinement (Sec. 3.1, 3.3, 3.4): refine the given leaves (ids in the
