@@ -494,6 +494,22 @@ def batch_case(p, args, flush, pk, pk_kind, torch, pkg):
     return out
 
 
+def run_batch(args):
+    """The bench line's batched-path records alone (rank 0 at N = 1 prints
+    one JSON line per degree)."""
+    import torch
+    import paper_2502_12620_gb300 as pkg
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    pk, pk_kind = peaks()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for q in (1, 2):
+        out = batch_case(q, args, flush, pk, pk_kind, torch, pkg)
+        if rank == 0:
+            print(json.dumps({"metric": "batched path DOF-updates/s per RK stage", "impl": "ours", **out}))
+    return 0
+
+
 # affine periodic cubes of B^3 roots of 8^3 cells whose state is far above the
 # 129 MB L2: the roofline of the stage kernel where HBM is the bound
 OVER_L2 = {
@@ -987,6 +1003,8 @@ def main():
                     help="precision of the --quick run")
     ap.add_argument("--serve", action="store_true", help="continuous-batching run instead of the step benchmark")
     ap.add_argument("--amr", action="store_true", help="dynamic-refinement blast run (steps = regrid periods)")
+    ap.add_argument("--batch", action="store_true",
+                    help="the batched path alone: one batch of three affine cubes at p = 1 and 2")
     ap.add_argument("--sweep", action="store_true", help="accuracy / precision sweep on periodic vortex cubes")
     ap.add_argument("--nonconforming", default="paper", choices=["paper", "mortar"],
                     help="level jumps: the paper's guard-cell scheme (default) or the conservative mortar repair")
@@ -1013,6 +1031,8 @@ def main():
         return run_serve(args)
     if args.amr:
         return run_amr(args)
+    if args.batch:
+        return run_batch(args)
     if args.sweep:
         return run_sweep(args)
     return run_ours(args)
